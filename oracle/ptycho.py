@@ -1,0 +1,153 @@
+"""FP64 oracle of the iterative ptychographic reconstruction that consumes the fused patterns.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy in complex128.
+
+The forward model is §3.3: exit wave psi_j = P * O_j (Eq. 2, O_j the N x N object patch whose
+top-left corner is the scan position r_j = (y_j, x_j)), far-field intensity |F psi_j|^2 (Eq. 3).
+The paper does not name its phase-retrieval algorithm (§1 cites PIE, ePIE and the difference
+map).  The reading used here is full-batch alternating projections, one iteration being:
+
+  for every position j (index order):
+      Psi_j  = F(P * O_j)                                   (Eq. 2, Eq. 3; F unitary)
+      e     += sum_q (|Psi_j| - A_j)^2                       (Fourier error, before projection)
+      Psi_j' = A_j Psi_j / |Psi_j|   (A_j where |Psi_j| = 0) (modulus constraint |F psi|^2 = I)
+      psi_j' = F^-1 Psi_j'
+  overlap projection for the object (least squares over all patches, regularised):
+      O <- sum_j conj(P) psi_j' / (sum_j |P|^2 + alpha_O max sum_j |P|^2)
+      on pixels that some patch covers (others keep their value)
+  then, with the new object and from iteration ``probe_update_start`` on:
+      P <- sum_j conj(O_j) psi_j' / (sum_j |O_j|^2 + alpha_P max sum_j |O_j|^2)
+  reported error: e / sum_j sum_q A_j^2
+
+A_j = sqrt(max(I_MNF_j, 0)) with the detector's centred DC moved to index 0 (the fused
+pattern is DC-centred; F puts DC at index 0).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def fft2u(x: np.ndarray) -> np.ndarray:
+    """Unitary 2-D DFT over the last two axes, exp(-2 pi i k n / N) kernel, DC at index 0."""
+    return np.fft.fft2(x, norm="ortho")
+
+
+def ifft2u(x: np.ndarray) -> np.ndarray:
+    """Inverse of ``fft2u``."""
+    return np.fft.ifft2(x, norm="ortho")
+
+
+def amplitudes(fused: np.ndarray) -> np.ndarray:
+    """A = sqrt(max(I, 0)), DC moved from the array centre to index 0 (ifftshift)."""
+    a = np.sqrt(np.maximum(np.asarray(fused, dtype=np.float64), 0.0))
+    return np.fft.ifftshift(a, axes=(-2, -1))
+
+
+def modulus_projection(Psi: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Replace |Psi| by A, keep the phase; where Psi = 0 the result is A (zero phase)."""
+    mag = np.abs(Psi)
+    nz = mag > 0
+    return np.where(nz, A * Psi / np.where(nz, mag, 1.0), A + 0j)
+
+
+def fourier_error(Psi: np.ndarray, A: np.ndarray) -> float:
+    return float(np.sum((np.abs(Psi) - A) ** 2))
+
+
+def exit_wave_update(obj: np.ndarray, probe: np.ndarray, pos, A_j: np.ndarray):
+    """One position: psi' = F^-1 proj(F(P * O_j)) and the position's Fourier error."""
+    N = probe.shape[0]
+    y, x = int(pos[0]), int(pos[1])
+    psi = probe * obj[y:y + N, x:x + N]
+    Psi = fft2u(psi)
+    err = fourier_error(Psi, A_j)
+    return ifft2u(modulus_projection(Psi, A_j)), err
+
+
+def illumination(probe: np.ndarray, pos, M: int) -> np.ndarray:
+    """sum_j |P(r - r_j)|^2 over the object grid."""
+    N = probe.shape[0]
+    den = np.zeros((M, M))
+    p2 = np.abs(probe) ** 2
+    for y, x in pos:
+        den[y:y + N, x:x + N] += p2
+    return den
+
+
+def object_update(obj, probe, pos, psi_new, alpha_O: float):
+    """Overlap projection for the object: the regularised least-squares solution
+    O = sum_j conj(P) psi_j' / (sum_j |P|^2 + alpha_O max sum_j |P|^2) on covered pixels."""
+    M = obj.shape[0]
+    N = probe.shape[0]
+    num_o = np.zeros((M, M), dtype=np.complex128)
+    den_o = np.zeros((M, M))
+    pc = np.conj(probe)
+    p2 = np.abs(probe) ** 2
+    for j in range(len(pos)):
+        y, x = int(pos[j][0]), int(pos[j][1])
+        num_o[y:y + N, x:x + N] += pc * psi_new[j]
+        den_o[y:y + N, x:x + N] += p2
+    out = np.array(obj, dtype=np.complex128, copy=True)
+    cover = den_o > 0
+    out[cover] = num_o[cover] / (den_o[cover] + alpha_O * den_o.max())
+    return out
+
+
+def probe_update(obj, probe, pos, psi_new, alpha_P: float):
+    """Least-squares probe from the (already updated) object:
+    P = sum_j conj(O_j) psi_j' / (sum_j |O_j|^2 + alpha_P max sum_j |O_j|^2)."""
+    N = probe.shape[0]
+    num_p = np.zeros((N, N), dtype=np.complex128)
+    den_p = np.zeros((N, N))
+    for j in range(len(pos)):
+        y, x = int(pos[j][0]), int(pos[j][1])
+        oj = obj[y:y + N, x:x + N]
+        num_p += np.conj(oj) * psi_new[j]
+        den_p += np.abs(oj) ** 2
+    out = np.array(probe, dtype=np.complex128, copy=True)
+    ok = den_p > 0
+    out[ok] = num_p[ok] / (den_p[ok] + alpha_P * den_p.max())
+    return out
+
+
+def iterate_once(obj, probe, pos, A, alpha_O, alpha_P, update_probe: bool):
+    """One full-batch iteration (see the module docstring).  Returns (obj, probe, error)."""
+    N = probe.shape[0]
+    J = len(pos)
+    psi_new = np.empty((J, N, N), dtype=np.complex128)
+    err = 0.0
+    for j in range(J):
+        psi_new[j], e = exit_wave_update(obj, probe, pos[j], A[j])
+        err += e
+    obj = object_update(obj, probe, pos, psi_new, alpha_O)
+    if update_probe:
+        probe = probe_update(obj, probe, pos, psi_new, alpha_P)
+    return obj, probe, err
+
+
+def reconstruct(fused, pos, obj0, probe0, n_iter: int, alpha_O: float = 1e-3,
+                alpha_P: float = 1e-3, probe_update_start: int = 0, A=None):
+    """Run ``n_iter`` iterations from (obj0, probe0).  Returns (obj, probe, errors[n_iter])
+    with errors normalised by sum_j sum_q A_j^2."""
+    if A is None:
+        A = amplitudes(fused)
+    obj = np.asarray(obj0, dtype=np.complex128).copy()
+    probe = np.asarray(probe0, dtype=np.complex128).copy()
+    pos = np.asarray(pos)
+    norm = float(np.sum(A * A))
+    errs = np.empty(n_iter)
+    for it in range(n_iter):
+        obj, probe, e = iterate_once(obj, probe, pos, A, alpha_O, alpha_P,
+                                     it >= probe_update_start)
+        errs[it] = e / norm if norm > 0 else 0.0
+    return obj, probe, errs
+
+
+def nrmse(obj: np.ndarray, truth: np.ndarray, mask: np.ndarray) -> float:
+    """min over complex c of ||c O - O_true|| / ||O_true|| on ``mask`` (removes the global
+    phase and scale that far-field data cannot fix)."""
+    o = obj[mask]
+    t = truth[mask]
+    denom = np.vdot(o, o)
+    c = np.vdot(o, t) / denom if abs(denom) > 0 else 0.0
+    return float(np.linalg.norm(c * o - t) / np.linalg.norm(t))
