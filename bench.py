@@ -1,0 +1,346 @@
+"""Benchmark of the whole hot path: MNF fusion of every position's exposure bracket followed by
+the iterative reconstruction, on the lab-scale workload (1024^2 object, 256^2 probe, 1600
+Fermat-spiral positions, 5 exposures, 6 pyramid levels, 200 iterations), synthetic data.
+
+One step = fuse_stack over all positions + ptycho_init + ptycho_iterate(200) + ptycho_destroy.
+The metric is position-updates per second (one update = one position through patch extraction,
+FFT, modulus replacement, inverse FFT and the object/probe updates, in one iteration); fusion
+and set-up time count against it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (it is the only reference that exists: the paper publishes no code or timings).
+Under torchrun each rank reconstructs its own independent scan (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "position-updates/s"
+WORKLOAD = "lab"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="override the iteration count (profiling runs only; not a bench value)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = [s for s in sm if s >= 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(hi), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def fuse_launches(levels: int) -> int:
+    # reduce0 + (L-2) reduces + base + (L-1) collapses; L = 1: base only
+    return 1 if levels == 1 else 2 * levels - 1
+
+
+def exit_wave_bytes_per_position(N: int) -> int:
+    """Algorithmic bytes of one position through the exit-wave kernel: amplitudes A_j (4 N^2),
+    object patch (8 N^2) and probe (8 N^2) read, psi_j' (8 N^2) written."""
+    return 28 * N * N
+
+
+def exit_wave_flops_per_position(N: int) -> float:
+    """Two unitary 2-D FFTs (5 n log2 n each, n = N^2) and ~60 flops per pixel of patch product,
+    modulus replacement and error."""
+    n = N * N
+    return 2 * 5.0 * n * np.log2(n) + 60.0 * n
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2608_01746_b300 import api, synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CONFIGS[WORKLOAD]
+    n_iter = args.iters or cfg.n_iter
+    sc = synth.make_scan_torch(cfg, seed=synth.seed_for(WORKLOAD) + 7919 * rank, device=dev)
+    raw = sc["raw"]
+    J, K, N = raw.shape[0], cfg.K, cfg.N
+    M = cfg.M
+    params = api.fuse_params(levels=cfg.levels, clip=float(cfg.clip))
+    obj0 = torch.ones((M, M), dtype=torch.complex64, device=dev)
+    probe0 = torch.from_numpy(sc["probe"].astype(np.complex64)).to(dev)
+    pos = sc["pos"]
+    fused = torch.empty((J, N, N), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    stage_ms = np.zeros(4)
+    stage_n = np.zeros(4, dtype=np.int64)
+
+    def step(timing=False):
+        api.fuse_stack(raw, cfg.times, params, out=fused, stream=stream)
+        h = api.ptycho_init(fused, pos, obj0, probe0, stream=stream)
+        if timing:
+            api.ptycho_set_timing(h, True)
+        api.ptycho_iterate(h, n_iter, errors=False)
+        if timing:
+            ms, n = api.ptycho_stage_times(h)
+            stage_ms[:] += ms
+            stage_n[:] += n
+        api.ptycho_destroy(h)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(timing=True)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    updates = J * n_iter * args.steps * world
+    value = updates / (ms_total / 1e3)
+
+    # end to end through the same calls with host buffers: H2D of the raw stack, object and
+    # probe each step, D2H of the reconstructed object and probe
+    e2e = None
+    if not args.no_e2e:
+        raw_h = raw.cpu().pin_memory()
+        obj_h = np.ones((M, M), np.complex64)
+        probe_h = sc["probe"].astype(np.complex64)
+        out_o = np.empty((M, M), np.complex64)
+        out_p = np.empty((N, N), np.complex64)
+        raw_d = torch.empty_like(raw)
+
+        def e2e_step():
+            raw_d.copy_(raw_h, non_blocking=True)
+            api.fuse_stack(raw_d, cfg.times, params, out=fused, stream=stream)
+            h = api.ptycho_init(fused, pos, obj_h, probe_h, stream=stream)
+            api.ptycho_iterate(h, n_iter, errors=False)
+            api.ptycho_get_object(h, out_o)
+            api.ptycho_get_probe(h, out_p)
+            api.ptycho_destroy(h)
+
+        e2e_step()
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e2e_s = time.perf_counter() - w0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": updates / e2e_s, "unit": METRIC,
+               "h2d_bytes_per_step": int(raw_h.numel() * 2 + obj_h.nbytes + probe_h.nbytes + pos.nbytes),
+               "d2h_bytes_per_step": int(out_o.nbytes + out_p.nbytes)}
+
+    # roofline of the dominant kernel (exit-wave), from the per-stage CUDA events of the timed
+    # steps (recorded on the library's stream)
+    hbm_peak, peak_kind = peaks()
+    dom = int(np.argmax(stage_ms))
+    names = ["k_exit_wave", "object update (k_object_gather + k_apply)",
+             "probe update (k_probe_partial + k_probe_reduce + k_apply)", "k_error_reduce"]
+    exit_ms = stage_ms[0] / max(stage_n[0], 1)
+    achieved = exit_wave_bytes_per_position(N) * J / (exit_ms / 1e3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "exit_wave_lab_traffic.json")
+    if os.path.exists(tp):
+        traffic = json.load(open(tp)).get("bytes_per_launch")
+    roof = {"kernel": "k_exit_wave", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+            "peak_kind": peak_kind, "traffic": traffic, "avg_launch_ms": round(exit_ms, 4),
+            "flop_rate_tflops": round(exit_wave_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12, 2)}
+    fuse_n = fuse_launches(cfg.levels)
+    launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Fermat-spiral scan, Poisson counts, 16-bit clip)",
+        "config": {"workload": "lab-scale MNF + reconstruction: object 1024x1024 c64, probe 256x256, "
+                               "1600 positions, 5 exposures (1/4/16/64/256), 6-level pyramid, "
+                               f"{n_iter} iterations per step",
+                   "positions": J, "exposures": K, "detector": N, "object": M, "levels": cfg.levels,
+                   "iterations": n_iter, "l2": "inputs larger than L2 (raw stack 1.05 GB per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "stage_ms_per_step": {n: round(float(m) / args.steps, 3) for n, m in zip(names, stage_ms)},
+        "dominant_stage": names[dom],
+        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(n_fuse: int = 8):
+    """Time the FP64 oracle on a bounded sample of the lab workload: fuse ``n_fuse`` positions
+    (the share of one iteration when fusion of all J positions is amortised over 200 iterations)
+    and one full-batch iteration over all 1600 positions.  Returns (seconds, position-updates)."""
+    import oracle
+    from paper_2608_01746_b300 import synth
+
+    cfg = synth.CONFIGS[WORKLOAD]
+    sel = list(range(n_fuse))
+    sc = synth.make_scan(cfg, frames_for=sel)
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    A = oracle.amplitudes(sc["intensity"])     # fusing all 1600 positions in FP64 takes ~15 min
+    obj = np.ones((cfg.M, cfg.M), complex)
+    t0 = time.perf_counter()
+    for j in range(n_fuse):
+        oracle.mnf_position(sc["raw"][j], sc["times"], p)
+    oracle.iterate_once(obj, sc["probe"], sc["pos"], A, 1e-3, 1e-3, True)
+    dt = time.perf_counter() - t0
+    return dt, len(sc["pos"])
+
+
+def cpu_baseline():
+    dt, upd = oracle_sample()
+    return {"value": round(upd / dt, 2), "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle: fusion of 8 positions + one full-batch iteration over all "
+                      "1600 positions of the lab scan (numpy FFT, single thread)",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(n_fuse=1)
+    total = 0.0
+    upd = 0
+    for _ in range(args.steps):
+        dt, u = oracle_sample()
+        total += dt
+        upd += u
+    value = upd / total
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lab-scale sample: fuse 8 positions + 1 iteration over 1600 positions "
+                                   "(object 1024x1024, probe 256x256, 5 exposures, 6 levels)"},
+            "cpu_baseline": {"value": round(value, 2), "kind": "oracle", "cores": 1,
+                             "sample": "per step: fusion of 8 positions + one full-batch iteration"},
+            "e2e": {"value": round(value, 2), "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,139 @@
+/*
+ * ptycho_mnf.h -- C ABI of the B300 (sm_103a) library for Multi-Scale Non-Linear Fusion of
+ * multi-exposure diffraction stacks and the iterative ptychographic reconstruction that
+ * consumes the fused patterns.
+ *
+ * Conventions shared by every entry point
+ *   - Every int-returning call returns PTYCHO_OK (0) or a negative PTYCHO_E* code; the message
+ *     of the last failure on the calling host thread is ptycho_last_error() (library-owned,
+ *     valid until the next failing call on that thread).
+ *   - Invalid arguments are rejected before any device work or allocation (PTYCHO_EINVAL).
+ *   - "device" pointers are CUDA device addresses on the current device; "host" pointers are
+ *     ordinary host memory.  Caller-owned buffers stay caller-owned; the library never frees
+ *     them and never keeps them past the call (it copies what it needs).
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  All device work of a call
+ *     is enqueued on that stream; calls return without waiting unless stated otherwise.
+ *   - Complex numbers are interleaved (re, im) float32 pairs ("complex64"), row-major arrays.
+ *   - Detector patterns are stored with their DC term at the array centre (index N/2, N/2).
+ */
+#ifndef PTYCHO_MNF_H
+#define PTYCHO_MNF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PTYCHO_OK = 0,
+    PTYCHO_EINVAL = -1,     /* bad argument (sizes, ranges, NULL pointers) */
+    PTYCHO_ENOMEM = -2,     /* a device allocation failed */
+    PTYCHO_ECUDA = -3,      /* a CUDA call failed; the CUDA error string is in the message */
+    PTYCHO_ENONFINITE = -4, /* the reconstruction error became NaN or Inf */
+    PTYCHO_ETIMEDOUT = -5   /* a bounded device wait gave up */
+};
+
+/* Base layer of the per-exposure collapse (§3.4.4): the paper propagates the base from the
+ * Gaussian pyramid without weight modulation.  MEAN = G_{L-1}[E_k] / K (default), SUM =
+ * G_{L-1}[E_k] (Eq. 10 literally), WEIGHTED = G_{L-1}[W_k] * G_{L-1}[E_k]. */
+enum { PTYCHO_BASE_MEAN = 0, PTYCHO_BASE_SUM = 1, PTYCHO_BASE_WEIGHTED = 2 };
+
+/* Pyramid input domain: RADIANCE = I_k * t_max / t_k (default), RAW = I_k as recorded. */
+enum { PTYCHO_DOMAIN_RADIANCE = 0, PTYCHO_DOMAIN_RAW = 1 };
+
+typedef struct {
+    float mu;          /* centre of the exposure-quality curve, Eq. 5 (default 0.5)        */
+    float sigma;       /* width of the exposure-quality curve, Eq. 5 (default 0.2), > 0     */
+    int levels;        /* pyramid levels L (§3.4.2), >= 1, with N / 2^(L-1) >= 4            */
+    float delta0;      /* quantiser step of the finest level, Eq. 8; 0 disables quantising */
+    float delta_ratio; /* Delta_l = delta0 * delta_ratio^l (l = 0 finest), > 0             */
+    float clip;        /* detector full scale in counts; Ibar = min(I, clip) / clip, > 0    */
+    int base_mode;     /* PTYCHO_BASE_*                                                     */
+    int domain;        /* PTYCHO_DOMAIN_*                                                   */
+} fuse_params;
+
+/*
+ * fuse_stack -- Multi-Scale Non-Linear Fusion of every position's exposure bracket
+ * (§3.4: Eq. 5 weights normalised to sum 1, Eq. 6 Gaussian and Eq. 7 Laplacian pyramids,
+ * modulation and Eq. 8 quantisation, Eq. 9 per-exposure collapse, Eq. 10 sum over k).
+ *
+ *   d_raw    device, uint16 counts [J][K][N][N] (the bracket S_j of Eq. 1), read-only
+ *   J        positions, >= 0 (0 is a no-op)
+ *   K        exposures per position, 1 <= K <= 8
+ *   N        detector side, a power of two, 8 <= N <= 1024
+ *   h_t      host, [K] exposure times t_k > 0 (only their ratios matter)
+ *   p        host, fusion parameters (see fuse_params)
+ *   d_fused  device, float32 [J][N][N] output I_MNF (DC-centred like the input), caller-owned
+ *   cuda_stream  stream for all work
+ * Scratch: the call takes stream-ordered device scratch (about 4 (2K + 1) N^2 / 3 bytes per
+ * position) and releases it on the same stream.  Returns PTYCHO_EINVAL for bad sizes or
+ * parameters, PTYCHO_ENOMEM / PTYCHO_ECUDA on device failures.  Asynchronous.
+ */
+int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
+               const fuse_params *p, float *d_fused, void *cuda_stream);
+
+typedef struct ptycho_ctx *ptycho_handle;
+
+typedef struct {
+    int M;                  /* object side (M x M complex64), M >= N                          */
+    int N;                  /* probe / detector side: 16, 64 or 256                           */
+    int J;                  /* scan positions, >= 1                                           */
+    const int32_t *h_pos;   /* host [J][2] (y, x) top-left patch corner, 0 <= y, x <= M - N   */
+    const float *d_fused;   /* device [J][N][N] fused intensities, DC-centred (fuse_stack's
+                               output); A = sqrt(max(I, 0)) is formed once here              */
+    const void *obj0;       /* complex64 [M][M] initial object                                */
+    const void *probe0;     /* complex64 [N][N] initial probe                                 */
+    int init_on_device;     /* 1: obj0 / probe0 are device pointers, 0: host pointers         */
+    float alpha_O;          /* object regulariser relative to max sum_j |P|^2 (>= 0)          */
+    float alpha_P;          /* probe regulariser relative to max sum_j |O_j|^2 (>= 0)         */
+    int probe_update_start; /* first iteration (counted from init) that updates the probe     */
+    void *cuda_stream;      /* stream for all work of this handle                             */
+} ptycho_desc;
+
+/*
+ * ptycho_init -- set up a reconstruction (§3.3 forward model, Eqs. 2-3).  Copies positions,
+ * fused intensities (as amplitudes with DC moved to index 0), initial object and probe into
+ * handle-owned device memory; the caller may free its inputs when the call returns.  Builds
+ * the per-tile position lists of the object update on the host.  Synchronises the stream.
+ * Returns PTYCHO_EINVAL (sizes, N unsupported, position out of range, NULL pointers),
+ * PTYCHO_ENOMEM, PTYCHO_ECUDA.  *out is NULL on failure.
+ */
+int ptycho_init(ptycho_handle *out, const ptycho_desc *d);
+
+/*
+ * ptycho_iterate -- run n_iter >= 0 iterations of full-batch alternating projections:
+ * per position psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] (Eqs. 2-3 and the modulus
+ * constraint), then the least-squares object update from all psi_j', then (from iteration
+ * probe_update_start on) the least-squares probe update from the new object.
+ *   h_err  host [n_iter] or NULL: per-iteration Fourier error
+ *          sum_j sum_q (|Psi_j| - A_j)^2 / sum_j sum_q A_j^2 measured before each projection.
+ * With h_err the call synchronises and returns PTYCHO_ENONFINITE if any error is NaN/Inf;
+ * without it the call is asynchronous.
+ */
+int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err);
+
+/* Copy the current object (complex64 [M][M]) / probe (complex64 [N][N]) into dst, a device
+ * pointer if dst_on_device else a host pointer.  A host copy synchronises the stream. */
+int ptycho_get_object(ptycho_handle h, void *dst, int dst_on_device);
+int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device);
+
+/* Release every device resource of the handle (waits for its stream).  NULL is a no-op. */
+void ptycho_destroy(ptycho_handle h);
+
+/* Per-stage device timing with CUDA events on the handle's stream (for measurement only).
+ * While enabled, ptycho_iterate records events around each stage and synchronises at its end.
+ * Stages: 0 exit-wave kernel (patch, FFT, modulus, inverse FFT), 1 object update,
+ * 2 probe update, 3 error reduction.  ms[s] is the summed device time of stage s and
+ * launches[s] the number of kernel launches it made since timing was (re-)enabled. */
+int ptycho_set_timing(ptycho_handle h, int enable);
+int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches /*[4]*/);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *ptycho_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTYCHO_MNF_H */

@@ -14,7 +14,7 @@ map).  The reading used here is full-batch alternating projections, one iteratio
       psi_j' = F^-1 Psi_j'
   overlap projection for the object (least squares over all patches, regularised):
       O <- sum_j conj(P) psi_j' / (sum_j |P|^2 + alpha_O max sum_j |P|^2)
-      on pixels that some patch covers (others keep their value)
+      on pixels inside some scan patch (others keep their value)
   then, with the new object and from iteration ``probe_update_start`` on:
       P <- sum_j conj(O_j) psi_j' / (sum_j |O_j|^2 + alpha_P max sum_j |O_j|^2)
   reported error: e / sum_j sum_q A_j^2
@@ -76,7 +76,11 @@ def illumination(probe: np.ndarray, pos, M: int) -> np.ndarray:
 
 def object_update(obj, probe, pos, psi_new, alpha_O: float):
     """Overlap projection for the object: the regularised least-squares solution
-    O = sum_j conj(P) psi_j' / (sum_j |P|^2 + alpha_O max sum_j |P|^2) on covered pixels."""
+    O = sum_j conj(P) psi_j' / (sum_j |P|^2 + alpha_O max sum_j |P|^2) on every pixel that lies
+    inside some scan patch (others keep their value; so does a patch pixel whose denominator is
+    exactly zero, which needs alpha_O = 0).  Coverage is decided by the scan footprint, not by
+    the value of sum_j |P|^2, so the decision does not depend on the precision of |P|^2 where
+    the probe amplitude underflows."""
     M = obj.shape[0]
     N = probe.shape[0]
     num_o = np.zeros((M, M), dtype=np.complex128)
@@ -87,9 +91,14 @@ def object_update(obj, probe, pos, psi_new, alpha_O: float):
         y, x = int(pos[j][0]), int(pos[j][1])
         num_o[y:y + N, x:x + N] += pc * psi_new[j]
         den_o[y:y + N, x:x + N] += p2
+    cover = np.zeros((M, M), dtype=bool)          # pixels inside some scan patch
+    for j in range(len(pos)):
+        y, x = int(pos[j][0]), int(pos[j][1])
+        cover[y:y + N, x:x + N] = True
+    reg = alpha_O * den_o.max()
+    upd = cover & (den_o + reg > 0)
     out = np.array(obj, dtype=np.complex128, copy=True)
-    cover = den_o > 0
-    out[cover] = num_o[cover] / (den_o[cover] + alpha_O * den_o.max())
+    out[upd] = num_o[upd] / (den_o[upd] + reg)
     return out
 
 
@@ -104,9 +113,10 @@ def probe_update(obj, probe, pos, psi_new, alpha_P: float):
         oj = obj[y:y + N, x:x + N]
         num_p += np.conj(oj) * psi_new[j]
         den_p += np.abs(oj) ** 2
+    reg = alpha_P * den_p.max()
+    upd = den_p + reg > 0                          # every probe pixel lies in every patch
     out = np.array(probe, dtype=np.complex128, copy=True)
-    ok = den_p > 0
-    out[ok] = num_p[ok] / (den_p[ok] + alpha_P * den_p.max())
+    out[upd] = num_p[upd] / (den_p[upd] + reg)
     return out
 
 

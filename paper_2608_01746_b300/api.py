@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in ``include/ptycho_mnf.h`` (argument marshalling only).
+
+Every function keeps the C name and forwards to ``libptycho_mnf.so``; all arithmetic runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device memory
+and streams), host buffers are numpy arrays.  Loading fails loudly if the library is missing:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PTYCHO_OK = 0
+PTYCHO_EINVAL = -1
+PTYCHO_ENOMEM = -2
+PTYCHO_ECUDA = -3
+PTYCHO_ENONFINITE = -4
+PTYCHO_ETIMEDOUT = -5
+
+BASE_MODES = {"mean": 0, "sum": 1, "weighted": 2}
+DOMAINS = {"radiance": 0, "raw": 1}
+
+EXPORTS = ("fuse_stack", "ptycho_init", "ptycho_iterate", "ptycho_get_object", "ptycho_get_probe",
+           "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
+
+
+class FuseParamsC(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_float), ("sigma", ctypes.c_float), ("levels", ctypes.c_int),
+                ("delta0", ctypes.c_float), ("delta_ratio", ctypes.c_float),
+                ("clip", ctypes.c_float), ("base_mode", ctypes.c_int), ("domain", ctypes.c_int)]
+
+
+class PtychoDescC(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("J", ctypes.c_int),
+                ("h_pos", ctypes.c_void_p), ("d_fused", ctypes.c_void_p),
+                ("obj0", ctypes.c_void_p), ("probe0", ctypes.c_void_p),
+                ("init_on_device", ctypes.c_int), ("alpha_O", ctypes.c_float),
+                ("alpha_P", ctypes.c_float), ("probe_update_start", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class PtychoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libptycho_mnf.so`` (built in-tree by ``__graft_entry__.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.fuse_stack.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float),
+                             ctypes.POINTER(FuseParamsC), vp, vp]
+    L.fuse_stack.restype = ci
+    L.ptycho_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PtychoDescC)]
+    L.ptycho_init.restype = ci
+    L.ptycho_iterate.argtypes = [vp, ci, ctypes.POINTER(cd)]
+    L.ptycho_iterate.restype = ci
+    L.ptycho_get_object.argtypes = [vp, vp, ci]
+    L.ptycho_get_object.restype = ci
+    L.ptycho_get_probe.argtypes = [vp, vp, ci]
+    L.ptycho_get_probe.restype = ci
+    L.ptycho_destroy.argtypes = [vp]
+    L.ptycho_destroy.restype = None
+    L.ptycho_set_timing.argtypes = [vp, ci]
+    L.ptycho_set_timing.restype = ci
+    L.ptycho_stage_times.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_longlong)]
+    L.ptycho_stage_times.restype = ci
+    L.ptycho_last_error.argtypes = []
+    L.ptycho_last_error.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def last_error() -> str:
+    return lib().ptycho_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != PTYCHO_OK:
+        raise PtychoError(rc, last_error())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def fuse_params(levels: int, clip: float, mu: float = 0.5, sigma: float = 0.2,
+                delta0: float = 0.5, delta_ratio: float = 2.0, base_mode: str = "mean",
+                domain: str = "radiance") -> FuseParamsC:
+    return FuseParamsC(mu, sigma, levels, delta0, delta_ratio, clip, BASE_MODES[base_mode],
+                       DOMAINS[domain])
+
+
+def fuse_stack(raw, times, params: FuseParamsC, out=None, stream=None):
+    """MNF of raw[J][K][N][N] (torch.uint16 CUDA tensor) into out[J][N][N] (float32 CUDA)."""
+    import torch
+    if raw.dtype != torch.uint16 or not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw must be a contiguous torch.uint16 CUDA tensor [J][K][N][N]")
+    J, K, N, N2 = raw.shape
+    if N != N2:
+        raise ValueError("frames must be square")
+    if out is None:
+        out = torch.empty((J, N, N), dtype=torch.float32, device=raw.device)
+    if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (J, N, N):
+        raise ValueError("out must be a contiguous float32 tensor [J][N][N]")
+    t = (ctypes.c_float * K)(*[float(x) for x in times])
+    _check(lib().fuse_stack(ctypes.c_void_p(raw.data_ptr()), J, K, N, t, ctypes.byref(params),
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+class PtychoHandle:
+    """Owner of a ``ptycho_handle``; ``close()`` (or garbage collection) destroys it."""
+
+    def __init__(self, ptr: int, M: int, N: int, J: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.M, self.N, self.J = M, N, J
+
+    def close(self) -> None:
+        if self.ptr:
+            lib().ptycho_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float = 1e-3,
+                probe_update_start: int = 0, stream=None) -> PtychoHandle:
+    """fused: float32 CUDA tensor [J][N][N]; pos: int [J][2] (y, x); obj0 / probe0: complex64,
+    both numpy (host) or both torch CUDA tensors (device)."""
+    import torch
+    if fused.dtype != torch.float32 or not fused.is_cuda or not fused.is_contiguous():
+        raise ValueError("fused must be a contiguous float32 CUDA tensor [J][N][N]")
+    J, N, _ = fused.shape
+    pos = np.ascontiguousarray(pos, dtype=np.int32)
+    if pos.shape != (J, 2):
+        raise ValueError("pos must be [J][2]")
+    on_dev = isinstance(obj0, torch.Tensor)
+    if on_dev:
+        if not (isinstance(probe0, torch.Tensor) and obj0.is_cuda and probe0.is_cuda):
+            raise ValueError("obj0 and probe0 must both be CUDA tensors or both numpy arrays")
+        obj0 = obj0.to(torch.complex64).contiguous()
+        probe0 = probe0.to(torch.complex64).contiguous()
+        op, pp = obj0.data_ptr(), probe0.data_ptr()
+    else:
+        obj0 = np.ascontiguousarray(obj0, dtype=np.complex64)
+        probe0 = np.ascontiguousarray(probe0, dtype=np.complex64)
+        op, pp = obj0.ctypes.data, probe0.ctypes.data
+    M = obj0.shape[0]
+    desc = PtychoDescC(M, N, J, pos.ctypes.data, fused.data_ptr(), op, pp, 1 if on_dev else 0,
+                       alpha_O, alpha_P, probe_update_start, _stream_ptr(stream))
+    h = ctypes.c_void_p()
+    _check(lib().ptycho_init(ctypes.byref(h), ctypes.byref(desc)))
+    return PtychoHandle(h.value, M, N, J)
+
+
+def ptycho_iterate(h: PtychoHandle, n_iter: int, errors: bool = True):
+    """Run n_iter iterations; returns the per-iteration errors (numpy) or None."""
+    if errors:
+        err = np.zeros(max(n_iter, 1), dtype=np.float64)
+        _check(lib().ptycho_iterate(h.ptr, n_iter, err.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return err[:n_iter]
+    _check(lib().ptycho_iterate(h.ptr, n_iter, None))
+    return None
+
+
+def _get(fn, h: PtychoHandle, shape, out):
+    if out is None:
+        out = np.empty(shape, dtype=np.complex64)
+    import torch
+    if isinstance(out, torch.Tensor):
+        if out.dtype != torch.complex64 or not out.is_cuda or not out.is_contiguous() or tuple(out.shape) != shape:
+            raise ValueError(f"out must be a contiguous complex64 CUDA tensor {shape}")
+        _check(fn(h.ptr, ctypes.c_void_p(out.data_ptr()), 1))
+    else:
+        if out.dtype != np.complex64 or not out.flags.c_contiguous or out.shape != shape:
+            raise ValueError(f"out must be a contiguous complex64 array {shape}")
+        _check(fn(h.ptr, ctypes.c_void_p(out.ctypes.data), 0))
+    return out
+
+
+def ptycho_get_object(h: PtychoHandle, out=None):
+    return _get(lib().ptycho_get_object, h, (h.M, h.M), out)
+
+
+def ptycho_get_probe(h: PtychoHandle, out=None):
+    return _get(lib().ptycho_get_probe, h, (h.N, h.N), out)
+
+
+def ptycho_destroy(h: PtychoHandle) -> None:
+    h.close()
+
+
+def ptycho_set_timing(h: PtychoHandle, enable: bool) -> None:
+    _check(lib().ptycho_set_timing(h.ptr, 1 if enable else 0))
+
+
+def ptycho_stage_times(h: PtychoHandle):
+    """(ms[4], launches[4]) for stages exit-wave, object, probe, error."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_longlong * 4)()
+    _check(lib().ptycho_stage_times(h.ptr, ms, n))
+    return list(ms), list(n)

@@ -1,0 +1,41 @@
+// Shared host/device helpers of the CUDA library: error reporting and complex arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ptycho_mnf.h"
+
+namespace pm {
+
+// Records a printf-style message as the calling thread's last error and returns `code`.
+int fail(int code, const char *fmt, ...);
+// Records a CUDA failure ("<what>: <cuda error string>") and returns PTYCHO_ECUDA, or
+// PTYCHO_ENOMEM for cudaErrorMemoryAllocation.
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace pm
+
+#define PM_CUDA(call)                                                       \
+    do {                                                                    \
+        cudaError_t pm_e_ = (call);                                         \
+        if (pm_e_ != cudaSuccess) return pm::cuda_fail(pm_e_, #call);       \
+    } while (0)
+
+#define PM_LAUNCHED(what)                                                   \
+    do {                                                                    \
+        cudaError_t pm_e_ = cudaGetLastError();                             \
+        if (pm_e_ != cudaSuccess) return pm::cuda_fail(pm_e_, what);        \
+    } while (0)
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }

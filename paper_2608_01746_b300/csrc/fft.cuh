@@ -1,0 +1,109 @@
+// Register/shared-memory radix FFT for N = R * R points (R = 4, 8, 16) executed by a group of
+// R threads.  Thread t of a group holds the elements x[t + R m], m = 0 .. R-1, in registers
+// and, after the transform, X[t + R m] (natural order in both directions).
+//
+// Decomposition (n = n2 + R n1, k = k1 + R k2, W_N = exp(sign 2 pi i / N)):
+//   X[k1 + R k2] = sum_n2 W_R^(n2 k2) [ W_N^(n2 k1) sum_n1 x[n2 + R n1] W_R^(n1 k1) ]
+// Thread t = n2 does the inner R-point DFT in registers and the twiddle, the group exchanges
+// through a padded R x (R+1) shared-memory buffer (conflict-free for both the write and the
+// transposed read), then thread t = k1 does the outer R-point DFT in registers.
+#pragma once
+
+#include "common.cuh"
+
+namespace pm {
+
+// cos(2 pi k / 16), sin(2 pi k / 16) for k = 0 .. 7
+__device__ __forceinline__ float cos16(int k) {
+    switch (k) {
+        case 0: return 1.0f;
+        case 1: return 0.92387953251128674f;
+        case 2: return 0.70710678118654752f;
+        case 3: return 0.38268343236508977f;
+        case 4: return 0.0f;
+        case 5: return -0.38268343236508977f;
+        case 6: return -0.70710678118654752f;
+        default: return -0.92387953251128674f;
+    }
+}
+__device__ __forceinline__ float sin16(int k) {
+    switch (k) {
+        case 0: return 0.0f;
+        case 1: return 0.38268343236508977f;
+        case 2: return 0.70710678118654752f;
+        case 3: return 0.92387953251128674f;
+        case 4: return 1.0f;
+        case 5: return 0.92387953251128674f;
+        case 6: return 0.70710678118654752f;
+        default: return 0.38268343236508977f;
+    }
+}
+
+// v * exp(SIGN * 2 pi i k16 / 16) for a compile-time-foldable k16 in [0, 8).
+template <int SIGN>
+__device__ __forceinline__ float2 rot16(float2 v, int k16) {
+    if (k16 == 0) return v;
+    if (k16 == 4) return SIGN < 0 ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+    const float c = cos16(k16), s = SIGN * sin16(k16);
+    return make_float2(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// Bit reversal of i in [0, R), written out so that unrolled indices fold to constants.
+template <int R>
+__device__ __forceinline__ int bitrev(int i) {
+    if constexpr (R == 2) return i;
+    else if constexpr (R == 4) return ((i & 1) << 1) | ((i & 2) >> 1);
+    else if constexpr (R == 8) return ((i & 1) << 2) | (i & 2) | ((i & 4) >> 2);
+    else return ((i & 1) << 3) | ((i & 2) << 1) | ((i & 4) >> 1) | ((i & 8) >> 3);
+}
+
+// Radix-2 decimation-in-time butterflies of span LEN, then the next stage.
+template <int R, int SIGN, int LEN>
+__device__ __forceinline__ void dit_stage(float2 (&y)[R]) {
+#pragma unroll
+    for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+        for (int k = 0; k < LEN / 2; ++k) {
+            const float2 a = y[i + k];
+            const float2 b = rot16<SIGN>(y[i + k + LEN / 2], k * (16 / LEN));
+            y[i + k] = cadd(a, b);
+            y[i + k + LEN / 2] = csub(a, b);
+        }
+    }
+    if constexpr (LEN < R) dit_stage<R, SIGN, LEN * 2>(y);
+}
+
+// In-register R-point DFT (R in {2, 4, 8, 16}): d[k] <- sum_n d[n] exp(SIGN 2 pi i n k / R).
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&d)[R]) {
+    float2 y[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) y[i] = d[bitrev<R>(i)];
+    dit_stage<R, SIGN, 2>(y);
+#pragma unroll
+    for (int i = 0; i < R; ++i) d[i] = y[i];
+}
+
+// Group FFT of N = R*R points (see the file comment).  `xb` is the group's R*(R+1) float2
+// exchange buffer, `tw` the table W_N^(a b) (forward sign) indexed [a * R + b] (symmetric),
+// `t` the thread's rank in the group.  The caller's group is a warp-aligned run of R lanes;
+// `__syncwarp` orders the exchange.
+template <int R, int SIGN>
+__device__ __forceinline__ void fft_group(float2 (&d)[R], float2 *xb, const float2 *tw, int t) {
+    dft_reg<R, SIGN>(d);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) {
+        float2 w = tw[k1 * R + t];
+        if (SIGN > 0) w.y = -w.y;
+        d[k1] = cmul(d[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) xb[k1 * (R + 1) + t] = d[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) d[n2] = xb[t * (R + 1) + n2];
+    dft_reg<R, SIGN>(d);
+}
+
+}  // namespace pm

@@ -1,0 +1,413 @@
+// Multi-Scale Non-Linear Fusion (MNF) of multi-exposure diffraction brackets, §3.4.
+//
+// Per position j the method builds, for every exposure k, Gaussian pyramids of the radiance
+// E_k and of the normalised exposure weight W_k (Eq. 5, Eq. 6), the Laplacian pyramid of E_k
+// (Eq. 7), modulates and quantises the details (Eq. 8), collapses each exposure (Eq. 9) and
+// sums the collapsed images (Eq. 10).  Because U2 is linear, sum_k R_0^(k) equals one collapse
+// of the per-level sums sum_k Ltilde_l^(k) on top of the summed base, so the kernels below
+// accumulate over k per level and collapse once:
+//
+//   reduce0      raw counts -> (E_k, W_k) at level 0 -> G_1[E_k], G_1[W_k]  (shared-memory tile)
+//   reduce(l)    G_l -> G_{l+1} for E and W                                   (l = 1 .. L-2)
+//   base         R_{L-1} = sum_k base_k(G_{L-1}[E_k], G_{L-1}[W_k])
+//   collapse(l)  R_l = U2(R_{l+1}) + sum_k Q_l(G_l[W_k] (G_l[E_k] - U2(G_{l+1}[E_k])))
+//                (l = L-2 .. 1 into scratch, l = 0 from the raw counts into the output)
+//
+// Level-0 planes are never stored: E and W there are pointwise functions of the K raw counts.
+// Filters: w_G = [1,4,6,4,1]/16 per axis, D2 keeps even samples, U2 is zero insertion then
+// 2 w_G per axis, reflect-101 borders on the grid being filtered.  All arithmetic is FP32.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kMaxK = 8;
+constexpr int kMaxLevels = 11;
+
+struct FuseDev {
+    float mu, inv2s2, clip;
+    float tscale[kMaxK];        // E_k = I_k * tscale[k]
+    float delta[kMaxLevels];    // quantiser step per level (0 = off)
+    int N, L, base_mode;
+};
+
+__device__ __forceinline__ int refl(int i, int n) {
+    // reflect-101 for i in [-(n-1), 2n-2]
+    return i < 0 ? -i : (i >= n ? 2 * n - 2 - i : i);
+}
+
+__device__ __forceinline__ float wg(int a) {
+    // w_G = [1, 4, 6, 4, 1] / 16
+    return a == 2 ? 0.375f : ((a == 1 || a == 3) ? 0.25f : 0.0625f);
+}
+
+// Exposure weights (Eq. 5, normalised over k) and radiance of one level-0 pixel.
+template <int K>
+__device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, size_t p,
+                                             const FuseDev &f, float (&E)[K], float (&W)[K]) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float v = (float)__ldg(raw_j + k * NN + p);
+        E[k] = v * f.tscale[k];
+        const float d = fminf(v, f.clip) / f.clip - f.mu;
+        W[k] = expf(-d * d * f.inv2s2);
+        s += W[k];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) W[k] = (s > 0.f) ? W[k] / s : 1.0f / K;
+}
+
+// U2(X) at fine pixel (m1, m2) of a 2n x 2n grid, X an n x n plane.
+__device__ __forceinline__ float upsample_at(const float *X, int n, int m1, int m2) {
+    int iy[3], ix[3];
+    float wy[3], wx[3];
+    int ny, nx;
+    if (m1 & 1) { const int i = m1 >> 1; iy[0] = i; iy[1] = min(i + 1, n - 1); wy[0] = wy[1] = 0.5f; ny = 2; }
+    else { const int i = m1 >> 1; iy[0] = (i == 0) ? 1 : i - 1; iy[1] = i; iy[2] = min(i + 1, n - 1);
+           wy[0] = 0.125f; wy[1] = 0.75f; wy[2] = 0.125f; ny = 3; }
+    if (m2 & 1) { const int i = m2 >> 1; ix[0] = i; ix[1] = min(i + 1, n - 1); wx[0] = wx[1] = 0.5f; nx = 2; }
+    else { const int i = m2 >> 1; ix[0] = (i == 0) ? 1 : i - 1; ix[1] = i; ix[2] = min(i + 1, n - 1);
+           wx[0] = 0.125f; wx[1] = 0.75f; wx[2] = 0.125f; nx = 3; }
+    float acc = 0.f;
+    for (int a = 0; a < ny; ++a) {
+        float r = 0.f;
+        for (int b = 0; b < nx; ++b) r += wx[b] * __ldg(X + (size_t)iy[a] * n + ix[b]);
+        acc += wy[a] * r;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float quantise(float x, float delta) {
+    return delta > 0.f ? delta * rintf(x / delta) : x;
+}
+
+constexpr int kTile = 16;             // outputs per block side of a reduce
+constexpr int kIn = 2 * kTile + 3;    // input rows/cols a tile needs
+constexpr int kInP = kIn + 1;         // padded pitch
+
+// Level 0 -> level 1 for every exposure: blockIdx.z = position, tile of 16 x 16 outputs.
+template <int K>
+__global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ raw,
+                                                 float *__restrict__ ge1, float *__restrict__ gw1,
+                                                 FuseDev f) {
+    __shared__ float s_sum[kIn * kInP];
+    __shared__ float s_e[kIn * kInP];
+    __shared__ float s_w[kIn * kInP];
+    const int N = f.N, n1 = N >> 1;
+    const size_t NN = (size_t)N * N;
+    const int j = blockIdx.z;
+    const uint16_t *raw_j = raw + (size_t)j * K * NN;
+    const int oy0 = blockIdx.y * kTile, ox0 = blockIdx.x * kTile;
+    const int outs_y = min(kTile, n1 - oy0), outs_x = min(kTile, n1 - ox0);
+    const int rows = 2 * outs_y + 3, cols = 2 * outs_x + 3;
+    const int tid = threadIdx.x;
+    // sum_k w_k per input pixel (the normaliser of Eq. 5)
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+        const int a = e / cols, b = e % cols;
+        const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float d = fminf((float)__ldg(raw_j + k * NN + p), f.clip) / f.clip - f.mu;
+            s += expf(-d * d * f.inv2s2);
+        }
+        s_sum[a * kInP + b] = s;
+    }
+    const int ty = tid / kTile, tx = tid % kTile;
+    const size_t n1n1 = (size_t)n1 * n1;
+    for (int k = 0; k < K; ++k) {
+        __syncthreads();
+        for (int e = tid; e < rows * cols; e += blockDim.x) {
+            const int a = e / cols, b = e % cols;
+            const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
+            const float v = (float)__ldg(raw_j + k * NN + p);
+            const float d = fminf(v, f.clip) / f.clip - f.mu;
+            const float s = s_sum[a * kInP + b];
+            s_e[a * kInP + b] = v * f.tscale[k];
+            s_w[a * kInP + b] = (s > 0.f) ? expf(-d * d * f.inv2s2) / s : 1.0f / K;
+        }
+        __syncthreads();
+        if (ty < outs_y && tx < outs_x) {
+            float ae = 0.f, aw = 0.f;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                float re = 0.f, rw = 0.f;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) {
+                    re += wg(b) * s_e[(2 * ty + a) * kInP + 2 * tx + b];
+                    rw += wg(b) * s_w[(2 * ty + a) * kInP + 2 * tx + b];
+                }
+                ae += wg(a) * re;
+                aw += wg(a) * rw;
+            }
+            const size_t o = ((size_t)j * K + k) * n1n1 + (size_t)(oy0 + ty) * n1 + ox0 + tx;
+            ge1[o] = ae;
+            gw1[o] = aw;
+        }
+    }
+}
+
+// Level l -> l+1 (l >= 1) for one plane pair: blockIdx.z = j * K + k.
+__global__ void __launch_bounds__(256) k_reduce(const float *__restrict__ ge, const float *__restrict__ gw,
+                                                float *__restrict__ ge_next, float *__restrict__ gw_next,
+                                                int n) {
+    __shared__ float s_e[kIn * kInP];
+    __shared__ float s_w[kIn * kInP];
+    const int m = n >> 1;
+    const size_t plane = blockIdx.z;
+    const float *e_in = ge + plane * n * n, *w_in = gw + plane * n * n;
+    const int oy0 = blockIdx.y * kTile, ox0 = blockIdx.x * kTile;
+    const int outs_y = min(kTile, m - oy0), outs_x = min(kTile, m - ox0);
+    const int rows = 2 * outs_y + 3, cols = 2 * outs_x + 3;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+        const int a = e / cols, b = e % cols;
+        const size_t p = (size_t)refl(2 * oy0 - 2 + a, n) * n + refl(2 * ox0 - 2 + b, n);
+        s_e[a * kInP + b] = __ldg(e_in + p);
+        s_w[a * kInP + b] = __ldg(w_in + p);
+    }
+    __syncthreads();
+    const int ty = tid / kTile, tx = tid % kTile;
+    if (ty < outs_y && tx < outs_x) {
+        float ae = 0.f, aw = 0.f;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            float re = 0.f, rw = 0.f;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                re += wg(b) * s_e[(2 * ty + a) * kInP + 2 * tx + b];
+                rw += wg(b) * s_w[(2 * ty + a) * kInP + 2 * tx + b];
+            }
+            ae += wg(a) * re;
+            aw += wg(a) * rw;
+        }
+        const size_t o = plane * m * m + (size_t)(oy0 + ty) * m + ox0 + tx;
+        ge_next[o] = ae;
+        gw_next[o] = aw;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ float base_value(const float (&E)[K], const float (&W)[K], int mode) {
+    float b = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (mode == PTYCHO_BASE_WEIGHTED) b += W[k] * E[k];
+        else b += E[k];
+    }
+    return mode == PTYCHO_BASE_MEAN ? b / K : b;
+}
+
+// Base of the collapse at the coarsest level: from planes (L >= 2) or from raw (L == 1,
+// then written straight to the output).  One thread per (j, pixel).
+template <int K>
+__global__ void k_base(const float *__restrict__ ge, const float *__restrict__ gw,
+                       const uint16_t *__restrict__ raw, float *__restrict__ out, int n, int J,
+                       FuseDev f) {
+    const size_t nn = (size_t)n * n;
+    const size_t total = (size_t)J * nn;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = i / nn, p = i % nn;
+        float E[K], W[K];
+        if (raw) {
+            level0_pixel<K>(raw + j * K * nn, nn, p, f, E, W);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                E[k] = __ldg(ge + (j * K + k) * nn + p);
+                W[k] = __ldg(gw + (j * K + k) * nn + p);
+            }
+        }
+        out[i] = base_value<K>(E, W, f.base_mode);
+    }
+}
+
+// R_l = U2(R_{l+1}) + sum_k Q_l(G_l[W_k] (G_l[E_k] - U2(G_{l+1}[E_k]))); level 0 reads raw.
+template <int K>
+__global__ void k_collapse(const float *__restrict__ ge, const float *__restrict__ gw,
+                           const uint16_t *__restrict__ raw, const float *__restrict__ ge_next,
+                           const float *__restrict__ r_next, float *__restrict__ out, int n,
+                           int J, float delta, FuseDev f) {
+    const size_t nn = (size_t)n * n;
+    const int m = n >> 1;
+    const size_t mm = (size_t)m * m;
+    const size_t total = (size_t)J * nn;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = i / nn, p = i % nn;
+        const int py = (int)(p / n), px = (int)(p % n);
+        float E[K], W[K];
+        if (raw) {
+            level0_pixel<K>(raw + j * K * nn, nn, p, f, E, W);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                E[k] = __ldg(ge + (j * K + k) * nn + p);
+                W[k] = __ldg(gw + (j * K + k) * nn + p);
+            }
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float ue = upsample_at(ge_next + (j * K + k) * mm, m, py, px);
+            acc += quantise(W[k] * (E[k] - ue), delta);
+        }
+        out[i] = upsample_at(r_next + j * mm, m, py, px) + acc;
+    }
+}
+
+unsigned grid_for(size_t total, int threads) {
+    size_t b = (total + threads - 1) / threads;
+    return (unsigned)std::min<size_t>(std::max<size_t>(b, 1), 148u * 64u);
+}
+
+template <int K>
+int run_fuse(const uint16_t *d_raw, int J, int N, const FuseDev &f, float *d_fused,
+             float *scratch, cudaStream_t st) {
+    const int L = f.L;
+    if (L == 1) {
+        const size_t total = (size_t)J * N * N;
+        k_base<K><<<grid_for(total, 256), 256, 0, st>>>(nullptr, nullptr, d_raw, d_fused, N, J, f);
+        PM_LAUNCHED("k_base");
+        return PTYCHO_OK;
+    }
+    // scratch layout per level l >= 1: GE_l [J][K][n_l^2], GW_l [J][K][n_l^2], R_l [J][n_l^2]
+    float *ge[kMaxLevels] = {}, *gw[kMaxLevels] = {}, *rr[kMaxLevels] = {};
+    float *cur = scratch;
+    for (int l = 1; l < L; ++l) {
+        const size_t nl2 = (size_t)(N >> l) * (N >> l);
+        ge[l] = cur; cur += (size_t)J * K * nl2;
+        gw[l] = cur; cur += (size_t)J * K * nl2;
+        rr[l] = cur; cur += (size_t)J * nl2;
+    }
+    {
+        const int n1 = N >> 1;
+        dim3 grid((n1 + kTile - 1) / kTile, (n1 + kTile - 1) / kTile, J);
+        k_reduce0<K><<<grid, 256, 0, st>>>(d_raw, ge[1], gw[1], f);
+        PM_LAUNCHED("k_reduce0");
+    }
+    for (int l = 1; l + 1 < L; ++l) {
+        const int n = N >> l, m = n >> 1;
+        dim3 grid((m + kTile - 1) / kTile, (m + kTile - 1) / kTile, J * K);
+        k_reduce<<<grid, 256, 0, st>>>(ge[l], gw[l], ge[l + 1], gw[l + 1], n);
+        PM_LAUNCHED("k_reduce");
+    }
+    {
+        const int n = N >> (L - 1);
+        const size_t total = (size_t)J * n * n;
+        k_base<K><<<grid_for(total, 256), 256, 0, st>>>(ge[L - 1], gw[L - 1], nullptr, rr[L - 1], n, J, f);
+        PM_LAUNCHED("k_base");
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const int n = N >> l;
+        const size_t total = (size_t)J * n * n;
+        if (l == 0) {
+            k_collapse<K><<<grid_for(total, 256), 256, 0, st>>>(nullptr, nullptr, d_raw, ge[1], rr[1],
+                                                                d_fused, n, J, f.delta[0], f);
+        } else {
+            k_collapse<K><<<grid_for(total, 256), 256, 0, st>>>(ge[l], gw[l], nullptr, ge[l + 1], rr[l + 1],
+                                                                rr[l], n, J, f.delta[l], f);
+        }
+        PM_LAUNCHED("k_collapse");
+    }
+    return PTYCHO_OK;
+}
+
+size_t scratch_floats_per_position(int K, int N, int L) {
+    size_t s = 0;
+    for (int l = 1; l < L; ++l) s += (size_t)(2 * K + 1) * (N >> l) * (N >> l);
+    return s;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+namespace pm {
+
+int validate_fuse(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                  const fuse_params *p, float *d_fused, FuseDev *out) {
+    if (!p) return fail(PTYCHO_EINVAL, "fuse_stack: params is NULL");
+    if (J < 0) return fail(PTYCHO_EINVAL, "fuse_stack: J = %d < 0", J);
+    if (K < 1 || K > kMaxK) return fail(PTYCHO_EINVAL, "fuse_stack: K = %d not in [1, %d]", K, kMaxK);
+    if (!is_pow2(N) || N < 8 || N > 1024)
+        return fail(PTYCHO_EINVAL, "fuse_stack: N = %d is not a power of two in [8, 1024]", N);
+    if (p->levels < 1 || p->levels > kMaxLevels || (N >> (p->levels - 1)) < 4)
+        return fail(PTYCHO_EINVAL, "fuse_stack: levels = %d needs N / 2^(L-1) >= 4 (N = %d)", p->levels, N);
+    if (!(p->sigma > 0.f) || !std::isfinite(p->sigma) || !std::isfinite(p->mu))
+        return fail(PTYCHO_EINVAL, "fuse_stack: sigma must be finite and > 0, mu finite");
+    if (!(p->clip > 0.f) || !std::isfinite(p->clip)) return fail(PTYCHO_EINVAL, "fuse_stack: clip must be finite and > 0");
+    if (!(p->delta0 >= 0.f) || !std::isfinite(p->delta0) || !(p->delta_ratio > 0.f) || !std::isfinite(p->delta_ratio))
+        return fail(PTYCHO_EINVAL, "fuse_stack: delta0 >= 0 and delta_ratio > 0 required");
+    if (p->base_mode < PTYCHO_BASE_MEAN || p->base_mode > PTYCHO_BASE_WEIGHTED)
+        return fail(PTYCHO_EINVAL, "fuse_stack: unknown base_mode %d", p->base_mode);
+    if (p->domain != PTYCHO_DOMAIN_RADIANCE && p->domain != PTYCHO_DOMAIN_RAW)
+        return fail(PTYCHO_EINVAL, "fuse_stack: unknown domain %d", p->domain);
+    if (!h_t) return fail(PTYCHO_EINVAL, "fuse_stack: exposure times pointer is NULL");
+    float tmax = 0.f;
+    for (int k = 0; k < K; ++k) {
+        if (!(h_t[k] > 0.f) || !std::isfinite(h_t[k]))
+            return fail(PTYCHO_EINVAL, "fuse_stack: t[%d] = %g must be finite and > 0", k, (double)h_t[k]);
+        tmax = std::max(tmax, h_t[k]);
+    }
+    if (J > 0 && (!d_raw || !d_fused)) return fail(PTYCHO_EINVAL, "fuse_stack: NULL raw or output pointer");
+    FuseDev f{};
+    f.mu = p->mu;
+    f.inv2s2 = (float)(1.0 / (2.0 * (double)p->sigma * (double)p->sigma));
+    f.clip = p->clip;
+    for (int k = 0; k < K; ++k)
+        f.tscale[k] = (p->domain == PTYCHO_DOMAIN_RAW) ? 1.0f : (float)((double)tmax / (double)h_t[k]);
+    for (int l = 0; l < kMaxLevels; ++l)
+        f.delta[l] = (float)((double)p->delta0 * std::pow((double)p->delta_ratio, (double)l));
+    f.N = N;
+    f.L = p->levels;
+    f.base_mode = p->base_mode;
+    *out = f;
+    return PTYCHO_OK;
+}
+
+int fuse_dispatch(const uint16_t *d_raw, int J, int K, int N, const FuseDev &f, float *d_fused,
+                  float *scratch, cudaStream_t st) {
+    switch (K) {
+        case 1: return run_fuse<1>(d_raw, J, N, f, d_fused, scratch, st);
+        case 2: return run_fuse<2>(d_raw, J, N, f, d_fused, scratch, st);
+        case 3: return run_fuse<3>(d_raw, J, N, f, d_fused, scratch, st);
+        case 4: return run_fuse<4>(d_raw, J, N, f, d_fused, scratch, st);
+        case 5: return run_fuse<5>(d_raw, J, N, f, d_fused, scratch, st);
+        case 6: return run_fuse<6>(d_raw, J, N, f, d_fused, scratch, st);
+        case 7: return run_fuse<7>(d_raw, J, N, f, d_fused, scratch, st);
+        default: return run_fuse<8>(d_raw, J, N, f, d_fused, scratch, st);
+    }
+}
+
+}  // namespace pm
+
+extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                          const fuse_params *p, float *d_fused, void *cuda_stream) {
+    FuseDev f;
+    int rc = pm::validate_fuse(d_raw, J, K, N, h_t, p, d_fused, &f);
+    if (rc != PTYCHO_OK || J == 0) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t per_pos = scratch_floats_per_position(K, N, f.L);
+    // Positions are independent: process them in chunks whose scratch stays below 2 GiB.
+    const size_t cap_floats = ((size_t)2 << 30) / sizeof(float);
+    int chunk = J;
+    if (per_pos > 0) chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)J, cap_floats / per_pos));
+    chunk = std::min(chunk, 65535 / K);           // grid.z of the reduce kernels is J * K
+    float *scratch = nullptr;
+    if (per_pos > 0) PM_CUDA(cudaMallocAsync((void **)&scratch, per_pos * chunk * sizeof(float), st));
+    const size_t NN = (size_t)N * N;
+    for (int j0 = 0; j0 < J && rc == PTYCHO_OK; j0 += chunk) {
+        const int jn = std::min(chunk, J - j0);
+        rc = pm::fuse_dispatch(d_raw + (size_t)j0 * K * NN, jn, K, N, f, d_fused + (size_t)j0 * NN, scratch, st);
+    }
+    if (scratch) {
+        cudaError_t e = cudaFreeAsync(scratch, st);
+        if (rc == PTYCHO_OK && e != cudaSuccess) return pm::cuda_fail(e, "cudaFreeAsync");
+    }
+    return rc;
+}

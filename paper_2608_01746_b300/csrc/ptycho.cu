@@ -1,0 +1,703 @@
+// Iterative ptychographic reconstruction on one GPU (§3.3 forward model, Eqs. 2-3).
+//
+// One iteration (full-batch alternating projections):
+//   k_exit_wave    per position j (one CTA at a time, persistent grid):
+//                  psi = P * O_j  ->  row FFTs  ->  column FFTs, modulus replacement against
+//                  A_j and Fourier error, inverse column FFTs  ->  inverse row FFTs  ->  psi_j'
+//                  The N x N intermediate lives in a per-CTA global slot (L2-resident),
+//                  stored column-major between the passes so that every global access is a
+//                  contiguous run; FFTs are register/shared-memory radix passes (fft.cuh).
+//   k_object_gather  owner-computes object update: each 32 x 32 object tile sums
+//                  conj(P) psi_j' and |P|^2 over the positions whose patch covers it, in
+//                  ascending j (deterministic, no atomics).
+//   k_apply        O = num / (den + alpha_O max den) on pixels inside some scan patch.
+//   k_probe_partial / k_probe_reduce / k_apply
+//                  P = sum_j conj(O_j) psi_j' / (sum_j |O_j|^2 + alpha_P max), with the new
+//                  object, as fixed-order partial sums over position chunks.
+//   k_error_reduce   per-iteration Fourier error in FP64, fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kOT = 32;          // object tile side of the gather
+constexpr int kQT = 32;          // probe tile side of the probe partial sums
+
+enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
+
+struct ExitArgs {
+    const float2 *obj;
+    const float2 *probe;
+    const float *amp;        // [J][N][N] column-major per position: amp[j][kx][ky]
+    const int2 *pos;         // (y, x)
+    float2 *psi;             // [J][N][N] row-major exit-wave update
+    float2 *slot;            // [grid][N][N] per-CTA column-major intermediate
+    double *err;             // [J] Fourier error per position
+    int M, J;
+};
+
+template <int R>
+constexpr size_t exit_smem_bytes() {
+    constexpr int N = R * R;
+    constexpr int G = kThreads / R;
+    return sizeof(float2) * ((size_t)N + (size_t)G * R * (R + 1) + (size_t)G * (N + 1));
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
+    constexpr int N = R * R;
+    constexpr int G = kThreads / R;          // FFT groups per CTA
+    constexpr int TP = N + 1;                // padded tile pitch
+    extern __shared__ float2 smem[];
+    float2 *tw = smem;                       // [N] W_N^(a b), forward sign
+    float2 *xb_all = tw + N;                 // [G][R][R+1]
+    float2 *tile = xb_all + G * R * (R + 1); // [G][N+1] row batch
+    __shared__ double s_red[kThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int t = tid % R, g = tid / R;
+    for (int i = tid; i < N; i += kThreads) {
+        const int ab = (i / R) * (i % R);
+        double s, c;
+        sincospi(-2.0 * (double)ab / (double)N, &s, &c);
+        tw[i] = make_float2((float)c, (float)s);
+    }
+    __syncthreads();
+    float2 *xb = xb_all + g * R * (R + 1);
+    float2 *slot = a.slot + (size_t)blockIdx.x * N * N;
+    const float invN = 1.0f / (float)N;
+    const int M = a.M;
+
+    for (int j = blockIdx.x; j < a.J; j += gridDim.x) {
+        const int2 pj = a.pos[j];
+        // (1) psi = P * O_j, forward row FFTs, written column-major into the slot
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int r = r0 + g;
+            if (r < N) {                                    // warp-uniform (see fft.cuh)
+                float2 d[R];
+                const float2 *orow = a.obj + (size_t)(pj.x + r) * M + pj.y;
+                const float2 *prow = a.probe + (size_t)r * N;
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
+                pm::fft_group<R, -1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) tile[g * TP + t + R * m] = d[m];
+            }
+            __syncthreads();
+            const int rows = min(G, N - r0);
+            for (int e = tid; e < rows * N; e += kThreads) {
+                const int rr = e % rows, c = e / rows;
+                slot[(size_t)c * N + r0 + rr] = tile[rr * TP + c];
+            }
+            __syncthreads();
+        }
+        // (2) column FFTs, modulus replacement, inverse column FFTs (in place in the slot)
+        float err = 0.f;
+        const float *amp_j = a.amp + (size_t)j * N * N;
+        for (int c0 = 0; c0 < N; c0 += G) {
+            const int c = c0 + g;
+            if (c < N) {
+                float2 d[R];
+                float2 *col = slot + (size_t)c * N;
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
+                pm::fft_group<R, -1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const float2 X = cscale(d[m], invN);
+                    const float A = __ldg(amp_j + (size_t)c * N + t + R * m);
+                    const float mag = sqrtf(cabs2(X));
+                    const float dm = mag - A;
+                    err += dm * dm;
+                    d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+                }
+                pm::fft_group<R, +1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) col[t + R * m] = d[m];
+            }
+        }
+        __syncthreads();
+        // (3) inverse row FFTs from the column-major slot, psi_j' written row-major
+        float2 *psi_j = a.psi + (size_t)j * N * N;
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int rows = min(G, N - r0);
+            for (int e = tid; e < rows * N; e += kThreads) {
+                const int rr = e % rows, c = e / rows;
+                tile[rr * TP + c] = slot[(size_t)c * N + r0 + rr];
+            }
+            __syncthreads();
+            const int r = r0 + g;
+            if (r < N) {
+                float2 d[R];
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = tile[g * TP + t + R * m];
+                pm::fft_group<R, +1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) psi_j[(size_t)r * N + t + R * m] = cscale(d[m], invN);
+            }
+            __syncthreads();
+        }
+        // Fourier error of position j (FP64 block sum)
+        double e = (double)err;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = e;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += s_red[w];
+            a.err[j] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Owner-computes object numerator and denominator, one 32 x 32 tile per block.
+__global__ void __launch_bounds__(kThreads) k_object_gather(
+    const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
+    const int *__restrict__ tstart, const int *__restrict__ tlist, float2 *__restrict__ num,
+    float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx) {
+    __shared__ float s_max[kThreads / 32];
+    const int tile = blockIdx.x;
+    const int ty0 = (tile / ntx) * kOT, tx0 = (tile % ntx) * kOT;
+    const int tx = threadIdx.x % kOT, tyb = threadIdx.x / kOT;   // 8 row groups
+    constexpr int PER = kOT / (kThreads / kOT);                  // 4 pixels per thread
+    float2 acc[PER];
+    float dn[PER];
+    bool hit[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { acc[q] = make_float2(0.f, 0.f); dn[q] = 0.f; hit[q] = false; }
+    const int px = tx0 + tx;
+    const size_t NN = (size_t)N * N;
+    for (int e = tstart[tile]; e < tstart[tile + 1]; ++e) {
+        const int j = tlist[e];
+        const int2 pj = pos[j];
+        const int lx = px - pj.y;
+        if (lx < 0 || lx >= N) continue;
+        const float2 *psi_j = psi + (size_t)j * NN;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int ly = ty0 + tyb + q * (kThreads / kOT) - pj.x;
+            if (ly >= 0 && ly < N) {
+                const float2 p = __ldg(probe + ly * N + lx);
+                const float2 v = __ldg(psi_j + (size_t)ly * N + lx);
+                const float2 pv = cmulc(p, v);
+                acc[q] = cadd(acc[q], pv);
+                dn[q] += cabs2(p);
+                hit[q] = true;
+            }
+        }
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int py = ty0 + tyb + q * (kThreads / kOT);
+        if (py < M && px < M) {
+            num[(size_t)py * M + px] = acc[q];
+            den[(size_t)py * M + px] = hit[q] ? dn[q] : -1.0f;   // -1: outside every patch
+            mx = fmaxf(mx, dn[q]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, s_max[w]);
+        tile_max[tile] = m;
+    }
+}
+
+__device__ float block_max(const float *v, int n) {
+    __shared__ float s[kThreads / 32];
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, v[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) r = fmaxf(r, s[w]);
+    return r;
+}
+
+// x = num / (den + alpha max den) where den >= 0 (the pixel lies in some patch; -1 marks
+// pixels outside every patch) and den + alpha max den > 0; elsewhere x keeps its value.
+__global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, const float2 *__restrict__ num,
+                                                    const float *__restrict__ den, const float *__restrict__ partial_max,
+                                                    int nmax, size_t n, float alpha) {
+    const float reg = alpha * block_max(partial_max, nmax);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = den[i];
+        if (d >= 0.f && d + reg > 0.f) {
+            const float s = 1.0f / (d + reg);
+            x[i] = cscale(num[i], s);
+        }
+    }
+}
+
+// Probe partial sums: block (q tile, chunk of positions) -> partial[chunk][q].
+__global__ void __launch_bounds__(kThreads) k_probe_partial(
+    const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
+    float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk) {
+    const int nqx = (N + kQT - 1) / kQT;
+    const int qt = blockIdx.x, chunk = blockIdx.y;
+    const int qy0 = (qt / nqx) * kQT, qx0 = (qt % nqx) * kQT;
+    const int tx = threadIdx.x % kQT, tyb = threadIdx.x / kQT;
+    constexpr int PER = kQT / (kThreads / kQT);
+    const int qx = qx0 + tx;
+    float2 acc[PER];
+    float dn[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { acc[q] = make_float2(0.f, 0.f); dn[q] = 0.f; }
+    const int j0 = chunk * per_chunk, j1 = min(J, j0 + per_chunk);
+    const size_t NN = (size_t)N * N;
+    if (qx < N) {
+        for (int j = j0; j < j1; ++j) {
+            const int2 pj = pos[j];
+            const float2 *psi_j = psi + (size_t)j * NN;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int qy = qy0 + tyb + q * (kThreads / kQT);
+                if (qy < N) {
+                    const float2 o = __ldg(obj + (size_t)(pj.x + qy) * M + pj.y + qx);
+                    const float2 v = __ldg(psi_j + (size_t)qy * N + qx);
+                    acc[q] = cadd(acc[q], cmulc(o, v));
+                    dn[q] += cabs2(o);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int qy = qy0 + tyb + q * (kThreads / kQT);
+            if (qy < N) {
+                pnum[(size_t)chunk * NN + (size_t)qy * N + qx] = acc[q];
+                pden[(size_t)chunk * NN + (size_t)qy * N + qx] = dn[q];
+            }
+        }
+    }
+}
+
+// Fixed-order sum of the chunk partials; per-block max of the denominator.
+__global__ void __launch_bounds__(kThreads) k_probe_reduce(const float2 *__restrict__ pnum,
+                                                           const float *__restrict__ pden, float2 *__restrict__ num,
+                                                           float *__restrict__ den, float *__restrict__ bmax, int NN,
+                                                           int nchunk) {
+    __shared__ float s[kThreads / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.f;
+    if (i < NN) {
+        float2 a = make_float2(0.f, 0.f);
+        for (int c = 0; c < nchunk; ++c) {
+            a = cadd(a, pnum[(size_t)c * NN + i]);
+            d += pden[(size_t)c * NN + i];
+        }
+        num[i] = a;
+        den[i] = d;
+    }
+    float m = d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) r = fmaxf(r, s[w]);
+        bmax[blockIdx.x] = r;
+    }
+}
+
+// Per-iteration error: sum_j err[j] (fixed order) * inv_norm.
+__global__ void k_error_reduce(const double *__restrict__ err, int J, const double *__restrict__ inv_norm,
+                               double *__restrict__ out) {
+    __shared__ double s[kThreads];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < J; i += blockDim.x) a += err[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0] * inv_norm[0];
+}
+
+// A = sqrt(max(I, 0)) with DC moved from the centre to index 0, stored column-major per
+// position (amp[j][kx][ky]); also sum of A^2 per position.
+__global__ void __launch_bounds__(kThreads) k_amplitudes(const float *__restrict__ fused, float *__restrict__ amp,
+                                                         double *__restrict__ a2, int N) {
+    __shared__ double s[kThreads / 32];
+    const int j = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    const int h = N / 2;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int kx = i / N, ky = i % N;            // destination (column-major)
+        const int sy = (ky + h) % N, sx = (kx + h) % N;
+        const float v = sqrtf(fmaxf(fused[(size_t)j * NN + (size_t)sy * N + sx], 0.f));
+        amp[(size_t)j * NN + i] = v;
+        acc += (double)v * (double)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) r += s[w];
+        a2[j] = r;
+    }
+}
+
+__global__ void k_inv_norm(const double *__restrict__ a2, int J, double *__restrict__ inv_norm) {
+    __shared__ double s[kThreads];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < J; i += blockDim.x) a += a2[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) inv_norm[0] = s[0] > 0.0 ? 1.0 / s[0] : 0.0;
+}
+
+}  // namespace
+
+struct ptycho_ctx {
+    int M = 0, N = 0, J = 0, R = 0;
+    float alpha_O = 0.f, alpha_P = 0.f;
+    int probe_update_start = 0;
+    long long iter = 0;
+    cudaStream_t st = nullptr;
+    int2 *d_pos = nullptr;
+    float2 *d_obj = nullptr, *d_probe = nullptr, *d_psi = nullptr, *d_slot = nullptr;
+    float2 *d_num_o = nullptr, *d_num_p = nullptr, *d_pnum = nullptr;
+    float *d_amp = nullptr, *d_den_o = nullptr, *d_den_p = nullptr, *d_pden = nullptr;
+    float *d_tile_max = nullptr, *d_pmax = nullptr;
+    double *d_err_pos = nullptr, *d_a2 = nullptr, *d_inv_norm = nullptr, *d_err = nullptr;
+    int err_cap = 0;
+    int *d_tstart = nullptr, *d_tlist = nullptr;
+    int ntx = 0, ntiles = 0;
+    int grid_exit = 0, nchunk = 0, per_chunk = 0, nqt = 0, nred = 0;
+    size_t exit_smem = 0;
+    // timing
+    bool timing = false;
+    double stage_ms[ST_COUNT] = {};
+    long long stage_launches[ST_COUNT] = {};
+    std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) return pm::cuda_fail(e, "cudaMalloc");
+    return PTYCHO_OK;
+}
+
+void free_ctx(ptycho_ctx *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
+                    h->d_amp, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+template <int R>
+int setup_exit_kernel(ptycho_ctx *h) {
+    const size_t smem = exit_smem_bytes<R>();
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<R>, kThreads, smem));
+    if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "exit-wave kernel cannot be resident (smem %zu)", smem);
+    h->exit_smem = smem;
+    h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
+    return PTYCHO_OK;
+}
+
+template <int R>
+void launch_exit(ptycho_ctx *h) {
+    ExitArgs a;
+    a.obj = h->d_obj;
+    a.probe = h->d_probe;
+    a.amp = h->d_amp;
+    a.pos = h->d_pos;
+    a.psi = h->d_psi;
+    a.slot = h->d_slot;
+    a.err = h->d_err_pos;
+    a.M = h->M;
+    a.J = h->J;
+    k_exit_wave<R><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+}
+
+int stage_begin(ptycho_ctx *h, int s, size_t idx) {
+    if (!h->timing) return PTYCHO_OK;
+    (void)s;
+    PM_CUDA(cudaEventRecord(h->ev[2 * idx], h->st));
+    return PTYCHO_OK;
+}
+
+int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
+    if (!h->timing) return PTYCHO_OK;
+    PM_CUDA(cudaEventRecord(h->ev[2 * idx + 1], h->st));
+    h->stage_launches[s] += launches;
+    return PTYCHO_OK;
+}
+
+int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe) {
+    int rc;
+    // exit waves
+    if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
+    switch (h->R) {
+        case 4: launch_exit<4>(h); break;
+        case 8: launch_exit<8>(h); break;
+        default: launch_exit<16>(h); break;
+    }
+    PM_LAUNCHED("k_exit_wave");
+    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, 1))) return rc;
+    // object
+    if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
+    k_object_gather<<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
+                                                       h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N, h->ntx);
+    PM_LAUNCHED("k_object_gather");
+    const size_t MM = (size_t)h->M * h->M;
+    const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
+    k_apply<<<gapply, kThreads, 0, h->st>>>(h->d_obj, h->d_num_o, h->d_den_o, h->d_tile_max, h->ntiles, MM,
+                                            h->alpha_O);
+    PM_LAUNCHED("k_apply(object)");
+    if ((rc = stage_end(h, ST_OBJECT, ev_base + 1, 2))) return rc;
+    // probe
+    if ((rc = stage_begin(h, ST_PROBE, ev_base + 2))) return rc;
+    if (update_probe) {
+        const int NN = h->N * h->N;
+        k_probe_partial<<<dim3(h->nqt, h->nchunk), kThreads, 0, h->st>>>(h->d_psi, h->d_obj, h->d_pos, h->d_pnum,
+                                                                        h->d_pden, h->M, h->N, h->J, h->per_chunk);
+        PM_LAUNCHED("k_probe_partial");
+        k_probe_reduce<<<h->nred, kThreads, 0, h->st>>>(h->d_pnum, h->d_pden, h->d_num_p, h->d_den_p, h->d_pmax, NN,
+                                                        h->nchunk);
+        PM_LAUNCHED("k_probe_reduce");
+        const unsigned gp = (unsigned)std::min<int>((NN + kThreads - 1) / kThreads, 148 * 4);
+        k_apply<<<gp, kThreads, 0, h->st>>>(h->d_probe, h->d_num_p, h->d_den_p, h->d_pmax, h->nred, (size_t)NN,
+                                            h->alpha_P);
+        PM_LAUNCHED("k_apply(probe)");
+    }
+    if ((rc = stage_end(h, ST_PROBE, ev_base + 2, update_probe ? 3 : 0))) return rc;
+    // error
+    if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
+    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, h->d_err + it_in_call);
+    PM_LAUNCHED("k_error_reduce");
+    if ((rc = stage_end(h, ST_ERROR, ev_base + 3, 1))) return rc;
+    return PTYCHO_OK;
+}
+
+int copy_in_complex(float2 *dst, const void *src, size_t count, bool on_device, cudaStream_t st) {
+    PM_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(float2),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
+    if (!out) return pm::fail(PTYCHO_EINVAL, "ptycho_init: out is NULL");
+    *out = nullptr;
+    if (!d) return pm::fail(PTYCHO_EINVAL, "ptycho_init: desc is NULL");
+    int R = 0;
+    if (d->N == 16) R = 4;
+    else if (d->N == 64) R = 8;
+    else if (d->N == 256) R = 16;
+    else return pm::fail(PTYCHO_EINVAL, "ptycho_init: N = %d unsupported (16, 64 or 256)", d->N);
+    if (d->J < 1) return pm::fail(PTYCHO_EINVAL, "ptycho_init: J = %d < 1", d->J);
+    if (d->M < d->N || d->M > 32768) return pm::fail(PTYCHO_EINVAL, "ptycho_init: M = %d must be in [N, 32768]", d->M);
+    if (!d->h_pos || !d->d_fused || !d->obj0 || !d->probe0)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: NULL position, fused, object or probe pointer");
+    if (!(d->alpha_O >= 0.f) || !(d->alpha_P >= 0.f) || !std::isfinite(d->alpha_O) || !std::isfinite(d->alpha_P))
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: regularisers must be finite and >= 0");
+    if (d->probe_update_start < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_init: probe_update_start < 0");
+    const int M = d->M, N = d->N, J = d->J;
+    for (int j = 0; j < J; ++j) {
+        const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
+        if (y < 0 || x < 0 || y > M - N || x > M - N)
+            return pm::fail(PTYCHO_EINVAL, "ptycho_init: position %d = (%d, %d) outside [0, %d]", j, y, x, M - N);
+    }
+    ptycho_ctx *h = new (std::nothrow) ptycho_ctx();
+    if (!h) return pm::fail(PTYCHO_ENOMEM, "ptycho_init: host allocation failed");
+    h->M = M; h->N = N; h->J = J; h->R = R;
+    h->alpha_O = d->alpha_O; h->alpha_P = d->alpha_P;
+    h->probe_update_start = d->probe_update_start;
+    h->st = (cudaStream_t)d->cuda_stream;
+    int rc = PTYCHO_OK;
+    const size_t NN = (size_t)N * N, MM = (size_t)M * M;
+    // object tiles and their position lists (ascending j)
+    h->ntx = (M + kOT - 1) / kOT;
+    h->ntiles = h->ntx * h->ntx;
+    std::vector<int> tstart(h->ntiles + 1, 0), tlist;
+    {
+        std::vector<std::vector<int>> lists(h->ntiles);
+        for (int j = 0; j < J; ++j) {
+            const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
+            const int ty0 = y / kOT, ty1 = (y + N - 1) / kOT, tx0 = x / kOT, tx1 = (x + N - 1) / kOT;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) lists[ty * h->ntx + tx].push_back(j);
+        }
+        for (int t = 0; t < h->ntiles; ++t) tstart[t + 1] = tstart[t] + (int)lists[t].size();
+        tlist.reserve(tstart[h->ntiles]);
+        for (int t = 0; t < h->ntiles; ++t) tlist.insert(tlist.end(), lists[t].begin(), lists[t].end());
+    }
+    // probe partial-sum layout
+    h->nqt = ((N + kQT - 1) / kQT) * ((N + kQT - 1) / kQT);
+    h->nchunk = std::max(1, std::min(J, (148 * 8 + h->nqt - 1) / h->nqt));
+    h->per_chunk = (J + h->nchunk - 1) / h->nchunk;
+    h->nchunk = (J + h->per_chunk - 1) / h->per_chunk;
+    h->nred = (int)((NN + kThreads - 1) / kThreads);
+
+    switch (R) {
+        case 4: rc = setup_exit_kernel<4>(h); break;
+        case 8: rc = setup_exit_kernel<8>(h); break;
+        default: rc = setup_exit_kernel<16>(h); break;
+    }
+    if (!rc) rc = dalloc(&h->d_pos, J);
+    if (!rc) rc = dalloc(&h->d_obj, MM);
+    if (!rc) rc = dalloc(&h->d_probe, NN);
+    if (!rc) rc = dalloc(&h->d_psi, (size_t)J * NN);
+    if (!rc) rc = dalloc(&h->d_slot, (size_t)h->grid_exit * NN);
+    if (!rc) rc = dalloc(&h->d_num_o, MM);
+    if (!rc) rc = dalloc(&h->d_den_o, MM);
+    if (!rc) rc = dalloc(&h->d_tile_max, h->ntiles);
+    if (!rc) rc = dalloc(&h->d_num_p, NN);
+    if (!rc) rc = dalloc(&h->d_den_p, NN);
+    if (!rc) rc = dalloc(&h->d_pnum, (size_t)h->nchunk * NN);
+    if (!rc) rc = dalloc(&h->d_pden, (size_t)h->nchunk * NN);
+    if (!rc) rc = dalloc(&h->d_pmax, h->nred);
+    if (!rc) rc = dalloc(&h->d_amp, (size_t)J * NN);
+    if (!rc) rc = dalloc(&h->d_err_pos, J);
+    if (!rc) rc = dalloc(&h->d_a2, J);
+    if (!rc) rc = dalloc(&h->d_inv_norm, 1);
+    if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
+    if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
+    if (rc) { free_ctx(h); return rc; }
+    auto fail_cuda = [&](cudaError_t e, const char *what) {
+        int r = pm::cuda_fail(e, what);
+        free_ctx(h);
+        return r;
+    };
+    cudaError_t e;
+    std::vector<int2> pos2(J);
+    for (int j = 0; j < J; ++j) pos2[j] = make_int2(d->h_pos[2 * j], d->h_pos[2 * j + 1]);
+    if ((e = cudaMemcpyAsync(h->d_pos, pos2.data(), J * sizeof(int2), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy positions");
+    if ((e = cudaMemcpyAsync(h->d_tstart, tstart.data(), tstart.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy tile starts");
+    if (!tlist.empty() &&
+        (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy tile lists");
+    if ((rc = copy_in_complex(h->d_obj, d->obj0, MM, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
+    if ((rc = copy_in_complex(h->d_probe, d->probe0, NN, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
+    k_amplitudes<<<J, kThreads, 0, h->st>>>(d->d_fused, h->d_amp, h->d_a2, N);
+    if ((e = cudaGetLastError())) return fail_cuda(e, "k_amplitudes");
+    k_inv_norm<<<1, kThreads, 0, h->st>>>(h->d_a2, J, h->d_inv_norm);
+    if ((e = cudaGetLastError())) return fail_cuda(e, "k_inv_norm");
+    if ((e = cudaStreamSynchronize(h->st))) return fail_cuda(e, "ptycho_init synchronise");
+    *out = h;
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
+    if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_iterate: NULL handle");
+    if (n_iter < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_iterate: n_iter = %d < 0", n_iter);
+    if (n_iter == 0) return PTYCHO_OK;
+    if (n_iter > h->err_cap) {
+        if (h->d_err) {
+            PM_CUDA(cudaStreamSynchronize(h->st));
+            PM_CUDA(cudaFree(h->d_err));
+            h->d_err = nullptr;
+        }
+        int rc = dalloc(&h->d_err, (size_t)n_iter);
+        if (rc) { h->err_cap = 0; return rc; }
+        h->err_cap = n_iter;
+    }
+    if (h->timing) {
+        const size_t need = (size_t)n_iter * ST_COUNT * 2;
+        while (h->ev.size() < need) {
+            cudaEvent_t ev;
+            PM_CUDA(cudaEventCreate(&ev));
+            h->ev.push_back(ev);
+        }
+    }
+    for (int i = 0; i < n_iter; ++i) {
+        const bool upd = h->iter >= h->probe_update_start;
+        int rc = iterate_one(h, i, (size_t)i * ST_COUNT, upd);
+        if (rc) return rc;
+        ++h->iter;
+    }
+    if (h->timing) {
+        PM_CUDA(cudaEventSynchronize(h->ev[(size_t)n_iter * ST_COUNT * 2 - 1]));
+        for (int i = 0; i < n_iter; ++i)
+            for (int s = 0; s < ST_COUNT; ++s) {
+                float ms = 0.f;
+                const size_t b = ((size_t)i * ST_COUNT + s) * 2;
+                PM_CUDA(cudaEventElapsedTime(&ms, h->ev[b], h->ev[b + 1]));
+                h->stage_ms[s] += ms;
+            }
+    }
+    if (h_err) {
+        PM_CUDA(cudaMemcpyAsync(h_err, h->d_err, (size_t)n_iter * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        PM_CUDA(cudaStreamSynchronize(h->st));
+        for (int i = 0; i < n_iter; ++i)
+            if (!std::isfinite(h_err[i]))
+                return pm::fail(PTYCHO_ENONFINITE, "ptycho_iterate: error of iteration %d is not finite", i);
+    }
+    return PTYCHO_OK;
+}
+
+static int get_complex(ptycho_handle h, const float2 *src, size_t count, void *dst, int dst_on_device) {
+    if (!h || !dst) return pm::fail(PTYCHO_EINVAL, "get: NULL handle or destination");
+    PM_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(float2),
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    if (!dst_on_device) PM_CUDA(cudaStreamSynchronize(h->st));
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_get_object(ptycho_handle h, void *dst, int dst_on_device) {
+    if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_get_object: NULL handle");
+    return get_complex(h, h->d_obj, (size_t)h->M * h->M, dst, dst_on_device);
+}
+
+extern "C" int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device) {
+    if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_get_probe: NULL handle");
+    return get_complex(h, h->d_probe, (size_t)h->N * h->N, dst, dst_on_device);
+}
+
+extern "C" void ptycho_destroy(ptycho_handle h) { free_ctx(h); }
+
+extern "C" int ptycho_set_timing(ptycho_handle h, int enable) {
+    if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_set_timing: NULL handle");
+    h->timing = enable != 0;
+    for (int s = 0; s < ST_COUNT; ++s) { h->stage_ms[s] = 0.0; h->stage_launches[s] = 0; }
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_stage_times(ptycho_handle h, double *ms, long long *launches) {
+    if (!h || !ms || !launches) return pm::fail(PTYCHO_EINVAL, "ptycho_stage_times: NULL argument");
+    for (int s = 0; s < ST_COUNT; ++s) { ms[s] = h->stage_ms[s]; launches[s] = h->stage_launches[s]; }
+    return PTYCHO_OK;
+}

@@ -147,14 +147,15 @@ def _far_field_intensity(obj: np.ndarray, probe: np.ndarray, pos: np.ndarray) ->
 
 
 def make_scan(cfg: ScanConfig | str, seed: int | None = None, noise: bool = True,
-              clip: bool = True, times: tuple | None = None) -> dict:
+              clip: bool = True, times: tuple | None = None, frames_for=None) -> dict:
     """Ground truth plus a K-exposure raw stack ``raw[J][K][N][N]`` (uint16, DC-centred).
 
     The probe is scaled so that the brightest expected pixel of the longest exposure holds
     ``cfg.peak`` counts; frame k has mean ``I * t_k / t_max``.  ``noise=False`` rounds the mean
     instead of drawing Poisson counts; ``clip=False`` keeps counts above full scale (stored as
-    float64 in ``raw`` then).  Returns a dict with obj, probe (scaled), pos, times, clip_value,
-    intensity (expected counts at t_max) and raw.
+    float64 in ``raw`` then).  ``frames_for`` (position indices) simulates frames for those
+    positions only (``raw`` then has one row per listed position).  Returns a dict with obj,
+    probe (scaled), pos, times, clip_value, intensity (expected counts at t_max) and raw.
     """
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
@@ -171,9 +172,10 @@ def make_scan(cfg: ScanConfig | str, seed: int | None = None, noise: bool = True
     inten = inten * scale
     tmax = max(times)
     K = len(times)
-    raw = np.empty((len(pos), K, cfg.N, cfg.N), dtype=np.float64)
+    sel = np.arange(len(pos)) if frames_for is None else np.asarray(frames_for)
+    raw = np.empty((len(sel), K, cfg.N, cfg.N), dtype=np.float64)
     for k, t in enumerate(times):
-        lam = inten * (t / tmax)
+        lam = inten[sel] * (t / tmax)
         raw[:, k] = rng.poisson(lam) if noise else np.rint(lam)
     if clip:
         raw = np.minimum(raw, cfg.clip).astype(np.uint16)
