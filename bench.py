@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration count (profiling runs only; not a bench value)")
+    ap.add_argument("--positions", type=int, default=None,
+                    help="use only the first N scan positions (profiling runs only; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -145,6 +147,9 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     cfg = synth.CONFIGS[WORKLOAD]
     n_iter = args.iters or cfg.n_iter
+    if args.positions:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, J=args.positions)
     sc = synth.make_scan_torch(cfg, seed=synth.seed_for(WORKLOAD) + 7919 * rank, device=dev)
     raw = sc["raw"]
     J, K, N = raw.shape[0], cfg.K, cfg.N

@@ -107,3 +107,53 @@ __device__ __forceinline__ void fft_group(float2 (&d)[R], float2 *xb, const floa
 }
 
 }  // namespace pm
+
+namespace pm {
+
+// Same transform as fft_group, with an unpadded R*R exchange buffer laid out with an XOR
+// swizzle (element (k1, n2) at k1 * R + (n2 ^ k1)): conflict-free for the write and the
+// transposed read without padding.  `tw_reg[k1]` holds W_N^(t k1) (forward sign) for this
+// thread's t, so the twiddles cost no shared-memory traffic.
+template <int R, int SIGN>
+__device__ __forceinline__ void fft_group_x(float2 (&d)[R], float2 *xb, const float2 (&tw_reg)[R], int t) {
+    dft_reg<R, SIGN>(d);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) {
+        float2 w = tw_reg[k1];
+        if (SIGN > 0) w.y = -w.y;
+        d[k1] = cmul(d[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) xb[k1 * R + (t ^ k1)] = d[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) d[n2] = xb[t * R + (n2 ^ t)];
+    dft_reg<R, SIGN>(d);
+}
+
+}  // namespace pm
+
+namespace pm {
+
+// fft_group_x with the twiddles read from a shared-memory table tw[k1 * R + t] = W_N^(t k1)
+// (forward sign; consecutive t are consecutive words, so the reads are conflict-free).
+template <int R, int SIGN>
+__device__ __forceinline__ void fft_group_xs(float2 (&d)[R], float2 *xb, const float2 *tw, int t) {
+    dft_reg<R, SIGN>(d);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) {
+        float2 w = tw[k1 * R + t];
+        if (SIGN > 0) w.y = -w.y;
+        d[k1] = cmul(d[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) xb[k1 * R + (t ^ k1)] = d[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) d[n2] = xb[t * R + (n2 ^ t)];
+    dft_reg<R, SIGN>(d);
+}
+
+}  // namespace pm

@@ -1,12 +1,12 @@
 // Iterative ptychographic reconstruction on one GPU (§3.3 forward model, Eqs. 2-3).
 //
 // One iteration (full-batch alternating projections):
-//   k_exit_wave    per position j (one CTA at a time, persistent grid):
+//   k_exit_wave    per position j (one thread-block cluster at a time, persistent grid):
 //                  psi = P * O_j  ->  row FFTs  ->  column FFTs, modulus replacement against
 //                  A_j and Fourier error, inverse column FFTs  ->  inverse row FFTs  ->  psi_j'
-//                  The N x N intermediate lives in a per-CTA global slot (L2-resident),
-//                  stored column-major between the passes so that every global access is a
-//                  contiguous run; FFTs are register/shared-memory radix passes (fft.cuh).
+//                  The N x N intermediate stays in the cluster's distributed shared memory
+//                  (a 256 x 256 complex64 tile is 512 KB: 8 CTAs x 64 KB); FFTs are
+//                  register/shared-memory radix passes (fft.cuh).
 //   k_object_gather  owner-computes object update: each 32 x 32 object tile sums
 //                  conj(P) psi_j' and |P|^2 over the positions whose patch covers it, in
 //                  ascending j (deterministic, no atomics).
@@ -22,8 +22,12 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
+
 
 namespace {
 
@@ -39,49 +43,52 @@ struct ExitArgs {
     const float *amp;        // [J][N][N] column-major per position: amp[j][kx][ky]
     const int2 *pos;         // (y, x)
     float2 *psi;             // [J][N][N] row-major exit-wave update
-    float2 *slot;            // [grid][N][N] per-CTA column-major intermediate
     double *err;             // [J] Fourier error per position
     int M, J;
 };
 
+// Shared memory of the small-tile exit-wave kernel: twiddles, the FFT groups' exchange
+// buffers, and the whole N x N tile (pitch N + 1).
 template <int R>
 constexpr size_t exit_smem_bytes() {
     constexpr int N = R * R;
     constexpr int G = kThreads / R;
-    return sizeof(float2) * ((size_t)N + (size_t)G * R * (R + 1) + (size_t)G * (N + 1));
+    return sizeof(float2) * ((size_t)N + (size_t)G * R * (R + 1) + (size_t)N * (N + 1));
 }
 
+// N <= 64: one CTA per position at a time (persistent grid), the whole N x N tile in shared
+// memory: row FFTs, column FFTs with the modulus replacement between the forward and inverse
+// column transforms, inverse row FFTs written to psi_j'.
 template <int R>
 __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     constexpr int N = R * R;
     constexpr int G = kThreads / R;          // FFT groups per CTA
-    constexpr int TP = N + 1;                // padded tile pitch
+    constexpr int TP = N + 1;                // padded row pitch
     extern __shared__ float2 smem[];
     float2 *tw = smem;                       // [N] W_N^(a b), forward sign
     float2 *xb_all = tw + N;                 // [G][R][R+1]
-    float2 *tile = xb_all + G * R * (R + 1); // [G][N+1] row batch
+    float2 *rows = xb_all + G * R * (R + 1); // [N][N+1]
     __shared__ double s_red[kThreads / 32];
 
     const int tid = threadIdx.x;
     const int t = tid % R, g = tid / R;
     for (int i = tid; i < N; i += kThreads) {
         const int ab = (i / R) * (i % R);
-        double s, c;
-        sincospi(-2.0 * (double)ab / (double)N, &s, &c);
-        tw[i] = make_float2((float)c, (float)s);
+        double sn, cs;
+        sincospi(-2.0 * (double)ab / (double)N, &sn, &cs);
+        tw[i] = make_float2((float)cs, (float)sn);
     }
     __syncthreads();
     float2 *xb = xb_all + g * R * (R + 1);
-    float2 *slot = a.slot + (size_t)blockIdx.x * N * N;
     const float invN = 1.0f / (float)N;
     const int M = a.M;
 
     for (int j = blockIdx.x; j < a.J; j += gridDim.x) {
         const int2 pj = a.pos[j];
-        // (1) psi = P * O_j, forward row FFTs, written column-major into the slot
+        // (1) psi = P * O_j, forward row FFTs in place
         for (int r0 = 0; r0 < N; r0 += G) {
             const int r = r0 + g;
-            if (r < N) {                                    // warp-uniform (see fft.cuh)
+            if (r < N) {                                     // warp-uniform (see fft.cuh)
                 float2 d[R];
                 const float2 *orow = a.obj + (size_t)(pj.x + r) * M + pj.y;
                 const float2 *prow = a.probe + (size_t)r * N;
@@ -89,26 +96,19 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
                 for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
                 pm::fft_group<R, -1>(d, xb, tw, t);
 #pragma unroll
-                for (int m = 0; m < R; ++m) tile[g * TP + t + R * m] = d[m];
+                for (int m = 0; m < R; ++m) rows[r * TP + t + R * m] = d[m];
             }
-            __syncthreads();
-            const int rows = min(G, N - r0);
-            for (int e = tid; e < rows * N; e += kThreads) {
-                const int rr = e % rows, c = e / rows;
-                slot[(size_t)c * N + r0 + rr] = tile[rr * TP + c];
-            }
-            __syncthreads();
         }
-        // (2) column FFTs, modulus replacement, inverse column FFTs (in place in the slot)
+        __syncthreads();
+        // (2) column FFTs, modulus replacement, inverse column FFTs
         float err = 0.f;
         const float *amp_j = a.amp + (size_t)j * N * N;
         for (int c0 = 0; c0 < N; c0 += G) {
             const int c = c0 + g;
             if (c < N) {
                 float2 d[R];
-                float2 *col = slot + (size_t)c * N;
 #pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
+                for (int m = 0; m < R; ++m) d[m] = rows[(t + R * m) * TP + c];
                 pm::fft_group<R, -1>(d, xb, tw, t);
 #pragma unroll
                 for (int m = 0; m < R; ++m) {
@@ -121,42 +121,254 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
                 }
                 pm::fft_group<R, +1>(d, xb, tw, t);
 #pragma unroll
-                for (int m = 0; m < R; ++m) col[t + R * m] = d[m];
+                for (int m = 0; m < R; ++m) rows[(t + R * m) * TP + c] = d[m];
             }
         }
         __syncthreads();
-        // (3) inverse row FFTs from the column-major slot, psi_j' written row-major
+        // (3) inverse row FFTs, psi_j' written row-major
         float2 *psi_j = a.psi + (size_t)j * N * N;
         for (int r0 = 0; r0 < N; r0 += G) {
-            const int rows = min(G, N - r0);
-            for (int e = tid; e < rows * N; e += kThreads) {
-                const int rr = e % rows, c = e / rows;
-                tile[rr * TP + c] = slot[(size_t)c * N + r0 + rr];
-            }
-            __syncthreads();
             const int r = r0 + g;
             if (r < N) {
                 float2 d[R];
 #pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = tile[g * TP + t + R * m];
+                for (int m = 0; m < R; ++m) d[m] = rows[r * TP + t + R * m];
                 pm::fft_group<R, +1>(d, xb, tw, t);
 #pragma unroll
                 for (int m = 0; m < R; ++m) psi_j[(size_t)r * N + t + R * m] = cscale(d[m], invN);
             }
-            __syncthreads();
         }
-        // Fourier error of position j (FP64 block sum)
+        // Fourier error of position j (FP64 block sum); the barrier also keeps the next
+        // position's row pass from overwriting rows that step (3) still reads
         double e = (double)err;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
         if ((tid & 31) == 0) s_red[tid >> 5] = e;
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) s += s_red[w];
-            a.err[j] = s;
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+            a.err[j] = sum;
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// N = 256 exit-wave kernel: one 512-thread CTA per SM, persistent over positions, with a
+// TMA pipeline through a per-CTA 512 KB tile slot that stays in L2.  Batches are 32 rows or
+// columns (one per 16-thread FFT group); every batch of tile data is a bulk tensor copy that
+// runs while the previous batch is transformed.
+//
+//   phase R   rows r = 32 b + g: probe rows arrive by TMA (double-buffered), object patch rows
+//             by register-prefetched loads (the patch origin x is not 16-byte aligned);
+//             psi = P * O_j, forward row FFT, written (128-byte swizzle) to a staging buffer
+//             that is TMA-stored column-major into the slot.
+//   phase C   32 slot columns per TMA load (double-buffered); forward column FFT, modulus
+//             replacement against A_j (loads issued before the FFT), inverse column FFT;
+//             results TMA-stored (128-byte swizzle) into psi_j, row-major.
+//   phase R'  32 rows of psi_j per TMA load, inverse row FFT, TMA-stored back in place.
+// FFT exchanges happen in place in the group's own staged row or column.  Waits are bounded
+// (tma.cuh); on a timeout the kernel sets *a.status and returns.
+struct TmaArgs {
+    const float2 *obj;
+    const float *amp;        // [J][N][N] column-major per position
+    const int2 *pos;
+    double *err;             // [J] Fourier error per position
+    int *status;             // set to 1 if a bounded wait gave up
+    int M, J;
+};
+
+struct TmaMaps {
+    CUtensorMap prow;        // probe rows            box {256 c, 32 r}
+    CUtensorMap slot_r;      // slot, column-major    box {16 r, 256 c}, 128-byte swizzle
+    CUtensorMap slot_c;      // slot, column-major    box {256 r, 32 c}
+    CUtensorMap psi_c;       // psi, row-major        box {16 c, 256 r}, 128-byte swizzle
+    CUtensorMap psi_r;       // psi, row-major        box {256 c, 32 r}  (loads)
+    CUtensorMap psi_w;       // psi, row-major        box {256 c, 16 r}  (stores)
+};
+
+constexpr int kTmaThreads = 512;
+constexpr int kTmaBatch = 32;                                   // rows / columns per batch
+constexpr size_t kTmaBuf = (size_t)kTmaBatch * 256 * sizeof(float2);   // 64 KB
+constexpr size_t kTmaSmem = 1024 /*alignment slack*/ + 3 * kTmaBuf + 256 * sizeof(float2) + 64;
+
+__global__ void __launch_bounds__(kTmaThreads, 1)
+k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
+    constexpr int R = 16, N = 256, NB = N / kTmaBatch;
+    namespace T = pm::tma;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    auto bin = [&](int s) { return (float2 *)(base + s * kTmaBuf); };
+    float2 *bout = (float2 *)(base + 2 * kTmaBuf);
+    float2 *tw = (float2 *)(base + 3 * kTmaBuf);                 // tw[k1 * 16 + t] = W_N^(t k1)
+    uint64_t *bar = (uint64_t *)(base + 3 * kTmaBuf + 256 * sizeof(float2));
+    __shared__ double s_red[kTmaThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int t = tid & 15, g = tid >> 4;                        // g in [0, 32)
+    const int h = g >> 4, gl = g & 15;                           // half of the batch, row in it
+    if (tid < 256) {
+        double sn, cs;
+        sincospi(-2.0 * (double)((tid >> 4) * (tid & 15)) / (double)N, &sn, &cs);
+        tw[tid] = make_float2((float)cs, (float)sn);
+    }
+    if (tid == 0) {
+        T::mbar_init(&bar[0], 1);
+        T::mbar_init(&bar[1], 1);
+        T::fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0u;                                        // bit s: phase parity of bar[s]
+    const int slot_col = blockIdx.x * N;                         // this CTA's slot columns
+    const float invN = 1.0f / (float)N;
+    const int M = a.M;
+    bool failed = false;                                         // uniform after each barrier
+    bool timed_out = false;                                      // this thread's waits
+    auto wait_stage = [&](int s) {
+        if (!T::mbar_wait(&bar[s], (parity >> s) & 1u)) timed_out = true;
+        parity ^= 1u << s;
+    };
+    // Barrier A of every batch: the batch's input buffer is consumed, the staging buffer's
+    // previous store has finished reading it (thread 0 waited just before), and a timed-out
+    // wait anywhere in the CTA is agreed on.
+    auto barrier_a = [&]() {
+        if (tid == 0) T::wait_read<0>();
+        if (__syncthreads_or(timed_out)) failed = true;
+    };
+    // Staging buffer written: thread 0 stores it.
+    auto publish = [&](const CUtensorMap *map, int x0, int y0, int dx, int dy) {
+        T::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            T::store_2d(map, x0, y0, bout);
+            T::store_2d(map, x0 + dx, y0 + dy, bout + 4096);
+            T::commit();
+        }
+    };
+    auto prefetch = [&](int s, const CUtensorMap *map, int x, int y) {
+        if (tid == 0) {
+            T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
+            T::load_2d(bin(s), map, x, y, &bar[s]);
+        }
+    };
+
+    for (int j = blockIdx.x; j < a.J && !failed; j += gridDim.x) {
+        const int2 pj = a.pos[j];
+        // ---- phase R: forward row FFTs -> slot (column-major)
+        prefetch(0, &tm.prow, 0, 0);
+        prefetch(1, &tm.prow, 0, kTmaBatch);
+        float2 pO[R];
+        {
+            const float2 *orow = a.obj + (size_t)(pj.x + g) * M + pj.y;
+#pragma unroll
+            for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
+        }
+        for (int b = 0; b < NB; ++b) {
+            const int s = b & 1;
+            wait_stage(s);
+            float2 *row = bin(s) + g * 256;
+            float2 d[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) d[m] = cmul(row[t + R * m], pO[m]);
+            if (b + 1 < NB) {
+                const float2 *orow = a.obj + (size_t)(pj.x + kTmaBatch * (b + 1) + g) * M + pj.y;
+#pragma unroll
+                for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
+            }
+            pm::fft_group_xs<R, -1>(d, row, tw, t);
+            barrier_a();
+            if (failed) break;
+            if (b + 2 < NB) prefetch(s, &tm.prow, 0, kTmaBatch * (b + 2));
+            float2 *ob = bout + h * 4096;
+#pragma unroll
+            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
+            publish(&tm.slot_r, kTmaBatch * b, slot_col, 16, 0);
+        }
+        if (failed) break;
+        if (tid == 0) T::wait_all<0>();                 // slot complete before phase C reads it
+        prefetch(0, &tm.slot_c, 0, slot_col);
+        prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch);
+        // ---- phase C: column FFTs, modulus replacement, inverse column FFTs -> psi_j
+        float err = 0.f;
+        for (int b = 0; b < NB; ++b) {
+            const int s = b & 1;
+            const int c = kTmaBatch * b + g;
+            float A[R];                                   // A[k2] = |F psi| target at ky = t + 16 k2
+            {
+                const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c) * N + t * R);
+#pragma unroll
+                for (int v = 0; v < R / 4; ++v) {
+                    const float4 q = __ldg(amp + v);
+                    A[4 * v] = q.x; A[4 * v + 1] = q.y; A[4 * v + 2] = q.z; A[4 * v + 3] = q.w;
+                }
+            }
+            wait_stage(s);
+            float2 *col = bin(s) + g * 256;
+            float2 d[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
+            pm::fft_group_xs<R, -1>(d, col, tw, t);
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const float2 X = cscale(d[m], invN);
+                const float mag2 = cabs2(X);
+                if (mag2 > 0.f) {
+                    const float inv = rsqrtf(mag2);
+                    const float dm = mag2 * inv - A[m];
+                    err += dm * dm;
+                    d[m] = cscale(X, A[m] * inv);
+                } else {
+                    err += A[m] * A[m];
+                    d[m] = make_float2(A[m], 0.f);
+                }
+            }
+            pm::fft_group_xs<R, +1>(d, col, tw, t);
+            barrier_a();
+            if (failed) break;
+            if (b + 2 < NB) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2));
+            float2 *ob = bout + h * 4096;
+#pragma unroll
+            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
+            publish(&tm.psi_c, kTmaBatch * b, j * N, 16, 0);
+        }
+        if (failed) break;
+        if (tid == 0) T::wait_all<0>();                 // psi_j columns complete before R'
+        prefetch(0, &tm.psi_r, 0, j * N);
+        prefetch(1, &tm.psi_r, 0, j * N + kTmaBatch);
+        // ---- phase R': inverse row FFTs of psi_j -> psi_j'
+        for (int b = 0; b < NB; ++b) {
+            const int s = b & 1;
+            wait_stage(s);
+            float2 *row = bin(s) + g * 256;
+            float2 d[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) d[m] = row[t + R * m];
+            pm::fft_group_xs<R, +1>(d, row, tw, t);
+            barrier_a();
+            if (failed) break;
+            if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, j * N + kTmaBatch * (b + 2));
+#pragma unroll
+            for (int m = 0; m < R; ++m) bout[g * 256 + t + R * m] = cscale(d[m], invN);
+            publish(&tm.psi_w, 0, j * N + kTmaBatch * b, 0, 16);
+        }
+        if (failed) break;
+        double e = (double)err;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = e;
+        __syncthreads();
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < kTmaThreads / 32; ++w) sum += s_red[w];
+            a.err[j] = sum;
+            T::wait_all<0>();                           // psi_j complete; buffers free for j + 1
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        T::wait_all<0>();
+        if (failed) atomicExch(a.status, 1);
     }
 }
 
@@ -331,17 +543,20 @@ __global__ void k_error_reduce(const double *__restrict__ err, int J, const doub
     if (threadIdx.x == 0) *out = s[0] * inv_norm[0];
 }
 
-// A = sqrt(max(I, 0)) with DC moved from the centre to index 0, stored column-major per
-// position (amp[j][kx][ky]); also sum of A^2 per position.
+// A = sqrt(max(I, 0)) with DC moved from the centre to index 0, stored per position column by
+// column (amp[j][kx][...]).  Within a column the order is ky (R = 0) or, for the N = 256
+// kernel (R = 16), the order its FFT groups consume: thread t's targets ky = t + 16 k2 are
+// contiguous (index t * 16 + k2).  Also the sum of A^2 per position.
 __global__ void __launch_bounds__(kThreads) k_amplitudes(const float *__restrict__ fused, float *__restrict__ amp,
-                                                         double *__restrict__ a2, int N) {
+                                                         double *__restrict__ a2, int N, int R) {
     __shared__ double s[kThreads / 32];
     const int j = blockIdx.x;
     const size_t NN = (size_t)N * N;
     const int h = N / 2;
     double acc = 0.0;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int kx = i / N, ky = i % N;            // destination (column-major)
+        const int kx = i / N, w = i % N;             // destination column kx, slot w
+        const int ky = R ? (w / R) + R * (w % R) : w;
         const int sy = (ky + h) % N, sx = (kx + h) % N;
         const float v = sqrtf(fmaxf(fused[(size_t)j * NN + (size_t)sy * N + sx], 0.f));
         amp[(size_t)j * NN + i] = v;
@@ -388,6 +603,9 @@ struct ptycho_ctx {
     int err_cap = 0;
     int *d_tstart = nullptr, *d_tlist = nullptr;
     int ntx = 0, ntiles = 0;
+    int *d_status = nullptr;
+    TmaMaps tm;
+    bool exit_tma = false;
     int grid_exit = 0, nchunk = 0, per_chunk = 0, nqt = 0, nred = 0;
     size_t exit_smem = 0;
     // timing
@@ -413,11 +631,89 @@ void free_ctx(ptycho_ctx *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
-                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist};
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int tensor_map_encoder(EncodeTiledFn *fn) {
+    static EncodeTiledFn cached = nullptr;
+    if (!cached) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        PM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p)
+            return pm::fail(PTYCHO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        cached = (EncodeTiledFn)p;
+    }
+    *fn = cached;
+    return PTYCHO_OK;
+}
+
+// Row-major 2-D tensor [outer][inner] of `esize`-byte elements, box {box_in, box_out}.
+int encode_2d(CUtensorMap *m, void *addr, CUtensorMapDataType dt, size_t esize, uint64_t inner, uint64_t outer,
+              uint32_t box_in, uint32_t box_out, CUtensorMapSwizzle sw) {
+    EncodeTiledFn enc;
+    int rc = tensor_map_encoder(&enc);
+    if (rc) return rc;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * esize};
+    const cuuint32_t box[2] = {box_in, box_out};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, dt, 2, addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return pm::fail(PTYCHO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PTYCHO_OK;
+}
+
+int setup_exit_tma(ptycho_ctx *h) {
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem));
+    int dev = 0, sms = 0, per_sm = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave_tma, kTmaThreads, kTmaSmem));
+    if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
+    h->exit_smem = kTmaSmem;
+    h->exit_tma = true;
+    h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
+    return PTYCHO_OK;
+}
+
+// Tensor maps of the TMA kernel; called once the buffers exist.
+int encode_exit_tma(ptycho_ctx *h) {
+    const uint64_t N = (uint64_t)h->N;
+    const CUtensorMapDataType c64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;    // one complex64 = 8 bytes
+    int rc;
+    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N, 256, kTmaBatch, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = encode_2d(&h->tm.slot_r, h->d_slot, c64, 8, N, N * h->grid_exit, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B)))
+        return rc;
+    if ((rc = encode_2d(&h->tm.slot_c, h->d_slot, c64, 8, N, N * h->grid_exit, 256, kTmaBatch,
+                        CU_TENSOR_MAP_SWIZZLE_NONE)))
+        return rc;
+    if ((rc = encode_2d(&h->tm.psi_c, h->d_psi, c64, 8, N, N * h->J, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, N * h->J, 256, kTmaBatch, CU_TENSOR_MAP_SWIZZLE_NONE)))
+        return rc;
+    return encode_2d(&h->tm.psi_w, h->d_psi, c64, 8, N, N * h->J, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+int launch_exit_tma(ptycho_ctx *h) {
+    TmaArgs a;
+    a.obj = h->d_obj;
+    a.amp = h->d_amp;
+    a.pos = h->d_pos;
+    a.err = h->d_err_pos;
+    a.status = h->d_status;
+    a.M = h->M;
+    a.J = h->J;
+    k_exit_wave_tma<<<h->grid_exit, kTmaThreads, h->exit_smem, h->st>>>(a, h->tm);
+    PM_LAUNCHED("k_exit_wave_tma");
+    return PTYCHO_OK;
 }
 
 template <int R>
@@ -430,23 +726,41 @@ int setup_exit_kernel(ptycho_ctx *h) {
     PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<R>, kThreads, smem));
     if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "exit-wave kernel cannot be resident (smem %zu)", smem);
     h->exit_smem = smem;
+    h->exit_tma = false;
     h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
     return PTYCHO_OK;
 }
 
 template <int R>
-void launch_exit(ptycho_ctx *h) {
+int launch_exit(ptycho_ctx *h) {
     ExitArgs a;
     a.obj = h->d_obj;
     a.probe = h->d_probe;
     a.amp = h->d_amp;
     a.pos = h->d_pos;
     a.psi = h->d_psi;
-    a.slot = h->d_slot;
     a.err = h->d_err_pos;
     a.M = h->M;
     a.J = h->J;
     k_exit_wave<R><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    PM_LAUNCHED("k_exit_wave");
+    return PTYCHO_OK;
+}
+
+int setup_exit(ptycho_ctx *h) {
+    switch (h->R) {
+        case 4: return setup_exit_kernel<4>(h);
+        case 8: return setup_exit_kernel<8>(h);
+        default: return setup_exit_tma(h);
+    }
+}
+
+int launch_exit_any(ptycho_ctx *h) {
+    switch (h->R) {
+        case 4: return launch_exit<4>(h);
+        case 8: return launch_exit<8>(h);
+        default: return launch_exit_tma(h);
+    }
 }
 
 int stage_begin(ptycho_ctx *h, int s, size_t idx) {
@@ -467,12 +781,7 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     int rc;
     // exit waves
     if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
-    switch (h->R) {
-        case 4: launch_exit<4>(h); break;
-        case 8: launch_exit<8>(h); break;
-        default: launch_exit<16>(h); break;
-    }
-    PM_LAUNCHED("k_exit_wave");
+    if ((rc = launch_exit_any(h))) return rc;
     if ((rc = stage_end(h, ST_EXIT, ev_base + 0, 1))) return rc;
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
@@ -570,16 +879,13 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->nchunk = (J + h->per_chunk - 1) / h->per_chunk;
     h->nred = (int)((NN + kThreads - 1) / kThreads);
 
-    switch (R) {
-        case 4: rc = setup_exit_kernel<4>(h); break;
-        case 8: rc = setup_exit_kernel<8>(h); break;
-        default: rc = setup_exit_kernel<16>(h); break;
-    }
+    rc = setup_exit(h);
     if (!rc) rc = dalloc(&h->d_pos, J);
     if (!rc) rc = dalloc(&h->d_obj, MM);
     if (!rc) rc = dalloc(&h->d_probe, NN);
     if (!rc) rc = dalloc(&h->d_psi, (size_t)J * NN);
-    if (!rc) rc = dalloc(&h->d_slot, (size_t)h->grid_exit * NN);
+    if (!rc && h->exit_tma) rc = dalloc(&h->d_slot, (size_t)h->grid_exit * NN);
+    if (!rc) rc = dalloc(&h->d_status, 1);
     if (!rc) rc = dalloc(&h->d_num_o, MM);
     if (!rc) rc = dalloc(&h->d_den_o, MM);
     if (!rc) rc = dalloc(&h->d_tile_max, h->ntiles);
@@ -589,11 +895,12 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_pden, (size_t)h->nchunk * NN);
     if (!rc) rc = dalloc(&h->d_pmax, h->nred);
     if (!rc) rc = dalloc(&h->d_amp, (size_t)J * NN);
-    if (!rc) rc = dalloc(&h->d_err_pos, J);
+    if (!rc) rc = dalloc(&h->d_err_pos, (size_t)J);
     if (!rc) rc = dalloc(&h->d_a2, J);
     if (!rc) rc = dalloc(&h->d_inv_norm, 1);
     if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
     if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
+    if (!rc && h->exit_tma) rc = encode_exit_tma(h);
     if (rc) { free_ctx(h); return rc; }
     auto fail_cuda = [&](cudaError_t e, const char *what) {
         int r = pm::cuda_fail(e, what);
@@ -612,7 +919,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         return fail_cuda(e, "copy tile lists");
     if ((rc = copy_in_complex(h->d_obj, d->obj0, MM, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
     if ((rc = copy_in_complex(h->d_probe, d->probe0, NN, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
-    k_amplitudes<<<J, kThreads, 0, h->st>>>(d->d_fused, h->d_amp, h->d_a2, N);
+    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st))) return fail_cuda(e, "clear status");
+    k_amplitudes<<<J, kThreads, 0, h->st>>>(d->d_fused, h->d_amp, h->d_a2, N, h->exit_tma ? 16 : 0);
     if ((e = cudaGetLastError())) return fail_cuda(e, "k_amplitudes");
     k_inv_norm<<<1, kThreads, 0, h->st>>>(h->d_a2, J, h->d_inv_norm);
     if ((e = cudaGetLastError())) return fail_cuda(e, "k_inv_norm");
@@ -660,8 +968,11 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
             }
     }
     if (h_err) {
+        int status = 0;
         PM_CUDA(cudaMemcpyAsync(h_err, h->d_err, (size_t)n_iter * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        PM_CUDA(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
         PM_CUDA(cudaStreamSynchronize(h->st));
+        if (status) return pm::fail(PTYCHO_ETIMEDOUT, "ptycho_iterate: a bounded device wait gave up");
         for (int i = 0; i < n_iter; ++i)
             if (!std::isfinite(h_err[i]))
                 return pm::fail(PTYCHO_ENONFINITE, "ptycho_iterate: error of iteration %d is not finite", i);
