@@ -32,8 +32,8 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kOT = 32;          // object tile side of the gather
-constexpr int kQT = 32;          // probe tile side of the probe partial sums
+constexpr int kTW = 32;          // tile width (columns) of the object gather and probe sums
+constexpr int kTR = 8;           // tile height (rows): one register per row and lane
 
 enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
 
@@ -372,55 +372,89 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     }
 }
 
-// Owner-computes object numerator and denominator, one 32 x 32 tile per block.
+// Adds each warp's kTR x 32 register tile into a shared tile, warp by warp in a fixed order
+// (deterministic sums); afterwards the block holds the tile's totals in s_num / s_den / s_hit.
+__device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const float (&dn)[kTR], unsigned hit,
+                                              float2 (*s_num)[kTW], float (*s_den)[kTW], unsigned *s_hit) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (warp == w) {
+#pragma unroll
+            for (int r = 0; r < kTR; ++r) {
+                if (w == 0) {
+                    s_num[r][lane] = acc[r];
+                    s_den[r][lane] = dn[r];
+                } else {
+                    s_num[r][lane] = cadd(s_num[r][lane], acc[r]);
+                    s_den[r][lane] += dn[r];
+                }
+            }
+            s_hit[lane] = (w == 0) ? hit : (s_hit[lane] | hit);
+        }
+        __syncthreads();
+    }
+}
+
+// Owner-computes object numerator and denominator, one kTR x 32 object tile per block.
+// Warp w takes every 8th position of the tile's (ascending) list; lane = tile column, and
+// each lane keeps its column's kTR pixels in registers.
 __global__ void __launch_bounds__(kThreads) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
     const int *__restrict__ tstart, const int *__restrict__ tlist, float2 *__restrict__ num,
     float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx) {
+    __shared__ float2 s_num[kTR][kTW];
+    __shared__ float s_den[kTR][kTW];
+    __shared__ unsigned s_hit[kTW];
     __shared__ float s_max[kThreads / 32];
     const int tile = blockIdx.x;
-    const int ty0 = (tile / ntx) * kOT, tx0 = (tile % ntx) * kOT;
-    const int tx = threadIdx.x % kOT, tyb = threadIdx.x / kOT;   // 8 row groups
-    constexpr int PER = kOT / (kThreads / kOT);                  // 4 pixels per thread
-    float2 acc[PER];
-    float dn[PER];
-    bool hit[PER];
+    const int ty0 = (tile / ntx) * kTR, tx0 = (tile % ntx) * kTW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 acc[kTR];
+    float dn[kTR];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) { acc[q] = make_float2(0.f, 0.f); dn[q] = 0.f; hit[q] = false; }
-    const int px = tx0 + tx;
+    for (int r = 0; r < kTR; ++r) { acc[r] = make_float2(0.f, 0.f); dn[r] = 0.f; }
+    unsigned hit = 0u;
     const size_t NN = (size_t)N * N;
-    for (int e = tstart[tile]; e < tstart[tile + 1]; ++e) {
-        const int j = tlist[e];
-        const int2 pj = pos[j];
-        const int lx = px - pj.y;
-        if (lx < 0 || lx >= N) continue;
+    const int e0 = tstart[tile] + warp, e1 = tstart[tile + 1];
+    int jn = e0 < e1 ? tlist[e0] : 0;
+    int2 pn = e0 < e1 ? pos[jn] : make_int2(0, 0);
+    for (int e = e0; e < e1; e += kThreads / 32) {
+        const int2 pj = pn;
+        const int j = jn;
+        if (e + kThreads / 32 < e1) {                    // prefetch the warp's next position
+            jn = tlist[e + kThreads / 32];
+            pn = pos[jn];
+        }
+        const int lx = tx0 + lane - pj.y;
+        const bool okx = lx >= 0 && lx < N;
         const float2 *psi_j = psi + (size_t)j * NN;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int ly = ty0 + tyb + q * (kThreads / kOT) - pj.x;
-            if (ly >= 0 && ly < N) {
+        for (int r = 0; r < kTR; ++r) {
+            const int ly = ty0 + r - pj.x;
+            if (okx && ly >= 0 && ly < N) {
                 const float2 p = __ldg(probe + ly * N + lx);
                 const float2 v = __ldg(psi_j + (size_t)ly * N + lx);
-                const float2 pv = cmulc(p, v);
-                acc[q] = cadd(acc[q], pv);
-                dn[q] += cabs2(p);
-                hit[q] = true;
+                acc[r] = cadd(acc[r], cmulc(p, v));
+                dn[r] += cabs2(p);
+                hit |= 1u << r;
             }
         }
     }
+    combine_warps(acc, dn, hit, s_num, s_den, s_hit);
     float mx = 0.f;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int py = ty0 + tyb + q * (kThreads / kOT);
+    if (threadIdx.x < kTR * kTW) {
+        const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
+        const int py = ty0 + r, px = tx0 + c;
         if (py < M && px < M) {
-            num[(size_t)py * M + px] = acc[q];
-            den[(size_t)py * M + px] = hit[q] ? dn[q] : -1.0f;   // -1: outside every patch
-            mx = fmaxf(mx, dn[q]);
+            const float d = s_den[r][c];
+            num[(size_t)py * M + px] = s_num[r][c];
+            den[(size_t)py * M + px] = ((s_hit[c] >> r) & 1u) ? d : -1.0f;   // -1: outside every patch
+            mx = d;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    if (lane == 0) s_max[warp] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         float m = 0.f;
@@ -457,44 +491,50 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
     }
 }
 
-// Probe partial sums: block (q tile, chunk of positions) -> partial[chunk][q].
+// Probe partial sums: block (kTR x 32 probe tile, chunk of positions) -> partial[chunk][q].
+// Warp w takes every 8th position of the chunk; lane = tile column, kTR rows in registers.
 __global__ void __launch_bounds__(kThreads) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
     float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk) {
-    const int nqx = (N + kQT - 1) / kQT;
+    __shared__ float2 s_num[kTR][kTW];
+    __shared__ float s_den[kTR][kTW];
+    __shared__ unsigned s_hit[kTW];
+    const int nqx = (N + kTW - 1) / kTW;
     const int qt = blockIdx.x, chunk = blockIdx.y;
-    const int qy0 = (qt / nqx) * kQT, qx0 = (qt % nqx) * kQT;
-    const int tx = threadIdx.x % kQT, tyb = threadIdx.x / kQT;
-    constexpr int PER = kQT / (kThreads / kQT);
-    const int qx = qx0 + tx;
-    float2 acc[PER];
-    float dn[PER];
+    const int qy0 = (qt / nqx) * kTR, qx0 = (qt % nqx) * kTW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int qx = qx0 + lane;
+    float2 acc[kTR];
+    float dn[kTR];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) { acc[q] = make_float2(0.f, 0.f); dn[q] = 0.f; }
+    for (int r = 0; r < kTR; ++r) { acc[r] = make_float2(0.f, 0.f); dn[r] = 0.f; }
     const int j0 = chunk * per_chunk, j1 = min(J, j0 + per_chunk);
     const size_t NN = (size_t)N * N;
-    if (qx < N) {
-        for (int j = j0; j < j1; ++j) {
-            const int2 pj = pos[j];
-            const float2 *psi_j = psi + (size_t)j * NN;
+    int2 pn = (j0 + warp < j1) ? pos[j0 + warp] : make_int2(0, 0);
+    for (int j = j0 + warp; j < j1; j += kThreads / 32) {
+        const int2 pj = pn;
+        if (j + kThreads / 32 < j1) pn = pos[j + kThreads / 32];
+        const float2 *psi_j = psi + (size_t)j * NN;
+        if (qx < N) {
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int qy = qy0 + tyb + q * (kThreads / kQT);
+            for (int r = 0; r < kTR; ++r) {
+                const int qy = qy0 + r;
                 if (qy < N) {
                     const float2 o = __ldg(obj + (size_t)(pj.x + qy) * M + pj.y + qx);
                     const float2 v = __ldg(psi_j + (size_t)qy * N + qx);
-                    acc[q] = cadd(acc[q], cmulc(o, v));
-                    dn[q] += cabs2(o);
+                    acc[r] = cadd(acc[r], cmulc(o, v));
+                    dn[r] += cabs2(o);
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int qy = qy0 + tyb + q * (kThreads / kQT);
-            if (qy < N) {
-                pnum[(size_t)chunk * NN + (size_t)qy * N + qx] = acc[q];
-                pden[(size_t)chunk * NN + (size_t)qy * N + qx] = dn[q];
-            }
+    }
+    combine_warps(acc, dn, 0u, s_num, s_den, s_hit);
+    if (threadIdx.x < kTR * kTW) {
+        const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
+        const int y = qy0 + r, x = qx0 + c;
+        if (y < N && x < N) {
+            pnum[(size_t)chunk * NN + (size_t)y * N + x] = s_num[r][c];
+            pden[(size_t)chunk * NN + (size_t)y * N + x] = s_den[r][c];
         }
     }
 }
@@ -857,14 +897,15 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     int rc = PTYCHO_OK;
     const size_t NN = (size_t)N * N, MM = (size_t)M * M;
     // object tiles and their position lists (ascending j)
-    h->ntx = (M + kOT - 1) / kOT;
-    h->ntiles = h->ntx * h->ntx;
+    h->ntx = (M + kTW - 1) / kTW;
+    const int nty = (M + kTR - 1) / kTR;
+    h->ntiles = h->ntx * nty;
     std::vector<int> tstart(h->ntiles + 1, 0), tlist;
     {
         std::vector<std::vector<int>> lists(h->ntiles);
         for (int j = 0; j < J; ++j) {
             const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
-            const int ty0 = y / kOT, ty1 = (y + N - 1) / kOT, tx0 = x / kOT, tx1 = (x + N - 1) / kOT;
+            const int ty0 = y / kTR, ty1 = (y + N - 1) / kTR, tx0 = x / kTW, tx1 = (x + N - 1) / kTW;
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx) lists[ty * h->ntx + tx].push_back(j);
         }
@@ -873,9 +914,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         for (int t = 0; t < h->ntiles; ++t) tlist.insert(tlist.end(), lists[t].begin(), lists[t].end());
     }
     // probe partial-sum layout
-    h->nqt = ((N + kQT - 1) / kQT) * ((N + kQT - 1) / kQT);
-    h->nchunk = std::max(1, std::min(J, (148 * 8 + h->nqt - 1) / h->nqt));
-    h->per_chunk = (J + h->nchunk - 1) / h->nchunk;
+    h->nqt = ((N + kTW - 1) / kTW) * ((N + kTR - 1) / kTR);
+    h->per_chunk = 128;                                  // 16 positions per warp
     h->nchunk = (J + h->per_chunk - 1) / h->per_chunk;
     h->nred = (int)((NN + kThreads - 1) / kThreads);
 
