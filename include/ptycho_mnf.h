@@ -73,6 +73,25 @@ typedef struct {
 int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
                const fuse_params *p, float *d_fused, void *cuda_stream);
 
+/*
+ * fuse_stack_noalloc -- the same fusion as fuse_stack, for callers that cannot allocate device
+ * memory (for example while another framework's caching allocator holds nearly all of it, or
+ * inside a latency-critical loop where an allocation, which can synchronise the device, is
+ * not acceptable).  The paper has no counterpart: this is a deployment variant of the
+ * library.  Arguments, layouts and results are those of fuse_stack.
+ *   - Scratch lives in a 16 MiB array compiled into the library: every GPU that loads the
+ *     library holds it until the process exits.  The call allocates and frees nothing.
+ *   - Positions are processed in chunks that fit the array; a configuration whose single
+ *     position needs more than 16 MiB of scratch (about 4 (2K + 1) N^2 / 3 bytes) is rejected
+ *     with PTYCHO_EINVAL and a message naming the sizes.
+ *   - The first call on a device (with that device current) looks up the array's device
+ *     address; make that first call before any stream capture.
+ *   - All calls share the array: calls whose work may overlap on the GPU (different streams,
+ *     other host threads) race on it and must be serialised by the caller.
+ */
+int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                       const fuse_params *p, float *d_fused, void *cuda_stream);
+
 typedef struct ptycho_ctx *ptycho_handle;
 
 typedef struct {

@@ -24,7 +24,7 @@ PTYCHO_ETIMEDOUT = -5
 BASE_MODES = {"mean": 0, "sum": 1, "weighted": 2}
 DOMAINS = {"radiance": 0, "raw": 1}
 
-EXPORTS = ("fuse_stack", "ptycho_init", "ptycho_iterate", "ptycho_get_object", "ptycho_get_probe",
+EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "ptycho_init", "ptycho_iterate", "ptycho_get_object", "ptycho_get_probe",
            "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
 
 
@@ -69,6 +69,8 @@ def lib() -> ctypes.CDLL:
     L.fuse_stack.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float),
                              ctypes.POINTER(FuseParamsC), vp, vp]
     L.fuse_stack.restype = ci
+    L.fuse_stack_noalloc.argtypes = L.fuse_stack.argtypes
+    L.fuse_stack_noalloc.restype = ci
     L.ptycho_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PtychoDescC)]
     L.ptycho_init.restype = ci
     L.ptycho_iterate.argtypes = [vp, ci, ctypes.POINTER(cd)]
@@ -127,6 +129,21 @@ def fuse_stack(raw, times, params: FuseParamsC, out=None, stream=None):
     t = (ctypes.c_float * K)(*[float(x) for x in times])
     _check(lib().fuse_stack(ctypes.c_void_p(raw.data_ptr()), J, K, N, t, ctypes.byref(params),
                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def fuse_stack_noalloc(raw, times, params: FuseParamsC, out, stream=None):
+    """Allocation-free fusion (scratch in the library's static 16 MiB device array).  ``out``
+    must be preallocated: a contiguous float32 CUDA tensor [J][N][N]."""
+    import torch
+    if raw.dtype != torch.uint16 or not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw must be a contiguous torch.uint16 CUDA tensor [J][K][N][N]")
+    J, K, N, _ = raw.shape
+    if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (J, N, N):
+        raise ValueError("out must be a contiguous float32 tensor [J][N][N]")
+    t = (ctypes.c_float * K)(*[float(x) for x in times])
+    _check(lib().fuse_stack_noalloc(ctypes.c_void_p(raw.data_ptr()), J, K, N, t, ctypes.byref(params),
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
     return out
 
 

@@ -18,6 +18,7 @@
 // 2 w_G per axis, reflect-101 borders on the grid being filtered.  All arithmetic is FP32.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -408,6 +409,72 @@ extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const floa
     if (scratch) {
         cudaError_t e = cudaFreeAsync(scratch, st);
         if (rc == PTYCHO_OK && e != cudaSuccess) return pm::cuda_fail(e, "cudaFreeAsync");
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of fuse_stack.
+//
+// Some callers cannot call cudaMalloc or any other device allocator: for example code that
+// runs while another framework's caching allocator has reserved nearly all device memory, or
+// a latency-critical loop in which an allocation (which can synchronise the device) is not
+// acceptable.  fuse_stack_noalloc runs the same kernels with its scratch in a fixed,
+// file-scope device array instead of stream-ordered allocations.
+//
+// The array below is part of the library image: every GPU that loads the library holds it
+// until the process exits.  Its host-side name is only a stand-in for the symbol, so the
+// device address is looked up with cudaGetSymbolAddress, once per device, on the first call
+// made with that device current; that first call should therefore happen before any stream
+// capture.  All calls share the array and it keeps the previous call's contents (every element
+// a call reads is written by that call first, so nothing needs clearing); calls whose work
+// overlaps on the GPU race on it.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
+constexpr int kMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) float g_fuse_scratch[kNoAllocScratchBytes / sizeof(float)];
+
+static int noalloc_scratch(float **out) {
+    static std::mutex mu;
+    static float *by_device[kMaxDevices] = {};
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return pm::fail(PTYCHO_EINVAL, "fuse_stack_noalloc: device %d unsupported", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!by_device[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fuse_scratch);
+        if (e != cudaSuccess) return pm::cuda_fail(e, "cudaGetSymbolAddress(fusion scratch)");
+        by_device[dev] = (float *)p;
+    }
+    *out = by_device[dev];
+    return PTYCHO_OK;
+}
+
+extern "C" int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                                  const fuse_params *p, float *d_fused, void *cuda_stream) {
+    FuseDev f;
+    int rc = pm::validate_fuse(d_raw, J, K, N, h_t, p, d_fused, &f);
+    if (rc != PTYCHO_OK) return rc;
+    const size_t per_pos = scratch_floats_per_position(K, N, f.L);
+    const size_t cap = kNoAllocScratchBytes / sizeof(float);
+    if (per_pos > cap)
+        return pm::fail(PTYCHO_EINVAL,
+                        "fuse_stack_noalloc: one position needs %zu bytes of scratch (N = %d, K = %d, L = %d), "
+                        "more than the %zu-byte static buffer",
+                        per_pos * sizeof(float), N, K, f.L, kNoAllocScratchBytes);
+    if (J == 0) return PTYCHO_OK;
+    float *scratch = nullptr;
+    if (per_pos > 0 && (rc = noalloc_scratch(&scratch))) return rc;
+    int chunk = per_pos > 0 ? (int)std::min<size_t>((size_t)J, cap / per_pos) : J;
+    chunk = std::max(1, std::min(chunk, 65535 / K));
+    const size_t NN = (size_t)N * N;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    for (int j0 = 0; j0 < J && rc == PTYCHO_OK; j0 += chunk) {
+        const int jn = std::min(chunk, J - j0);
+        rc = pm::fuse_dispatch(d_raw + (size_t)j0 * K * NN, jn, K, N, f, d_fused + (size_t)j0 * NN, scratch, st);
     }
     return rc;
 }
