@@ -372,41 +372,48 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     }
 }
 
-// Adds each warp's kTR x 32 register tile into a shared tile, warp by warp in a fixed order
-// (deterministic sums); afterwards the block holds the tile's totals in s_num / s_den / s_hit.
+// Each warp parks its kTR x 32 register tile in shared memory; after one barrier, thread
+// (r, c) sums the 8 warps' values for pixel (r, c) in warp order (deterministic).
+struct WarpTiles {
+    float2 num[kThreads / 32][kTR][kTW];
+    float den[kThreads / 32][kTR][kTW];
+    unsigned hit[kThreads / 32][kTW];
+};
+
 __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const float (&dn)[kTR], unsigned hit,
-                                              float2 (*s_num)[kTW], float (*s_den)[kTW], unsigned *s_hit) {
+                                              WarpTiles &wt, float2 &num, float &den, bool &covered) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        if (warp == w) {
 #pragma unroll
-            for (int r = 0; r < kTR; ++r) {
-                if (w == 0) {
-                    s_num[r][lane] = acc[r];
-                    s_den[r][lane] = dn[r];
-                } else {
-                    s_num[r][lane] = cadd(s_num[r][lane], acc[r]);
-                    s_den[r][lane] += dn[r];
-                }
-            }
-            s_hit[lane] = (w == 0) ? hit : (s_hit[lane] | hit);
+    for (int r = 0; r < kTR; ++r) {
+        wt.num[warp][r][lane] = acc[r];
+        wt.den[warp][r][lane] = dn[r];
+    }
+    wt.hit[warp][lane] = hit;
+    __syncthreads();
+    num = make_float2(0.f, 0.f);
+    den = 0.f;
+    covered = false;
+    if (threadIdx.x < kTR * kTW) {
+        const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            num = cadd(num, wt.num[w][r][c]);
+            den += wt.den[w][r][c];
+            covered |= ((wt.hit[w][c] >> r) & 1u) != 0u;
         }
-        __syncthreads();
     }
 }
 
 // Owner-computes object numerator and denominator, one kTR x 32 object tile per block.
 // Warp w takes every 8th position of the tile's (ascending) list; lane = tile column, and
 // each lane keeps its column's kTR pixels in registers.
-__global__ void __launch_bounds__(kThreads) k_object_gather(
+__global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
-    const int *__restrict__ tstart, const int *__restrict__ tlist, float2 *__restrict__ num,
-    float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx) {
-    __shared__ float2 s_num[kTR][kTW];
-    __shared__ float s_den[kTR][kTW];
-    __shared__ unsigned s_hit[kTW];
+    const int *__restrict__ tstart, const int4 *__restrict__ tlist, const int *__restrict__ torder,
+    float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx) {
+    __shared__ WarpTiles wt;
     __shared__ float s_max[kThreads / 32];
-    const int tile = blockIdx.x;
+    const int tile = torder[blockIdx.x];              // longest position lists first
     const int ty0 = (tile / ntx) * kTR, tx0 = (tile % ntx) * kTW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float2 acc[kTR];
@@ -416,40 +423,46 @@ __global__ void __launch_bounds__(kThreads) k_object_gather(
     unsigned hit = 0u;
     const size_t NN = (size_t)N * N;
     const int e0 = tstart[tile] + warp, e1 = tstart[tile + 1];
-    int jn = e0 < e1 ? tlist[e0] : 0;
-    int2 pn = e0 < e1 ? pos[jn] : make_int2(0, 0);
+    int4 en = e0 < e1 ? tlist[e0] : make_int4(0, 0, 0, 0);    // (j, y, x, -)
     for (int e = e0; e < e1; e += kThreads / 32) {
-        const int2 pj = pn;
-        const int j = jn;
-        if (e + kThreads / 32 < e1) {                    // prefetch the warp's next position
-            jn = tlist[e + kThreads / 32];
-            pn = pos[jn];
-        }
+        const int2 pj = make_int2(en.y, en.z);
+        const int j = en.x;
+        if (e + kThreads / 32 < e1) en = tlist[e + kThreads / 32];   // prefetch the next entry
         const int lx = tx0 + lane - pj.y;
         const bool okx = lx >= 0 && lx < N;
+        const int lxc = min(max(lx, 0), N - 1);
         const float2 *psi_j = psi + (size_t)j * NN;
+        // All loads first, from clamped (always valid) addresses, so they are in flight
+        // together; pixels outside the patch are masked out afterwards.
+        float2 pv[kTR], vv[kTR];
+#pragma unroll
+        for (int r = 0; r < kTR; ++r) {
+            const int lyc = min(max(ty0 + r - pj.x, 0), N - 1);
+            pv[r] = __ldg(probe + lyc * N + lxc);
+            vv[r] = __ldg(psi_j + (size_t)lyc * N + lxc);
+        }
 #pragma unroll
         for (int r = 0; r < kTR; ++r) {
             const int ly = ty0 + r - pj.x;
             if (okx && ly >= 0 && ly < N) {
-                const float2 p = __ldg(probe + ly * N + lx);
-                const float2 v = __ldg(psi_j + (size_t)ly * N + lx);
-                acc[r] = cadd(acc[r], cmulc(p, v));
-                dn[r] += cabs2(p);
+                acc[r] = cadd(acc[r], cmulc(pv[r], vv[r]));
+                dn[r] += cabs2(pv[r]);
                 hit |= 1u << r;
             }
         }
     }
-    combine_warps(acc, dn, hit, s_num, s_den, s_hit);
+    float2 tnum;
+    float tden;
+    bool covered;
+    combine_warps(acc, dn, hit, wt, tnum, tden, covered);
     float mx = 0.f;
     if (threadIdx.x < kTR * kTW) {
         const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
         const int py = ty0 + r, px = tx0 + c;
         if (py < M && px < M) {
-            const float d = s_den[r][c];
-            num[(size_t)py * M + px] = s_num[r][c];
-            den[(size_t)py * M + px] = ((s_hit[c] >> r) & 1u) ? d : -1.0f;   // -1: outside every patch
-            mx = d;
+            num[(size_t)py * M + px] = tnum;
+            den[(size_t)py * M + px] = covered ? tden : -1.0f;       // -1: outside every patch
+            mx = tden;
         }
     }
 #pragma unroll
@@ -493,12 +506,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
 
 // Probe partial sums: block (kTR x 32 probe tile, chunk of positions) -> partial[chunk][q].
 // Warp w takes every 8th position of the chunk; lane = tile column, kTR rows in registers.
-__global__ void __launch_bounds__(kThreads) k_probe_partial(
+__global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
     float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk) {
-    __shared__ float2 s_num[kTR][kTW];
-    __shared__ float s_den[kTR][kTW];
-    __shared__ unsigned s_hit[kTW];
+    __shared__ WarpTiles wt;
     const int nqx = (N + kTW - 1) / kTW;
     const int qt = blockIdx.x, chunk = blockIdx.y;
     const int qy0 = (qt / nqx) * kTR, qx0 = (qt % nqx) * kTW;
@@ -515,26 +526,34 @@ __global__ void __launch_bounds__(kThreads) k_probe_partial(
         const int2 pj = pn;
         if (j + kThreads / 32 < j1) pn = pos[j + kThreads / 32];
         const float2 *psi_j = psi + (size_t)j * NN;
+        const int qxc = min(qx, N - 1);
+        float2 ov[kTR], vv[kTR];
+#pragma unroll
+        for (int r = 0; r < kTR; ++r) {                  // loads first (clamped, always valid)
+            const int qyc = min(qy0 + r, N - 1);
+            ov[r] = __ldg(obj + (size_t)(pj.x + qyc) * M + pj.y + qxc);
+            vv[r] = __ldg(psi_j + (size_t)qyc * N + qxc);
+        }
         if (qx < N) {
 #pragma unroll
             for (int r = 0; r < kTR; ++r) {
-                const int qy = qy0 + r;
-                if (qy < N) {
-                    const float2 o = __ldg(obj + (size_t)(pj.x + qy) * M + pj.y + qx);
-                    const float2 v = __ldg(psi_j + (size_t)qy * N + qx);
-                    acc[r] = cadd(acc[r], cmulc(o, v));
-                    dn[r] += cabs2(o);
+                if (qy0 + r < N) {
+                    acc[r] = cadd(acc[r], cmulc(ov[r], vv[r]));
+                    dn[r] += cabs2(ov[r]);
                 }
             }
         }
     }
-    combine_warps(acc, dn, 0u, s_num, s_den, s_hit);
+    float2 tnum;
+    float tden;
+    bool covered;
+    combine_warps(acc, dn, 0u, wt, tnum, tden, covered);
     if (threadIdx.x < kTR * kTW) {
         const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
         const int y = qy0 + r, x = qx0 + c;
         if (y < N && x < N) {
-            pnum[(size_t)chunk * NN + (size_t)y * N + x] = s_num[r][c];
-            pden[(size_t)chunk * NN + (size_t)y * N + x] = s_den[r][c];
+            pnum[(size_t)chunk * NN + (size_t)y * N + x] = tnum;
+            pden[(size_t)chunk * NN + (size_t)y * N + x] = tden;
         }
     }
 }
@@ -641,7 +660,8 @@ struct ptycho_ctx {
     float *d_tile_max = nullptr, *d_pmax = nullptr;
     double *d_err_pos = nullptr, *d_a2 = nullptr, *d_inv_norm = nullptr, *d_err = nullptr;
     int err_cap = 0;
-    int *d_tstart = nullptr, *d_tlist = nullptr;
+    int *d_tstart = nullptr, *d_torder = nullptr;
+    int4 *d_tlist = nullptr;                              // tile lists: (j, y, x, 0)
     int ntx = 0, ntiles = 0;
     int *d_status = nullptr;
     TmaMaps tm;
@@ -671,7 +691,7 @@ void free_ctx(ptycho_ctx *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
-                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status};
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status, h->d_torder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -826,7 +846,8 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
     k_object_gather<<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
-                                                       h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N, h->ntx);
+                                                       h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max, h->M,
+                                                       h->N, h->ntx);
     PM_LAUNCHED("k_object_gather");
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
@@ -900,7 +921,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->ntx = (M + kTW - 1) / kTW;
     const int nty = (M + kTR - 1) / kTR;
     h->ntiles = h->ntx * nty;
-    std::vector<int> tstart(h->ntiles + 1, 0), tlist;
+    std::vector<int> tstart(h->ntiles + 1, 0), torder;
+    std::vector<int4> tlist;
     {
         std::vector<std::vector<int>> lists(h->ntiles);
         for (int j = 0; j < J; ++j) {
@@ -911,7 +933,12 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         }
         for (int t = 0; t < h->ntiles; ++t) tstart[t + 1] = tstart[t] + (int)lists[t].size();
         tlist.reserve(tstart[h->ntiles]);
-        for (int t = 0; t < h->ntiles; ++t) tlist.insert(tlist.end(), lists[t].begin(), lists[t].end());
+        for (int t = 0; t < h->ntiles; ++t)
+            for (int j : lists[t]) tlist.push_back(make_int4(j, d->h_pos[2 * j], d->h_pos[2 * j + 1], 0));
+        torder.resize(h->ntiles);
+        for (int t = 0; t < h->ntiles; ++t) torder[t] = t;
+        std::stable_sort(torder.begin(), torder.end(),
+                         [&](int a, int b) { return lists[a].size() > lists[b].size(); });
     }
     // probe partial-sum layout
     h->nqt = ((N + kTW - 1) / kTW) * ((N + kTR - 1) / kTR);
@@ -940,6 +967,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_inv_norm, 1);
     if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
     if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
+    if (!rc) rc = dalloc(&h->d_torder, (size_t)h->ntiles);
     if (!rc && h->exit_tma) rc = encode_exit_tma(h);
     if (rc) { free_ctx(h); return rc; }
     auto fail_cuda = [&](cudaError_t e, const char *what) {
@@ -954,8 +982,10 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         return fail_cuda(e, "copy positions");
     if ((e = cudaMemcpyAsync(h->d_tstart, tstart.data(), tstart.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile starts");
+    if ((e = cudaMemcpyAsync(h->d_torder, torder.data(), torder.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy tile order");
     if (!tlist.empty() &&
-        (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
+        (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile lists");
     if ((rc = copy_in_complex(h->d_obj, d->obj0, MM, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
     if ((rc = copy_in_complex(h->d_probe, d->probe0, NN, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
