@@ -188,14 +188,19 @@ struct TmaMaps {
     CUtensorMap psi_w;       // psi, row-major        box {256 c, 16 r}  (stores)
 };
 
-constexpr int kTmaThreads = 512;
-constexpr int kTmaBatch = 32;                                   // rows / columns per batch
-constexpr size_t kTmaBuf = (size_t)kTmaBatch * 256 * sizeof(float2);   // 64 KB
-constexpr size_t kTmaSmem = 1024 /*alignment slack*/ + 3 * kTmaBuf + 256 * sizeof(float2) + 64;
+// Batch = rows or columns per pipeline stage = FFT groups per CTA (16 threads each).  32:
+// one 512-thread CTA per SM; 16: two 256-thread CTAs per SM, each with its own position.
+template <int B>
+__host__ __device__ constexpr size_t tma_buf_bytes() { return (size_t)B * 256 * sizeof(float2); }
+template <int B>
+__host__ __device__ constexpr size_t tma_smem_bytes() { return 1024 /*alignment slack*/ + 3 * tma_buf_bytes<B>() + 256 * sizeof(float2) + 64; }
 
-__global__ void __launch_bounds__(kTmaThreads, 1)
+template <int B>
+__global__ void __launch_bounds__(B * 16, 32 / B)
 k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
-    constexpr int R = 16, N = 256, NB = N / kTmaBatch;
+    constexpr int R = 16, N = 256, NB = N / B;
+    constexpr int kTmaThreads = B * 16, kTmaBatch = B;
+    constexpr size_t kTmaBuf = tma_buf_bytes<B>();
     namespace T = pm::tma;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -206,8 +211,8 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     __shared__ double s_red[kTmaThreads / 32];
 
     const int tid = threadIdx.x;
-    const int t = tid & 15, g = tid >> 4;                        // g in [0, 32)
-    const int h = g >> 4, gl = g & 15;                           // half of the batch, row in it
+    const int t = tid & 15, g = tid >> 4;                        // g in [0, B)
+    const int h = g >> 4, gl = g & 15;                           // 16-wide box of the batch, row in it
     if (tid < 256) {
         double sn, cs;
         sincospi(-2.0 * (double)((tid >> 4) * (tid & 15)) / (double)N, &sn, &cs);
@@ -242,7 +247,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         __syncthreads();
         if (tid == 0) {
             T::store_2d(map, x0, y0, bout);
-            T::store_2d(map, x0 + dx, y0 + dy, bout + 4096);
+            if constexpr (B == 32) T::store_2d(map, x0 + dx, y0 + dy, bout + 4096);
             T::commit();
         }
     };
@@ -666,6 +671,7 @@ struct ptycho_ctx {
     int *d_status = nullptr;
     TmaMaps tm;
     bool exit_tma = false;
+    int tma_batch = 32;
     int grid_exit = 0, nchunk = 0, per_chunk = 0, nqt = 0, nred = 0;
     size_t exit_smem = 0;
     // timing
@@ -732,33 +738,47 @@ int encode_2d(CUtensorMap *m, void *addr, CUtensorMapDataType dt, size_t esize, 
     return PTYCHO_OK;
 }
 
-int setup_exit_tma(ptycho_ctx *h) {
-    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem));
+template <int B>
+int setup_exit_tma_b(ptycho_ctx *h) {
+    const size_t smem = tma_smem_bytes<B>();
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int dev = 0, sms = 0, per_sm = 0;
     PM_CUDA(cudaGetDevice(&dev));
     PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave_tma, kTmaThreads, kTmaSmem));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave_tma<B>, B * 16, smem));
     if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
-    h->exit_smem = kTmaSmem;
+    h->exit_smem = smem;
     h->exit_tma = true;
+    h->tma_batch = B;
     h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
     return PTYCHO_OK;
+}
+
+// Batch size of the N = 256 kernel (16 or 32 rows per stage); PTYCHO_TMA_BATCH overrides.
+int tma_batch_choice() {
+    const char *env = std::getenv("PTYCHO_TMA_BATCH");
+    if (env && std::atoi(env) == 32) return 32;
+    if (env && std::atoi(env) == 16) return 16;
+    return 16;
+}
+
+int setup_exit_tma(ptycho_ctx *h) {
+    return tma_batch_choice() == 32 ? setup_exit_tma_b<32>(h) : setup_exit_tma_b<16>(h);
 }
 
 // Tensor maps of the TMA kernel; called once the buffers exist.
 int encode_exit_tma(ptycho_ctx *h) {
     const uint64_t N = (uint64_t)h->N;
+    const uint32_t B = (uint32_t)h->tma_batch;
     const CUtensorMapDataType c64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;    // one complex64 = 8 bytes
     int rc;
-    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N, 256, kTmaBatch, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
     if ((rc = encode_2d(&h->tm.slot_r, h->d_slot, c64, 8, N, N * h->grid_exit, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B)))
         return rc;
-    if ((rc = encode_2d(&h->tm.slot_c, h->d_slot, c64, 8, N, N * h->grid_exit, 256, kTmaBatch,
-                        CU_TENSOR_MAP_SWIZZLE_NONE)))
+    if ((rc = encode_2d(&h->tm.slot_c, h->d_slot, c64, 8, N, N * h->grid_exit, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE)))
         return rc;
     if ((rc = encode_2d(&h->tm.psi_c, h->d_psi, c64, 8, N, N * h->J, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
-    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, N * h->J, 256, kTmaBatch, CU_TENSOR_MAP_SWIZZLE_NONE)))
-        return rc;
+    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, N * h->J, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
     return encode_2d(&h->tm.psi_w, h->d_psi, c64, 8, N, N * h->J, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
@@ -771,7 +791,10 @@ int launch_exit_tma(ptycho_ctx *h) {
     a.status = h->d_status;
     a.M = h->M;
     a.J = h->J;
-    k_exit_wave_tma<<<h->grid_exit, kTmaThreads, h->exit_smem, h->st>>>(a, h->tm);
+    if (h->tma_batch == 32)
+        k_exit_wave_tma<32><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else
+        k_exit_wave_tma<16><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     PM_LAUNCHED("k_exit_wave_tma");
     return PTYCHO_OK;
 }
