@@ -45,6 +45,8 @@ def parse():
                     help="use only the first N scan positions (profiling runs only; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-nrmse", action="store_true")
+    ap.add_argument("--nrmse-iters", type=int, default=400)
     return ap.parse_args()
 
 
@@ -287,6 +289,11 @@ def run_ours(args, world, rank, local):
     fuse_n = fuse_launches(cfg.levels)
     launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
 
+    conv = None
+    if rank == 0 and not args.no_nrmse:
+        conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
+                              probe_update_start=pus) for pus in (0, 10 ** 9)]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -305,12 +312,69 @@ def run_ours(args, world, rank, local):
         "stage_ms_per_step": {n: round(float(m) / args.steps, 3) for n, m in zip(names, stage_ms)},
         "dominant_stage": names[dom],
         "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "time_to_nrmse": conv,
         "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- convergence
+def illuminated_mask(probe, pos, M):
+    N = probe.shape[0]
+    den = np.zeros((M, M))
+    p2 = np.abs(probe) ** 2
+    for y, x in pos:
+        den[y:y + N, x:x + N] += p2
+    return den >= 0.1 * den.max()
+
+
+def nrmse_host(obj, truth, mask):
+    """min over complex c of ||c O - O_true|| / ||O_true|| on the mask (global phase/scale free)."""
+    o = obj[mask].astype(np.complex128)
+    t = truth[mask]
+    c = np.vdot(o, t) / np.vdot(o, o)
+    return float(np.linalg.norm(c * o - t) / np.linalg.norm(t))
+
+
+def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, max_iters, chunk=10,
+                  target=1e-2, probe_update_start=0):
+    """Plain FP32 reconstruction of the benchmarked scan from a flat object with the known probe:
+    NRMSE to the ground truth every `chunk` iterations.  Device time counts the fusion, set-up
+    and iterations (CUDA events), not the NRMSE evaluation."""
+    import torch
+    M = cfg.M
+    mask = illuminated_mask(sc["probe"], pos, M)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.fuse_stack(raw, cfg.times, params, out=fused, stream=stream)
+    h = api.ptycho_init(fused, pos, obj0, probe0, probe_update_start=probe_update_start, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    traj = []
+    obj = np.empty((M, M), np.complex64)
+    done = 0
+    while done < max_iters:
+        e0.record(stream)
+        api.ptycho_iterate(h, chunk, errors=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        done += chunk
+        api.ptycho_get_object(h, obj)
+        traj.append((done, round(t_ms, 2), nrmse_host(obj, sc["obj"], mask)))
+    api.ptycho_destroy(h)
+    floor = min(v for _, _, v in traj)
+    goal = target if floor <= target else 1.05 * floor
+    hit = next((it, ms) for it, ms, v in traj if v <= goal)
+    return {"target": target, "reached_target": floor <= target, "floor": round(floor, 5),
+            "goal_used": round(goal, 5), "iterations": hit[0], "seconds": round(hit[1] / 1e3, 4),
+            "start": "flat object, true probe, " + ("probe updates on" if probe_update_start == 0
+                                                     else "probe fixed"),
+            "trajectory_every_10": [round(v, 5) for _, _, v in traj]}
 
 
 # ----------------------------------------------------------------------------- oracle arm
