@@ -15,12 +15,13 @@ from .mnf import FuseParams, exposure_weights, radiance, blur_down, upsample, \
     gaussian_pyramid, laplacian_pyramid, quantise, mnf_position, mnf_stack
 from .ptycho import fft2u, ifft2u, amplitudes, modulus_projection, reconstruct, \
     iterate_once, exit_wave_update, object_update, probe_update, illumination, nrmse, \
-    fourier_error
+    fourier_error, modes_modulus_projection, iterate_once_modes, reconstruct_modes
 
 __all__ = [
     "FuseParams", "exposure_weights", "radiance", "blur_down", "upsample", "gaussian_pyramid",
     "laplacian_pyramid", "quantise", "mnf_position", "mnf_stack", "fft2u", "ifft2u",
     "amplitudes", "modulus_projection", "reconstruct", "iterate_once", "exit_wave_update",
     "object_update", "probe_update",
-    "illumination", "nrmse", "fourier_error",
+    "illumination", "nrmse", "fourier_error", "modes_modulus_projection", "iterate_once_modes",
+    "reconstruct_modes",
 ]

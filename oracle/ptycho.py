@@ -161,3 +161,83 @@ def nrmse(obj: np.ndarray, truth: np.ndarray, mask: np.ndarray) -> float:
     denom = np.vdot(o, o)
     c = np.vdot(o, t) / denom if abs(denom) > 0 else 0.0
     return float(np.linalg.norm(c * o - t) / np.linalg.norm(t))
+
+
+# ---------------------------------------------------------------------------------------------
+# Mixed-state (broadband) variant: §3.3, Eq. 4 with a discrete spectrum.  The measured intensity
+# is the incoherent sum over probe modes m (one per wavelength, equal spectral weights absorbed
+# into the mode amplitudes) of |F(P_m O_j)|^2; the object is shared (achromatic reading).
+#   Psi_m = F(P_m O_j);  S = sum_m |Psi_m|^2;  e += sum_q (sqrt(S) - A_j)^2
+#   Psi_m' = Psi_m A_j / sqrt(S)            (where S = 0: Psi_0' = A_j, other modes 0)
+#   O <- sum_j sum_m conj(P_m) psi_jm' / (sum_j sum_m |P_m|^2 + alpha_O max)   (covered pixels)
+#   P_m <- sum_j conj(O_j) psi_jm' / (sum_j |O_j|^2 + alpha_P max)             (new object)
+# With one mode every step is the single-mode iteration above.
+
+def modes_modulus_projection(Psi: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Psi: [Q, N, N] mode spectra; returns the projected spectra with sum_m |Psi_m'|^2 = A^2."""
+    S = np.sum(np.abs(Psi) ** 2, axis=0)
+    nz = S > 0
+    scale = np.where(nz, A / np.sqrt(np.where(nz, S, 1.0)), 0.0)
+    out = Psi * scale[None]
+    out[0] = np.where(nz, out[0], A + 0j)
+    return out
+
+
+def iterate_once_modes(obj, probes, pos, A, alpha_O, alpha_P, update_probe: bool):
+    """One full-batch mixed-state iteration.  probes: [Q, N, N].  Returns (obj, probes, error)."""
+    Q, N, _ = probes.shape
+    M = obj.shape[0]
+    J = len(pos)
+    psi_new = np.empty((J, Q, N, N), dtype=np.complex128)
+    err = 0.0
+    for j in range(J):
+        y, x = int(pos[j][0]), int(pos[j][1])
+        oj = obj[y:y + N, x:x + N]
+        Psi = fft2u(probes * oj[None])
+        S = np.sum(np.abs(Psi) ** 2, axis=0)
+        err += float(np.sum((np.sqrt(S) - A[j]) ** 2))
+        psi_new[j] = ifft2u(modes_modulus_projection(Psi, A[j]))
+    num_o = np.zeros((M, M), dtype=np.complex128)
+    den_o = np.zeros((M, M))
+    cover = np.zeros((M, M), dtype=bool)
+    pc = np.conj(probes)
+    p2 = np.sum(np.abs(probes) ** 2, axis=0)
+    for j in range(J):
+        y, x = int(pos[j][0]), int(pos[j][1])
+        num_o[y:y + N, x:x + N] += np.sum(pc * psi_new[j], axis=0)
+        den_o[y:y + N, x:x + N] += p2
+        cover[y:y + N, x:x + N] = True
+    reg = alpha_O * den_o.max()
+    upd = cover & (den_o + reg > 0)
+    obj = np.array(obj, dtype=np.complex128, copy=True)
+    obj[upd] = num_o[upd] / (den_o[upd] + reg)
+    if update_probe:
+        num_p = np.zeros((Q, N, N), dtype=np.complex128)
+        den_p = np.zeros((N, N))
+        for j in range(J):
+            y, x = int(pos[j][0]), int(pos[j][1])
+            oj = obj[y:y + N, x:x + N]
+            num_p += np.conj(oj)[None] * psi_new[j]
+            den_p += np.abs(oj) ** 2
+        reg = alpha_P * den_p.max()
+        upd = den_p + reg > 0
+        probes = np.array(probes, dtype=np.complex128, copy=True)
+        probes[:, upd] = num_p[:, upd] / (den_p[upd] + reg)[None]
+    return obj, probes, err
+
+
+def reconstruct_modes(fused, pos, obj0, probes0, n_iter: int, alpha_O: float = 1e-3,
+                      alpha_P: float = 1e-3, probe_update_start: int = 0, A=None):
+    """Mixed-state reconstruction; probes0: [Q, N, N].  Returns (obj, probes, errors)."""
+    if A is None:
+        A = amplitudes(fused)
+    obj = np.asarray(obj0, dtype=np.complex128).copy()
+    probes = np.asarray(probes0, dtype=np.complex128).copy()
+    pos = np.asarray(pos)
+    norm = float(np.sum(A * A))
+    errs = np.empty(n_iter)
+    for it in range(n_iter):
+        obj, probes, e = iterate_once_modes(obj, probes, pos, A, alpha_O, alpha_P,
+                                            it >= probe_update_start)
+        errs[it] = e / norm if norm > 0 else 0.0
+    return obj, probes, errs

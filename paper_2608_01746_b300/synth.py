@@ -22,8 +22,8 @@ import math
 
 import numpy as np
 
-__all__ = ["ScanConfig", "CONFIGS", "make_object", "make_probe", "raster_positions",
-           "spiral_positions", "make_scan", "make_scan_torch", "seed_for"]
+__all__ = ["ScanConfig", "CONFIGS", "make_object", "make_probe", "make_probe_modes",
+           "raster_positions", "spiral_positions", "make_scan", "make_scan_torch", "seed_for"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -43,6 +43,8 @@ class ScanConfig:
     jitter: int = 0             # raster: uniform integer jitter in [-jitter, jitter]
     J: int = 0                  # spiral: number of positions
     phase_sigma: float = 4.0    # smoothing of the object phase field (pixels)
+    modes: int = 1              # incoherent probe modes (one per wavelength)
+    bandwidth: float = 0.1      # wavelengths span lambda_0 (1 +- bandwidth)
 
     @property
     def K(self) -> int:
@@ -63,6 +65,14 @@ CONFIGS = {
     "lab": ScanConfig("lab", M=1024, N=256, scan="spiral", radius=80.0,
                       times=(1.0, 4.0, 16.0, 64.0, 256.0), peak=1e6, clip=65535, levels=6,
                       n_iter=200, J=1600),
+    # Mixed state: the lab scan with 8 probe modes over +-10% bandwidth, 100 iterations.
+    "mixed": ScanConfig("mixed", M=1024, N=256, scan="spiral", radius=80.0,
+                        times=(1.0, 4.0, 16.0, 64.0, 256.0), peak=1e6, clip=65535, levels=6,
+                        n_iter=100, J=1600, modes=8),
+    # The same construction on the small scan (fast enough for the oracle).
+    "mixed_small": ScanConfig("mixed_small", M=256, N=64, scan="raster", radius=20.0,
+                              times=(1.0, 10.0, 100.0), peak=1e4, clip=4095, levels=4, n_iter=20,
+                              n_side=10, step=8, jitter=1, modes=8),
     # Reduced cases for the CPU tests (same construction, smaller sizes).
     "tiny": ScanConfig("tiny", M=64, N=16, scan="raster", radius=5.0, times=(1.0, 10.0, 100.0),
                        peak=1e4, clip=4095, levels=3, n_iter=30, n_side=5, step=4, jitter=1,
@@ -73,7 +83,7 @@ CONFIGS = {
 
 
 def seed_for(name: str) -> int:
-    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid"]
+    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small"]
     return 1000 + (order.index(name) if name in order else 99)
 
 
@@ -102,6 +112,19 @@ def make_probe(N: int, radius: float) -> np.ndarray:
     w = radius / 10.0
     amp = np.where(r <= radius, 1.0, np.exp(-((r - radius) ** 2) / (2.0 * w * w)))
     return amp * np.exp(1j * math.pi * r * r / (radius * radius))
+
+
+def make_probe_modes(N: int, radius: float, modes: int, bandwidth: float) -> np.ndarray:
+    """Q probe modes, one per wavelength lambda_m = lambda_0 (1 + b (2m/(Q-1) - 1)): mode m is the
+    probe magnified by lambda_m / lambda_0, P_m(r) = P(r lambda_0 / lambda_m); equal spectral
+    weights (1/Q of the power each).  One mode returns the plain probe."""
+    if modes == 1:
+        return make_probe(N, radius)[None]
+    out = []
+    for m in range(modes):
+        lam = 1.0 + bandwidth * (2.0 * m / (modes - 1) - 1.0)
+        out.append(make_probe(N, radius * lam) / math.sqrt(modes))
+    return np.stack(out)
 
 
 def raster_positions(rng: np.random.Generator, M: int, N: int, n_side: int, step: int,
@@ -136,13 +159,15 @@ def _positions(cfg: ScanConfig, rng: np.random.Generator) -> np.ndarray:
     return spiral_positions(cfg.M, cfg.N, cfg.J)
 
 
-def _far_field_intensity(obj: np.ndarray, probe: np.ndarray, pos: np.ndarray) -> np.ndarray:
-    """|F[P * O_j]|^2, unitary 2-D DFT, DC moved to the array centre (detector layout)."""
-    N = probe.shape[0]
+def _far_field_intensity(obj: np.ndarray, probes: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """sum_m |F[P_m * O_j]|^2 over the probe modes (one mode: the coherent intensity), unitary
+    2-D DFT, DC moved to the array centre (detector layout)."""
+    Q, N, _ = probes.shape
     out = np.empty((len(pos), N, N))
     for j, (y, x) in enumerate(pos):
-        psi = probe * obj[y:y + N, x:x + N]
-        out[j] = np.abs(np.fft.fftshift(np.fft.fft2(psi, norm="ortho"))) ** 2
+        psi = probes * obj[y:y + N, x:x + N][None]
+        f = np.fft.fftshift(np.fft.fft2(psi, norm="ortho"), axes=(-2, -1))
+        out[j] = np.sum(np.abs(f) ** 2, axis=0)
     return out
 
 
@@ -164,7 +189,7 @@ def make_scan(cfg: ScanConfig | str, seed: int | None = None, noise: bool = True
     times = tuple(cfg.times if times is None else times)
     rng = np.random.default_rng(seed)
     obj = make_object(rng, cfg.M, cfg.phase_sigma)
-    probe = make_probe(cfg.N, cfg.radius)
+    probe = make_probe_modes(cfg.N, cfg.radius, cfg.modes, cfg.bandwidth)
     pos = _positions(cfg, rng)
     inten = _far_field_intensity(obj, probe, pos)
     scale = cfg.peak / inten.max()
@@ -179,6 +204,8 @@ def make_scan(cfg: ScanConfig | str, seed: int | None = None, noise: bool = True
         raw[:, k] = rng.poisson(lam) if noise else np.rint(lam)
     if clip:
         raw = np.minimum(raw, cfg.clip).astype(np.uint16)
+    if cfg.modes == 1:
+        probe = probe[0]                # single mode: [N][N] as before; else [Q][N][N]
     return {"cfg": cfg, "obj": obj, "probe": probe, "pos": pos, "times": np.asarray(times),
             "clip_value": float(cfg.clip), "intensity": inten, "raw": raw, "seed": seed}
 
@@ -198,7 +225,7 @@ def make_scan_torch(cfg: ScanConfig | str, seed: int | None = None, device="cuda
         seed = seed_for(cfg.name)
     rng = np.random.default_rng(seed)
     obj = make_object(rng, cfg.M, cfg.phase_sigma)
-    probe = make_probe(cfg.N, cfg.radius)
+    probe = make_probe_modes(cfg.N, cfg.radius, cfg.modes, cfg.bandwidth)
     pos = _positions(cfg, rng)
     J, N, K = len(pos), cfg.N, cfg.K
     dev = torch.device(device)
@@ -212,9 +239,12 @@ def make_scan_torch(cfg: ScanConfig | str, seed: int | None = None, device="cuda
         e = min(J, s + chunk)
         rows = (ys[s:e, None] + ar[None, :])[:, :, None]
         cols = (xs[s:e, None] + ar[None, :])[:, None, :]
-        psi = p_t[None] * o_t[rows, cols]
-        f = torch.fft.fftshift(torch.fft.fft2(psi, norm="ortho"), dim=(-2, -1))
-        inten[s:e] = f.real ** 2 + f.imag ** 2
+        acc = torch.zeros((e - s, N, N), dtype=torch.float32, device=dev)
+        patch = o_t[rows, cols]
+        for m in range(p_t.shape[0]):
+            f = torch.fft.fftshift(torch.fft.fft2(p_t[m][None] * patch, norm="ortho"), dim=(-2, -1))
+            acc += f.real ** 2 + f.imag ** 2
+        inten[s:e] = acc
     scale = cfg.peak / float(inten.max())
     inten *= scale
     probe = probe * math.sqrt(scale)
@@ -228,5 +258,7 @@ def make_scan_torch(cfg: ScanConfig | str, seed: int | None = None, device="cuda
             lam = inten[s:e] * float(t / tmax)
             cnt = torch.poisson(lam, generator=gen).clamp_(max=float(cfg.clip))
             raw[s:e, k] = cnt.to(torch.int32).to(torch.uint16)
+    if cfg.modes == 1:
+        probe = probe[0]
     return {"cfg": cfg, "obj": obj, "probe": probe, "pos": pos, "times": np.asarray(cfg.times),
             "clip_value": float(cfg.clip), "raw": raw, "seed": seed}
