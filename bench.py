@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["lab", "mixed"], default="lab",
+                    help="lab: coherent lab-scale scan (the headline); mixed: the same scan with "
+                         "8 incoherent probe modes, 100 iterations")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration count (profiling runs only; not a bench value)")
     ap.add_argument("--positions", type=int, default=None,
@@ -178,12 +181,12 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = synth.CONFIGS[WORKLOAD]
+    cfg = synth.CONFIGS[args.workload]
     n_iter = args.iters or cfg.n_iter
     if args.positions:
         import dataclasses
         cfg = dataclasses.replace(cfg, J=args.positions)
-    sc = synth.make_scan_torch(cfg, seed=rank_seed(synth.seed_for(WORKLOAD), rank), device=dev)
+    sc = synth.make_scan_torch(cfg, seed=rank_seed(synth.seed_for(args.workload), rank), device=dev)
     raw = sc["raw"]
     J, K, N = raw.shape[0], cfg.K, cfg.N
     M = cfg.M
@@ -240,7 +243,7 @@ def run_ours(args, world, rank, local):
         obj_h = np.ones((M, M), np.complex64)
         probe_h = sc["probe"].astype(np.complex64)
         out_o = np.empty((M, M), np.complex64)
-        out_p = np.empty((N, N), np.complex64)
+        out_p = np.empty(probe_h.shape, np.complex64)
         raw_d = torch.empty_like(raw)
 
         def e2e_step():
@@ -271,13 +274,16 @@ def run_ours(args, world, rank, local):
     dom = int(np.argmax(stage_ms))
     names = ["k_exit_wave", "object update (k_object_gather + k_apply)",
              "probe update (k_probe_partial + k_probe_reduce + k_apply)", "k_error_reduce"]
-    exit_ms = stage_ms[0] / max(stage_n[0], 1)
-    flops = exit_wave_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
+    Q = cfg.modes
+    exit_ms = stage_ms[0] / max(stage_n[0], 1) * (3 if Q > 1 else 1)   # per iteration
+    flops = Q * exit_wave_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
     alu_peak = fp32_peak_tflops(2032.0)
-    hbm_algo = exit_wave_bytes_per_position(N) * J / (exit_ms / 1e3) / 1e9
+    hbm_algo = Q * exit_wave_bytes_per_position(N) * J / (exit_ms / 1e3) / 1e9
     tpp = profiled_traffic_per_position()
-    traffic = int(tpp * J) if (tpp is not None and N == 256) else None
-    roof = {"kernel": "k_exit_wave_tma" if N == 256 else "k_exit_wave", "bound": "alu",
+    traffic = int(tpp * J) if (tpp is not None and N == 256 and Q == 1) else None
+    kname = ("k_exit_wave_tma" if N == 256 else "k_exit_wave") + (
+        " (forward + k_modulus_modes + inverse, per iteration)" if Q > 1 else "")
+    roof = {"kernel": kname, "bound": "alu",
             "achieved": round(flops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
             "frac": round(flops / alu_peak, 4),
             "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
@@ -290,12 +296,12 @@ def run_ours(args, world, rank, local):
     launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
 
     conv = None
-    if rank == 0 and not args.no_nrmse:
+    if rank == 0 and not args.no_nrmse and Q == 1:
         conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
                               probe_update_start=pus) for pus in (0, 10 ** 9)]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         cpu = cpu_baseline()
 
     out = {
@@ -303,9 +309,12 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded Fermat-spiral scan, Poisson counts, 16-bit clip)",
-        "config": {"workload": "lab-scale MNF + reconstruction: object 1024x1024 c64, probe 256x256, "
-                               "1600 positions, 5 exposures (1/4/16/64/256), 6-level pyramid, "
-                               f"{n_iter} iterations per step",
+        "config": {"workload": ("lab-scale MNF + reconstruction: object 1024x1024 c64, probe 256x256, "
+                                "1600 positions, 5 exposures (1/4/16/64/256), 6-level pyramid, "
+                                f"{n_iter} iterations per step") if Q == 1 else
+                               ("mixed-state: the lab scan with 8 incoherent probe modes (+-10% "
+                                f"bandwidth), modulus per mode, {n_iter} iterations per step"),
+                   "modes": Q,
                    "positions": J, "exposures": K, "detector": N, "object": M, "levels": cfg.levels,
                    "iterations": n_iter, "l2": "inputs larger than L2 (raw stack 1.05 GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -98,11 +98,13 @@ typedef struct {
     int M;                  /* object side (M x M complex64), M >= N                          */
     int N;                  /* probe / detector side: 16, 64 or 256                           */
     int J;                  /* scan positions, >= 1                                           */
+    int modes;              /* incoherent probe modes Q, 1..8 (Eq. 4 with a discrete spectrum:
+                               I = sum_m |F(P_m O_j)|^2, shared object); 1 = coherent Eq. 3   */
     const int32_t *h_pos;   /* host [J][2] (y, x) top-left patch corner, 0 <= y, x <= M - N   */
     const float *d_fused;   /* device [J][N][N] fused intensities, DC-centred (fuse_stack's
                                output); A = sqrt(max(I, 0)) is formed once here              */
     const void *obj0;       /* complex64 [M][M] initial object                                */
-    const void *probe0;     /* complex64 [N][N] initial probe                                 */
+    const void *probe0;     /* complex64 [modes][N][N] initial probe modes                    */
     int init_on_device;     /* 1: obj0 / probe0 are device pointers, 0: host pointers         */
     float alpha_O;          /* object regulariser relative to max sum_j |P|^2 (>= 0)          */
     float alpha_P;          /* probe regulariser relative to max sum_j |O_j|^2 (>= 0)         */
@@ -124,7 +126,9 @@ int ptycho_init(ptycho_handle *out, const ptycho_desc *d);
  * ptycho_iterate -- run n_iter >= 0 iterations of full-batch alternating projections:
  * per position psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] (Eqs. 2-3 and the modulus
  * constraint), then the least-squares object update from all psi_j', then (from iteration
- * probe_update_start on) the least-squares probe update from the new object.
+ * probe_update_start on) the least-squares probe update from the new object.  With modes > 1
+ * every mode's spectrum is scaled by A_j / sqrt(sum_m |F(P_m O_j)|^2), the object update sums
+ * over modes and each mode gets its own least-squares probe update.
  *   h_err  host [n_iter] or NULL: per-iteration Fourier error
  *          sum_j sum_q (|Psi_j| - A_j)^2 / sum_j sum_q A_j^2 measured before each projection.
  * With h_err the call synchronises and returns PTYCHO_ENONFINITE if any error is NaN/Inf;
@@ -132,8 +136,8 @@ int ptycho_init(ptycho_handle *out, const ptycho_desc *d);
  */
 int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err);
 
-/* Copy the current object (complex64 [M][M]) / probe (complex64 [N][N]) into dst, a device
- * pointer if dst_on_device else a host pointer.  A host copy synchronises the stream. */
+/* Copy the current object (complex64 [M][M]) / probe modes (complex64 [modes][N][N]) into dst,
+ * a device pointer if dst_on_device else a host pointer.  A host copy synchronises the stream. */
 int ptycho_get_object(ptycho_handle h, void *dst, int dst_on_device);
 int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device);
 

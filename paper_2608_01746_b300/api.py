@@ -36,7 +36,7 @@ class FuseParamsC(ctypes.Structure):
 
 class PtychoDescC(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("N", ctypes.c_int), ("J", ctypes.c_int),
-                ("h_pos", ctypes.c_void_p), ("d_fused", ctypes.c_void_p),
+                ("modes", ctypes.c_int), ("h_pos", ctypes.c_void_p), ("d_fused", ctypes.c_void_p),
                 ("obj0", ctypes.c_void_p), ("probe0", ctypes.c_void_p),
                 ("init_on_device", ctypes.c_int), ("alpha_O", ctypes.c_float),
                 ("alpha_P", ctypes.c_float), ("probe_update_start", ctypes.c_int),
@@ -150,9 +150,9 @@ def fuse_stack_noalloc(raw, times, params: FuseParamsC, out, stream=None):
 class PtychoHandle:
     """Owner of a ``ptycho_handle``; ``close()`` (or garbage collection) destroys it."""
 
-    def __init__(self, ptr: int, M: int, N: int, J: int):
+    def __init__(self, ptr: int, M: int, N: int, J: int, Q: int = 1):
         self.ptr = ctypes.c_void_p(ptr)
-        self.M, self.N, self.J = M, N, J
+        self.M, self.N, self.J, self.Q = M, N, J, Q
 
     def close(self) -> None:
         if self.ptr:
@@ -169,7 +169,8 @@ class PtychoHandle:
 def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float = 1e-3,
                 probe_update_start: int = 0, stream=None) -> PtychoHandle:
     """fused: float32 CUDA tensor [J][N][N]; pos: int [J][2] (y, x); obj0 / probe0: complex64,
-    both numpy (host) or both torch CUDA tensors (device)."""
+    both numpy (host) or both torch CUDA tensors (device); probe0 is [N][N] (one mode) or
+    [Q][N][N] (Q incoherent modes)."""
     import torch
     if fused.dtype != torch.float32 or not fused.is_cuda or not fused.is_contiguous():
         raise ValueError("fused must be a contiguous float32 CUDA tensor [J][N][N]")
@@ -189,11 +190,12 @@ def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float 
         probe0 = np.ascontiguousarray(probe0, dtype=np.complex64)
         op, pp = obj0.ctypes.data, probe0.ctypes.data
     M = obj0.shape[0]
-    desc = PtychoDescC(M, N, J, pos.ctypes.data, fused.data_ptr(), op, pp, 1 if on_dev else 0,
+    Q = probe0.shape[0] if len(probe0.shape) == 3 else 1
+    desc = PtychoDescC(M, N, J, Q, pos.ctypes.data, fused.data_ptr(), op, pp, 1 if on_dev else 0,
                        alpha_O, alpha_P, probe_update_start, _stream_ptr(stream))
     h = ctypes.c_void_p()
     _check(lib().ptycho_init(ctypes.byref(h), ctypes.byref(desc)))
-    return PtychoHandle(h.value, M, N, J)
+    return PtychoHandle(h.value, M, N, J, Q)
 
 
 def ptycho_iterate(h: PtychoHandle, n_iter: int, errors: bool = True):
@@ -226,7 +228,8 @@ def ptycho_get_object(h: PtychoHandle, out=None):
 
 
 def ptycho_get_probe(h: PtychoHandle, out=None):
-    return _get(lib().ptycho_get_probe, h, (h.N, h.N), out)
+    shape = (h.N, h.N) if h.Q == 1 else (h.Q, h.N, h.N)
+    return _get(lib().ptycho_get_probe, h, shape, out)
 
 
 def ptycho_destroy(h: PtychoHandle) -> None:

@@ -37,14 +37,20 @@ constexpr int kTR = 8;           // tile height (rows): one register per row and
 
 enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
 
+// What an exit-wave kernel launch does per unit of work.
+//   XM_FULL  unit = position j: psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] (one probe mode)
+//   XM_FWD   unit = (j, m): Psi_jm = F(P_m O_j), unitary, into psi[j][m] (row-major, DC at 0)
+//   XM_INV   unit = (j, m): psi[j][m] <- F^-1 psi[j][m] (after the mode-summed modulus step)
+enum { XM_FULL = 0, XM_FWD = 1, XM_INV = 2 };
+
 struct ExitArgs {
     const float2 *obj;
-    const float2 *probe;
+    const float2 *probe;     // [Q][N][N]
     const float *amp;        // [J][N][N] column-major per position: amp[j][kx][ky]
     const int2 *pos;         // (y, x)
-    float2 *psi;             // [J][N][N] row-major exit-wave update
-    double *err;             // [J] Fourier error per position
-    int M, J;
+    float2 *psi;             // [J][Q][N][N] row-major
+    double *err;             // [J] Fourier error per position (XM_FULL)
+    int M, J, Q;
 };
 
 // Shared memory of the small-tile exit-wave kernel: twiddles, the FFT groups' exchange
@@ -56,10 +62,10 @@ constexpr size_t exit_smem_bytes() {
     return sizeof(float2) * ((size_t)N + (size_t)G * R * (R + 1) + (size_t)N * (N + 1));
 }
 
-// N <= 64: one CTA per position at a time (persistent grid), the whole N x N tile in shared
-// memory: row FFTs, column FFTs with the modulus replacement between the forward and inverse
-// column transforms, inverse row FFTs written to psi_j'.
-template <int R>
+// N <= 64: one CTA per unit at a time (persistent grid), the whole N x N tile in shared
+// memory: row FFTs, column FFTs (with the modulus replacement between the forward and inverse
+// column transforms in XM_FULL), inverse row FFTs.
+template <int R, int XM>
 __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     constexpr int N = R * R;
     constexpr int G = kThreads / R;          // FFT groups per CTA
@@ -82,25 +88,33 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     float2 *xb = xb_all + g * R * (R + 1);
     const float invN = 1.0f / (float)N;
     const int M = a.M;
+    const int units = (XM == XM_FULL) ? a.J : a.J * a.Q;
 
-    for (int j = blockIdx.x; j < a.J; j += gridDim.x) {
-        const int2 pj = a.pos[j];
-        // (1) psi = P * O_j, forward row FFTs in place
-        for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
-            if (r < N) {                                     // warp-uniform (see fft.cuh)
-                float2 d[R];
-                const float2 *orow = a.obj + (size_t)(pj.x + r) * M + pj.y;
-                const float2 *prow = a.probe + (size_t)r * N;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int j = (XM == XM_FULL) ? u : u / a.Q;
+        const int mode = (XM == XM_FULL) ? 0 : u % a.Q;
+        float2 *psi_u = a.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
+        if constexpr (XM != XM_INV) {
+            // (1) psi = P_m * O_j, forward row FFTs in place
+            const int2 pj = a.pos[j];
+            for (int r0 = 0; r0 < N; r0 += G) {
+                const int r = r0 + g;
+                if (r < N) {                                 // warp-uniform (see fft.cuh)
+                    float2 d[R];
+                    const float2 *orow = a.obj + (size_t)(pj.x + r) * M + pj.y;
+                    const float2 *prow = a.probe + (size_t)mode * N * N + (size_t)r * N;
 #pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
-                pm::fft_group<R, -1>(d, xb, tw, t);
+                    for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
+                    pm::fft_group<R, -1>(d, xb, tw, t);
 #pragma unroll
-                for (int m = 0; m < R; ++m) rows[r * TP + t + R * m] = d[m];
+                    for (int m = 0; m < R; ++m) rows[r * TP + t + R * m] = d[m];
+                }
             }
+        } else {
+            for (int i = tid; i < N * N; i += kThreads) rows[(i / N) * TP + i % N] = psi_u[i];
         }
         __syncthreads();
-        // (2) column FFTs, modulus replacement, inverse column FFTs
+        // (2) column FFTs: forward (+ modulus + inverse in XM_FULL) or inverse (XM_INV)
         float err = 0.f;
         const float *amp_j = a.amp + (size_t)j * N * N;
         for (int c0 = 0; c0 < N; c0 += G) {
@@ -109,48 +123,98 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
                 float2 d[R];
 #pragma unroll
                 for (int m = 0; m < R; ++m) d[m] = rows[(t + R * m) * TP + c];
-                pm::fft_group<R, -1>(d, xb, tw, t);
+                if constexpr (XM == XM_INV) {
+                    pm::fft_group<R, +1>(d, xb, tw, t);
+                } else {
+                    pm::fft_group<R, -1>(d, xb, tw, t);
 #pragma unroll
-                for (int m = 0; m < R; ++m) {
-                    const float2 X = cscale(d[m], invN);
-                    const float A = __ldg(amp_j + (size_t)c * N + t + R * m);
-                    const float mag = sqrtf(cabs2(X));
-                    const float dm = mag - A;
-                    err += dm * dm;
-                    d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+                    for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
                 }
-                pm::fft_group<R, +1>(d, xb, tw, t);
+                if constexpr (XM == XM_FULL) {
+#pragma unroll
+                    for (int m = 0; m < R; ++m) {
+                        const float2 X = d[m];
+                        const float A = __ldg(amp_j + (size_t)c * N + t + R * m);
+                        const float mag = sqrtf(cabs2(X));
+                        const float dm = mag - A;
+                        err += dm * dm;
+                        d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+                    }
+                    pm::fft_group<R, +1>(d, xb, tw, t);
+                }
 #pragma unroll
                 for (int m = 0; m < R; ++m) rows[(t + R * m) * TP + c] = d[m];
             }
         }
         __syncthreads();
-        // (3) inverse row FFTs, psi_j' written row-major
-        float2 *psi_j = a.psi + (size_t)j * N * N;
-        for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
-            if (r < N) {
-                float2 d[R];
+        if constexpr (XM == XM_FWD) {
+            for (int i = tid; i < N * N; i += kThreads) psi_u[i] = rows[(i / N) * TP + i % N];
+        } else {
+            // (3) inverse row FFTs, psi' written row-major
+            for (int r0 = 0; r0 < N; r0 += G) {
+                const int r = r0 + g;
+                if (r < N) {
+                    float2 d[R];
 #pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = rows[r * TP + t + R * m];
-                pm::fft_group<R, +1>(d, xb, tw, t);
+                    for (int m = 0; m < R; ++m) d[m] = rows[r * TP + t + R * m];
+                    pm::fft_group<R, +1>(d, xb, tw, t);
 #pragma unroll
-                for (int m = 0; m < R; ++m) psi_j[(size_t)r * N + t + R * m] = cscale(d[m], invN);
+                    for (int m = 0; m < R; ++m) psi_u[(size_t)r * N + t + R * m] = cscale(d[m], invN);
+                }
             }
         }
-        // Fourier error of position j (FP64 block sum); the barrier also keeps the next
-        // position's row pass from overwriting rows that step (3) still reads
-        double e = (double)err;
+        if constexpr (XM == XM_FULL) {
+            // Fourier error of position j (FP64 block sum)
+            double e = (double)err;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = e;
-        __syncthreads();
-        if (tid == 0) {
-            double sum = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
-            a.err[j] = sum;
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if ((tid & 31) == 0) s_red[tid >> 5] = e;
+            __syncthreads();
+            if (tid == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+                a.err[j] = sum;
+            }
         }
-        __syncthreads();
+        __syncthreads();          // the next unit's first pass overwrites the tile
+    }
+}
+
+// Mixed-state modulus constraint, one block per position: S = sum_m |Psi_m|^2,
+// error (sqrt(S) - A)^2, Psi_m <- Psi_m A / sqrt(S) (where S = 0: Psi_0 = A, other modes 0).
+// psi: [J][Q][N][N] spectra (row-major, DC at 0); amp_nat: [J][N][N] row-major amplitudes.
+__global__ void __launch_bounds__(kThreads) k_modulus_modes(float2 *__restrict__ psi,
+                                                            const float *__restrict__ amp_nat,
+                                                            double *__restrict__ err, int N, int Q) {
+    __shared__ double s_red[kThreads / 32];
+    const int j = blockIdx.x;
+    const size_t NN = (size_t)N * N;
+    float2 *pj = psi + (size_t)j * Q * NN;
+    double acc = 0.0;
+    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
+        float S = 0.f;
+        for (int m = 0; m < Q; ++m) S += cabs2(pj[m * NN + q]);
+        const float A = __ldg(amp_nat + (size_t)j * NN + q);
+        if (S > 0.f) {
+            const float inv = rsqrtf(S);
+            const float dm = S * inv - A;
+            acc += (double)(dm * dm);
+            const float sc = A * inv;
+            for (int m = 0; m < Q; ++m) pj[m * NN + q] = cscale(pj[m * NN + q], sc);
+        } else {
+            acc += (double)A * (double)A;
+            pj[q] = make_float2(A, 0.f);
+            for (int m = 1; m < Q; ++m) pj[m * NN + q] = make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) r += s_red[w];
+        err[j] = r;
     }
 }
 
@@ -174,13 +238,13 @@ struct TmaArgs {
     const float2 *obj;
     const float *amp;        // [J][N][N] column-major per position
     const int2 *pos;
-    double *err;             // [J] Fourier error per position
+    double *err;             // [J] Fourier error per position (XM_FULL)
     int *status;             // set to 1 if a bounded wait gave up
-    int M, J;
+    int M, J, Q;
 };
 
 struct TmaMaps {
-    CUtensorMap prow;        // probe rows            box {256 c, 32 r}
+    CUtensorMap prow;        // probe rows ([Q N] rows) box {256 c, B r}
     CUtensorMap slot_r;      // slot, column-major    box {16 r, 256 c}, 128-byte swizzle
     CUtensorMap slot_c;      // slot, column-major    box {256 r, 32 c}
     CUtensorMap psi_c;       // psi, row-major        box {16 c, 256 r}, 128-byte swizzle
@@ -195,7 +259,7 @@ __host__ __device__ constexpr size_t tma_buf_bytes() { return (size_t)B * 256 * 
 template <int B>
 __host__ __device__ constexpr size_t tma_smem_bytes() { return 1024 /*alignment slack*/ + 3 * tma_buf_bytes<B>() + 256 * sizeof(float2) + 64; }
 
-template <int B>
+template <int B, int XM>
 __global__ void __launch_bounds__(B * 16, 32 / B)
 k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     constexpr int R = 16, N = 256, NB = N / B;
@@ -258,11 +322,16 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         }
     };
 
-    for (int j = blockIdx.x; j < a.J && !failed; j += gridDim.x) {
+    const int units = (XM == XM_FULL) ? a.J : a.J * a.Q;
+    for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+        const int j = (XM == XM_FULL) ? u : u / a.Q;
+        const int prow0 = (XM == XM_FULL) ? 0 : (u % a.Q) * N;    // first probe row of the mode
+        float err = 0.f;
+        if constexpr (XM != XM_INV) {
         const int2 pj = a.pos[j];
         // ---- phase R: forward row FFTs -> slot (column-major)
-        prefetch(0, &tm.prow, 0, 0);
-        prefetch(1, &tm.prow, 0, kTmaBatch);
+        prefetch(0, &tm.prow, 0, prow0);
+        prefetch(1, &tm.prow, 0, prow0 + kTmaBatch);
         float2 pO[R];
         {
             const float2 *orow = a.obj + (size_t)(pj.x + g) * M + pj.y;
@@ -284,7 +353,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
             pm::fft_group_xs<R, -1>(d, row, tw, t);
             barrier_a();
             if (failed) break;
-            if (b + 2 < NB) prefetch(s, &tm.prow, 0, kTmaBatch * (b + 2));
+            if (b + 2 < NB) prefetch(s, &tm.prow, 0, prow0 + kTmaBatch * (b + 2));
             float2 *ob = bout + h * 4096;
 #pragma unroll
             for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
@@ -294,13 +363,12 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         if (tid == 0) T::wait_all<0>();                 // slot complete before phase C reads it
         prefetch(0, &tm.slot_c, 0, slot_col);
         prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch);
-        // ---- phase C: column FFTs, modulus replacement, inverse column FFTs -> psi_j
-        float err = 0.f;
+        // ---- phase C: column FFTs (modulus replacement and inverse column FFTs in XM_FULL)
         for (int b = 0; b < NB; ++b) {
             const int s = b & 1;
             const int c = kTmaBatch * b + g;
             float A[R];                                   // A[k2] = |F psi| target at ky = t + 16 k2
-            {
+            if constexpr (XM == XM_FULL) {
                 const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c) * N + t * R);
 #pragma unroll
                 for (int v = 0; v < R / 4; ++v) {
@@ -314,34 +382,71 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
             pm::fft_group_xs<R, -1>(d, col, tw, t);
+            if constexpr (XM == XM_FULL) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const float2 X = cscale(d[m], invN);
-                const float mag2 = cabs2(X);
-                if (mag2 > 0.f) {
-                    const float inv = rsqrtf(mag2);
-                    const float dm = mag2 * inv - A[m];
-                    err += dm * dm;
-                    d[m] = cscale(X, A[m] * inv);
-                } else {
-                    err += A[m] * A[m];
-                    d[m] = make_float2(A[m], 0.f);
+                for (int m = 0; m < R; ++m) {
+                    const float2 X = cscale(d[m], invN);
+                    const float mag2 = cabs2(X);
+                    if (mag2 > 0.f) {
+                        const float inv = rsqrtf(mag2);
+                        const float dm = mag2 * inv - A[m];
+                        err += dm * dm;
+                        d[m] = cscale(X, A[m] * inv);
+                    } else {
+                        err += A[m] * A[m];
+                        d[m] = make_float2(A[m], 0.f);
+                    }
                 }
+                pm::fft_group_xs<R, +1>(d, col, tw, t);
+            } else {
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
             }
-            pm::fft_group_xs<R, +1>(d, col, tw, t);
             barrier_a();
             if (failed) break;
             if (b + 2 < NB) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2));
             float2 *ob = bout + h * 4096;
 #pragma unroll
             for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
-            publish(&tm.psi_c, kTmaBatch * b, j * N, 16, 0);
+            publish(&tm.psi_c, kTmaBatch * b, u * N, 16, 0);
+        }
+        } else {
+        // ---- phase C (XM_INV): inverse column FFTs of psi[j][m] in place
+        auto load_psi_cols = [&](int s, int c0) {
+            if (tid == 0) {
+                T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
+                T::load_2d(bin(s), &tm.psi_c, c0, u * N, &bar[s]);
+                if constexpr (B == 32) T::load_2d(bin(s) + 4096, &tm.psi_c, c0 + 16, u * N, &bar[s]);
+            }
+        };
+        if (tid == 0) T::wait_all<0>();
+        load_psi_cols(0, 0);
+        load_psi_cols(1, kTmaBatch);
+        for (int b = 0; b < NB; ++b) {
+            const int s = b & 1;
+            wait_stage(s);
+            float2 d[R];
+            const float2 *colsw = bin(s) + h * 4096;
+#pragma unroll
+            for (int m = 0; m < R; ++m) d[m] = colsw[T::swz128_index(t + R * m, gl)];
+            if (__syncthreads_or(timed_out)) failed = true;      // batch read: regions free
+            if (failed) break;
+            pm::fft_group_xs<R, +1>(d, bin(s) + g * 256, tw, t);
+            barrier_a();
+            if (failed) break;
+            if (b + 2 < NB) load_psi_cols(s, kTmaBatch * (b + 2));
+            float2 *ob = bout + h * 4096;
+#pragma unroll
+            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
+            publish(&tm.psi_c, kTmaBatch * b, u * N, 16, 0);
+        }
         }
         if (failed) break;
-        if (tid == 0) T::wait_all<0>();                 // psi_j columns complete before R'
-        prefetch(0, &tm.psi_r, 0, j * N);
-        prefetch(1, &tm.psi_r, 0, j * N + kTmaBatch);
-        // ---- phase R': inverse row FFTs of psi_j -> psi_j'
+        if constexpr (XM != XM_FWD) {
+        if (tid == 0) T::wait_all<0>();                 // psi columns complete before R'
+        prefetch(0, &tm.psi_r, 0, u * N);
+        prefetch(1, &tm.psi_r, 0, u * N + kTmaBatch);
+        // ---- phase R': inverse row FFTs of psi[u] -> psi'
         for (int b = 0; b < NB; ++b) {
             const int s = b & 1;
             wait_stage(s);
@@ -352,23 +457,26 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
             pm::fft_group_xs<R, +1>(d, row, tw, t);
             barrier_a();
             if (failed) break;
-            if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, j * N + kTmaBatch * (b + 2));
+            if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, u * N + kTmaBatch * (b + 2));
 #pragma unroll
             for (int m = 0; m < R; ++m) bout[g * 256 + t + R * m] = cscale(d[m], invN);
-            publish(&tm.psi_w, 0, j * N + kTmaBatch * b, 0, 16);
+            publish(&tm.psi_w, 0, u * N + kTmaBatch * b, 0, 16);
+        }
         }
         if (failed) break;
-        double e = (double)err;
+        if constexpr (XM == XM_FULL) {
+            double e = (double)err;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = e;
-        __syncthreads();
-        if (tid == 0) {
-            double sum = 0.0;
-            for (int w = 0; w < kTmaThreads / 32; ++w) sum += s_red[w];
-            a.err[j] = sum;
-            T::wait_all<0>();                           // psi_j complete; buffers free for j + 1
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if ((tid & 31) == 0) s_red[tid >> 5] = e;
+            __syncthreads();
+            if (tid == 0) a.err[j] = [&] {
+                double sum = 0.0;
+                for (int w = 0; w < kTmaThreads / 32; ++w) sum += s_red[w];
+                return sum;
+            }();
         }
+        if (tid == 0) T::wait_all<0>();                 // psi[u] complete; buffers free for u + 1
         __syncthreads();
     }
     if (tid == 0) {
@@ -415,7 +523,7 @@ __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const fl
 __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
     const int *__restrict__ tstart, const int4 *__restrict__ tlist, const int *__restrict__ torder,
-    float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx) {
+    float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx, int Q) {
     __shared__ WarpTiles wt;
     __shared__ float s_max[kThreads / 32];
     const int tile = torder[blockIdx.x];              // longest position lists first
@@ -436,23 +544,26 @@ __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
         const int lx = tx0 + lane - pj.y;
         const bool okx = lx >= 0 && lx < N;
         const int lxc = min(max(lx, 0), N - 1);
-        const float2 *psi_j = psi + (size_t)j * NN;
-        // All loads first, from clamped (always valid) addresses, so they are in flight
-        // together; pixels outside the patch are masked out afterwards.
-        float2 pv[kTR], vv[kTR];
+        for (int m = 0; m < Q; ++m) {                    // probe modes (one for coherent data)
+            const float2 *psi_j = psi + ((size_t)j * Q + m) * NN;
+            const float2 *probe_m = probe + (size_t)m * NN;
+            // All loads first, from clamped (always valid) addresses, so they are in flight
+            // together; pixels outside the patch are masked out afterwards.
+            float2 pv[kTR], vv[kTR];
 #pragma unroll
-        for (int r = 0; r < kTR; ++r) {
-            const int lyc = min(max(ty0 + r - pj.x, 0), N - 1);
-            pv[r] = __ldg(probe + lyc * N + lxc);
-            vv[r] = __ldg(psi_j + (size_t)lyc * N + lxc);
-        }
+            for (int r = 0; r < kTR; ++r) {
+                const int lyc = min(max(ty0 + r - pj.x, 0), N - 1);
+                pv[r] = __ldg(probe_m + lyc * N + lxc);
+                vv[r] = __ldg(psi_j + (size_t)lyc * N + lxc);
+            }
 #pragma unroll
-        for (int r = 0; r < kTR; ++r) {
-            const int ly = ty0 + r - pj.x;
-            if (okx && ly >= 0 && ly < N) {
-                acc[r] = cadd(acc[r], cmulc(pv[r], vv[r]));
-                dn[r] += cabs2(pv[r]);
-                hit |= 1u << r;
+            for (int r = 0; r < kTR; ++r) {
+                const int ly = ty0 + r - pj.x;
+                if (okx && ly >= 0 && ly < N) {
+                    acc[r] = cadd(acc[r], cmulc(pv[r], vv[r]));
+                    dn[r] += cabs2(pv[r]);
+                    hit |= 1u << r;
+                }
             }
         }
     }
@@ -513,7 +624,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
 // Warp w takes every 8th position of the chunk; lane = tile column, kTR rows in registers.
 __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
-    float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk) {
+    float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk, int Q) {
     __shared__ WarpTiles wt;
     const int nqx = (N + kTW - 1) / kTW;
     const int qt = blockIdx.x, chunk = blockIdx.y;
@@ -530,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
     for (int j = j0 + warp; j < j1; j += kThreads / 32) {
         const int2 pj = pn;
         if (j + kThreads / 32 < j1) pn = pos[j + kThreads / 32];
-        const float2 *psi_j = psi + (size_t)j * NN;
+        const float2 *psi_j = psi + ((size_t)j * Q + blockIdx.z) * NN;
         const int qxc = min(qx, N - 1);
         float2 ov[kTR], vv[kTR];
 #pragma unroll
@@ -557,8 +668,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
         const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
         const int y = qy0 + r, x = qx0 + c;
         if (y < N && x < N) {
-            pnum[(size_t)chunk * NN + (size_t)y * N + x] = tnum;
-            pden[(size_t)chunk * NN + (size_t)y * N + x] = tden;
+            const size_t o = ((size_t)chunk * Q + blockIdx.z) * NN + (size_t)y * N + x;
+            pnum[o] = tnum;
+            pden[o] = tden;
         }
     }
 }
@@ -608,11 +720,12 @@ __global__ void k_error_reduce(const double *__restrict__ err, int J, const doub
 }
 
 // A = sqrt(max(I, 0)) with DC moved from the centre to index 0, stored per position column by
-// column (amp[j][kx][...]).  Within a column the order is ky (R = 0) or, for the N = 256
+// column (amp[j][kx][...]) and, for the mixed-state path, also row-major (amp_nat[j][ky][kx]).  Within a column the order is ky (R = 0) or, for the N = 256
 // kernel (R = 16), the order its FFT groups consume: thread t's targets ky = t + 16 k2 are
 // contiguous (index t * 16 + k2).  Also the sum of A^2 per position.
 __global__ void __launch_bounds__(kThreads) k_amplitudes(const float *__restrict__ fused, float *__restrict__ amp,
-                                                         double *__restrict__ a2, int N, int R) {
+                                                         float *__restrict__ amp_nat, double *__restrict__ a2, int N,
+                                                         int R) {
     __shared__ double s[kThreads / 32];
     const int j = blockIdx.x;
     const size_t NN = (size_t)N * N;
@@ -624,6 +737,7 @@ __global__ void __launch_bounds__(kThreads) k_amplitudes(const float *__restrict
         const int sy = (ky + h) % N, sx = (kx + h) % N;
         const float v = sqrtf(fmaxf(fused[(size_t)j * NN + (size_t)sy * N + sx], 0.f));
         amp[(size_t)j * NN + i] = v;
+        if (amp_nat) amp_nat[(size_t)j * NN + (size_t)ky * N + kx] = v;   // row-major [ky][kx]
         acc += (double)v * (double)v;
     }
 #pragma unroll
@@ -653,7 +767,7 @@ __global__ void k_inv_norm(const double *__restrict__ a2, int J, double *__restr
 }  // namespace
 
 struct ptycho_ctx {
-    int M = 0, N = 0, J = 0, R = 0;
+    int M = 0, N = 0, J = 0, R = 0, Q = 1;
     float alpha_O = 0.f, alpha_P = 0.f;
     int probe_update_start = 0;
     long long iter = 0;
@@ -661,6 +775,7 @@ struct ptycho_ctx {
     int2 *d_pos = nullptr;
     float2 *d_obj = nullptr, *d_probe = nullptr, *d_psi = nullptr, *d_slot = nullptr;
     float2 *d_num_o = nullptr, *d_num_p = nullptr, *d_pnum = nullptr;
+    float *d_amp_nat = nullptr;                           // row-major amplitudes (Q > 1)
     float *d_amp = nullptr, *d_den_o = nullptr, *d_den_p = nullptr, *d_pden = nullptr;
     float *d_tile_max = nullptr, *d_pmax = nullptr;
     double *d_err_pos = nullptr, *d_a2 = nullptr, *d_inv_norm = nullptr, *d_err = nullptr;
@@ -696,7 +811,7 @@ void free_ctx(ptycho_ctx *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
-                    h->d_amp, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
+                    h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
                     h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status, h->d_torder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -738,51 +853,62 @@ int encode_2d(CUtensorMap *m, void *addr, CUtensorMapDataType dt, size_t esize, 
     return PTYCHO_OK;
 }
 
-template <int B>
-int setup_exit_tma_b(ptycho_ctx *h) {
+template <int B, int XM>
+int setup_tma_kernel(ptycho_ctx *h, int *per_sm) {
     const size_t smem = tma_smem_bytes<B>();
-    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    PM_CUDA(cudaGetDevice(&dev));
-    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave_tma<B>, B * 16, smem));
-    if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_exit_wave_tma<B, XM>, B * 16, smem));
+    if (*per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
     h->exit_smem = smem;
-    h->exit_tma = true;
-    h->tma_batch = B;
-    h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
     return PTYCHO_OK;
 }
 
 // Batch size of the N = 256 kernel (16 or 32 rows per stage); PTYCHO_TMA_BATCH overrides.
-int tma_batch_choice() {
+// The mixed-state forward/inverse kernels use 16.
+int tma_batch_choice(int Q) {
     const char *env = std::getenv("PTYCHO_TMA_BATCH");
-    if (env && std::atoi(env) == 32) return 32;
-    if (env && std::atoi(env) == 16) return 16;
+    if (Q == 1 && env && std::atoi(env) == 32) return 32;
     return 16;
 }
 
 int setup_exit_tma(ptycho_ctx *h) {
-    return tma_batch_choice() == 32 ? setup_exit_tma_b<32>(h) : setup_exit_tma_b<16>(h);
+    int dev = 0, sms = 0, per_sm = 0, rc;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    h->tma_batch = tma_batch_choice(h->Q);
+    if (h->Q > 1) {
+        int p2 = 0;
+        if ((rc = setup_tma_kernel<16, XM_FWD>(h, &per_sm))) return rc;
+        if ((rc = setup_tma_kernel<16, XM_INV>(h, &p2))) return rc;
+        per_sm = std::min(per_sm, p2);
+    } else if (h->tma_batch == 32) {
+        if ((rc = setup_tma_kernel<32, XM_FULL>(h, &per_sm))) return rc;
+    } else {
+        if ((rc = setup_tma_kernel<16, XM_FULL>(h, &per_sm))) return rc;
+    }
+    h->exit_tma = true;
+    h->grid_exit = std::max(1, std::min(h->J * h->Q, sms * per_sm));
+    return PTYCHO_OK;
 }
 
 // Tensor maps of the TMA kernel; called once the buffers exist.
 int encode_exit_tma(ptycho_ctx *h) {
-    const uint64_t N = (uint64_t)h->N;
+    const uint64_t N = (uint64_t)h->N, Q = (uint64_t)h->Q;
     const uint32_t B = (uint32_t)h->tma_batch;
     const CUtensorMapDataType c64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;    // one complex64 = 8 bytes
+    const uint64_t psi_rows = N * Q * (uint64_t)h->J;
     int rc;
-    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N * Q, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
     if ((rc = encode_2d(&h->tm.slot_r, h->d_slot, c64, 8, N, N * h->grid_exit, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B)))
         return rc;
     if ((rc = encode_2d(&h->tm.slot_c, h->d_slot, c64, 8, N, N * h->grid_exit, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE)))
         return rc;
-    if ((rc = encode_2d(&h->tm.psi_c, h->d_psi, c64, 8, N, N * h->J, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
-    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, N * h->J, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
-    return encode_2d(&h->tm.psi_w, h->d_psi, c64, 8, N, N * h->J, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if ((rc = encode_2d(&h->tm.psi_c, h->d_psi, c64, 8, N, psi_rows, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, psi_rows, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    return encode_2d(&h->tm.psi_w, h->d_psi, c64, 8, N, psi_rows, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
-int launch_exit_tma(ptycho_ctx *h) {
+TmaArgs tma_args(ptycho_ctx *h) {
     TmaArgs a;
     a.obj = h->d_obj;
     a.amp = h->d_amp;
@@ -791,31 +917,49 @@ int launch_exit_tma(ptycho_ctx *h) {
     a.status = h->d_status;
     a.M = h->M;
     a.J = h->J;
-    if (h->tma_batch == 32)
-        k_exit_wave_tma<32><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
-    else
-        k_exit_wave_tma<16><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    a.Q = h->Q;
+    return a;
+}
+
+int launch_exit_tma(ptycho_ctx *h, int xm) {
+    const TmaArgs a = tma_args(h);
+    if (xm == XM_FWD) k_exit_wave_tma<16, XM_FWD><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else if (xm == XM_INV) k_exit_wave_tma<16, XM_INV><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else if (h->tma_batch == 32) k_exit_wave_tma<32, XM_FULL><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else k_exit_wave_tma<16, XM_FULL><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     PM_LAUNCHED("k_exit_wave_tma");
+    return PTYCHO_OK;
+}
+
+template <int R, int XM>
+int setup_small_kernel(ptycho_ctx *h, int *per_sm) {
+    const size_t smem = exit_smem_bytes<R>();
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave<R, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_exit_wave<R, XM>, kThreads, smem));
+    if (*per_sm < 1) return pm::fail(PTYCHO_ECUDA, "exit-wave kernel cannot be resident (smem %zu)", smem);
+    h->exit_smem = smem;
     return PTYCHO_OK;
 }
 
 template <int R>
 int setup_exit_kernel(ptycho_ctx *h) {
-    const size_t smem = exit_smem_bytes<R>();
-    PM_CUDA(cudaFuncSetAttribute(k_exit_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, p2 = 0, rc;
     PM_CUDA(cudaGetDevice(&dev));
     PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<R>, kThreads, smem));
-    if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "exit-wave kernel cannot be resident (smem %zu)", smem);
-    h->exit_smem = smem;
+    if (h->Q > 1) {
+        if ((rc = setup_small_kernel<R, XM_FWD>(h, &per_sm))) return rc;
+        if ((rc = setup_small_kernel<R, XM_INV>(h, &p2))) return rc;
+        per_sm = std::min(per_sm, p2);
+    } else if ((rc = setup_small_kernel<R, XM_FULL>(h, &per_sm))) {
+        return rc;
+    }
     h->exit_tma = false;
-    h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
+    h->grid_exit = std::max(1, std::min(h->J * h->Q, sms * per_sm));
     return PTYCHO_OK;
 }
 
 template <int R>
-int launch_exit(ptycho_ctx *h) {
+int launch_exit(ptycho_ctx *h, int xm) {
     ExitArgs a;
     a.obj = h->d_obj;
     a.probe = h->d_probe;
@@ -825,7 +969,10 @@ int launch_exit(ptycho_ctx *h) {
     a.err = h->d_err_pos;
     a.M = h->M;
     a.J = h->J;
-    k_exit_wave<R><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    a.Q = h->Q;
+    if (xm == XM_FWD) k_exit_wave<R, XM_FWD><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    else if (xm == XM_INV) k_exit_wave<R, XM_INV><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    else k_exit_wave<R, XM_FULL><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
     PM_LAUNCHED("k_exit_wave");
     return PTYCHO_OK;
 }
@@ -838,12 +985,28 @@ int setup_exit(ptycho_ctx *h) {
     }
 }
 
-int launch_exit_any(ptycho_ctx *h) {
+int launch_exit_pass(ptycho_ctx *h, int xm) {
     switch (h->R) {
-        case 4: return launch_exit<4>(h);
-        case 8: return launch_exit<8>(h);
-        default: return launch_exit_tma(h);
+        case 4: return launch_exit<4>(h, xm);
+        case 8: return launch_exit<8>(h, xm);
+        default: return launch_exit_tma(h, xm);
     }
+}
+
+// Exit waves of one iteration: the fused kernel (one mode), or forward FFTs of every
+// (position, mode), the mode-summed modulus constraint, inverse FFTs (mixed state).
+// Returns the number of kernel launches through *launches.
+int launch_exit_any(ptycho_ctx *h, int *launches) {
+    int rc;
+    if (h->Q == 1) {
+        *launches = 1;
+        return launch_exit_pass(h, XM_FULL);
+    }
+    *launches = 3;
+    if ((rc = launch_exit_pass(h, XM_FWD))) return rc;
+    k_modulus_modes<<<h->J, kThreads, 0, h->st>>>(h->d_psi, h->d_amp_nat, h->d_err_pos, h->N, h->Q);
+    PM_LAUNCHED("k_modulus_modes");
+    return launch_exit_pass(h, XM_INV);
 }
 
 int stage_begin(ptycho_ctx *h, int s, size_t idx) {
@@ -864,13 +1027,14 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     int rc;
     // exit waves
     if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
-    if ((rc = launch_exit_any(h))) return rc;
-    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, 1))) return rc;
+    int exit_launches = 1;
+    if ((rc = launch_exit_any(h, &exit_launches))) return rc;
+    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, exit_launches))) return rc;
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
     k_object_gather<<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
                                                        h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max, h->M,
-                                                       h->N, h->ntx);
+                                                       h->N, h->ntx, h->Q);
     PM_LAUNCHED("k_object_gather");
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
@@ -881,9 +1045,9 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     // probe
     if ((rc = stage_begin(h, ST_PROBE, ev_base + 2))) return rc;
     if (update_probe) {
-        const int NN = h->N * h->N;
-        k_probe_partial<<<dim3(h->nqt, h->nchunk), kThreads, 0, h->st>>>(h->d_psi, h->d_obj, h->d_pos, h->d_pnum,
-                                                                        h->d_pden, h->M, h->N, h->J, h->per_chunk);
+        const int NN = h->N * h->N * h->Q;                // all probe modes
+        k_probe_partial<<<dim3(h->nqt, h->nchunk, h->Q), kThreads, 0, h->st>>>(
+            h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, h->Q);
         PM_LAUNCHED("k_probe_partial");
         k_probe_reduce<<<h->nred, kThreads, 0, h->st>>>(h->d_pnum, h->d_pden, h->d_num_p, h->d_den_p, h->d_pmax, NN,
                                                         h->nchunk);
@@ -926,7 +1090,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!(d->alpha_O >= 0.f) || !(d->alpha_P >= 0.f) || !std::isfinite(d->alpha_O) || !std::isfinite(d->alpha_P))
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: regularisers must be finite and >= 0");
     if (d->probe_update_start < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_init: probe_update_start < 0");
-    const int M = d->M, N = d->N, J = d->J;
+    if (d->modes < 1 || d->modes > 8) return pm::fail(PTYCHO_EINVAL, "ptycho_init: modes = %d not in [1, 8]", d->modes);
+    const int M = d->M, N = d->N, J = d->J, Q = d->modes;
     for (int j = 0; j < J; ++j) {
         const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
         if (y < 0 || x < 0 || y > M - N || x > M - N)
@@ -934,7 +1099,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     }
     ptycho_ctx *h = new (std::nothrow) ptycho_ctx();
     if (!h) return pm::fail(PTYCHO_ENOMEM, "ptycho_init: host allocation failed");
-    h->M = M; h->N = N; h->J = J; h->R = R;
+    h->M = M; h->N = N; h->J = J; h->R = R; h->Q = Q;
     h->alpha_O = d->alpha_O; h->alpha_P = d->alpha_P;
     h->probe_update_start = d->probe_update_start;
     h->st = (cudaStream_t)d->cuda_stream;
@@ -967,24 +1132,25 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->nqt = ((N + kTW - 1) / kTW) * ((N + kTR - 1) / kTR);
     h->per_chunk = 128;                                  // 16 positions per warp
     h->nchunk = (J + h->per_chunk - 1) / h->per_chunk;
-    h->nred = (int)((NN + kThreads - 1) / kThreads);
+    h->nred = (int)((NN * Q + kThreads - 1) / kThreads);
 
     rc = setup_exit(h);
     if (!rc) rc = dalloc(&h->d_pos, J);
     if (!rc) rc = dalloc(&h->d_obj, MM);
-    if (!rc) rc = dalloc(&h->d_probe, NN);
-    if (!rc) rc = dalloc(&h->d_psi, (size_t)J * NN);
+    if (!rc) rc = dalloc(&h->d_probe, NN * Q);
+    if (!rc) rc = dalloc(&h->d_psi, (size_t)J * Q * NN);
     if (!rc && h->exit_tma) rc = dalloc(&h->d_slot, (size_t)h->grid_exit * NN);
     if (!rc) rc = dalloc(&h->d_status, 1);
     if (!rc) rc = dalloc(&h->d_num_o, MM);
     if (!rc) rc = dalloc(&h->d_den_o, MM);
     if (!rc) rc = dalloc(&h->d_tile_max, h->ntiles);
-    if (!rc) rc = dalloc(&h->d_num_p, NN);
-    if (!rc) rc = dalloc(&h->d_den_p, NN);
-    if (!rc) rc = dalloc(&h->d_pnum, (size_t)h->nchunk * NN);
-    if (!rc) rc = dalloc(&h->d_pden, (size_t)h->nchunk * NN);
+    if (!rc) rc = dalloc(&h->d_num_p, NN * Q);
+    if (!rc) rc = dalloc(&h->d_den_p, NN * Q);
+    if (!rc) rc = dalloc(&h->d_pnum, (size_t)h->nchunk * Q * NN);
+    if (!rc) rc = dalloc(&h->d_pden, (size_t)h->nchunk * Q * NN);
     if (!rc) rc = dalloc(&h->d_pmax, h->nred);
     if (!rc) rc = dalloc(&h->d_amp, (size_t)J * NN);
+    if (!rc && Q > 1) rc = dalloc(&h->d_amp_nat, (size_t)J * NN);
     if (!rc) rc = dalloc(&h->d_err_pos, (size_t)J);
     if (!rc) rc = dalloc(&h->d_a2, J);
     if (!rc) rc = dalloc(&h->d_inv_norm, 1);
@@ -1011,9 +1177,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile lists");
     if ((rc = copy_in_complex(h->d_obj, d->obj0, MM, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
-    if ((rc = copy_in_complex(h->d_probe, d->probe0, NN, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
+    if ((rc = copy_in_complex(h->d_probe, d->probe0, NN * Q, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
     if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st))) return fail_cuda(e, "clear status");
-    k_amplitudes<<<J, kThreads, 0, h->st>>>(d->d_fused, h->d_amp, h->d_a2, N, h->exit_tma ? 16 : 0);
+    k_amplitudes<<<J, kThreads, 0, h->st>>>(d->d_fused, h->d_amp, h->d_amp_nat, h->d_a2, N, h->exit_tma ? 16 : 0);
     if ((e = cudaGetLastError())) return fail_cuda(e, "k_amplitudes");
     k_inv_norm<<<1, kThreads, 0, h->st>>>(h->d_a2, J, h->d_inv_norm);
     if ((e = cudaGetLastError())) return fail_cuda(e, "k_inv_norm");
@@ -1088,7 +1254,7 @@ extern "C" int ptycho_get_object(ptycho_handle h, void *dst, int dst_on_device) 
 
 extern "C" int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device) {
     if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_get_probe: NULL handle");
-    return get_complex(h, h->d_probe, (size_t)h->N * h->N, dst, dst_on_device);
+    return get_complex(h, h->d_probe, (size_t)h->Q * h->N * h->N, dst, dst_on_device);
 }
 
 extern "C" void ptycho_destroy(ptycho_handle h) { free_ctx(h); }

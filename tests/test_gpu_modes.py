@@ -1,0 +1,86 @@
+"""Mixed-state reconstruction (Eq. 4 with a discrete spectrum, 8 probe modes): CUDA FP32 vs the
+FP64 oracle through the C ABI, fed the same fused intensities (the oracle's fusion, in FP32)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_01746_b300 import synth
+from tests.parity_helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_01746_b300 import api as a
+    a.lib()
+    return a
+
+
+def noisy_start(M, seed=0):
+    rng = np.random.default_rng(seed)
+    return (1.0 + 0.1 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))).astype(np.complex64)
+
+
+def run(api, sc, fused32, n_iter, pus):
+    M = sc["cfg"].M
+    obj0 = noisy_start(M)
+    probes0 = sc["probe"].astype(np.complex64)
+    h = api.ptycho_init(torch.from_numpy(fused32).cuda(), sc["pos"], obj0, probes0, probe_update_start=pus)
+    e = api.ptycho_iterate(h, n_iter)
+    o = api.ptycho_get_object(h)
+    p = api.ptycho_get_probe(h)
+    api.ptycho_destroy(h)
+    ro, rp, re = oracle.reconstruct_modes(fused32.astype(np.float64), sc["pos"], obj0.astype(np.complex128),
+                                          probes0.astype(np.complex128), n_iter, 1e-3, 1e-3, pus)
+    return (o, p, e), (ro, rp, re)
+
+
+@pytest.mark.parametrize("n_iter,pus", [(10, 0), (10, 10**6)])
+def test_mixed_state_small_matches_oracle(api, n_iter, pus):
+    sc = synth.make_scan("mixed_small")
+    cfg = sc["cfg"]
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    fused = oracle.mnf_stack(sc["raw"], sc["times"], p).astype(np.float32)
+    (o, pr, e), (ro, rp, re) = run(api, sc, fused, n_iter, pus)
+    assert pr.shape == (8, 64, 64)
+    assert rel_l2(o, ro) <= 1e-5
+    assert rel_l2(pr, rp) <= 1e-5
+    np.testing.assert_allclose(e, re, rtol=1e-5)
+
+
+def test_mixed_state_256_matches_oracle(api):
+    """The N = 256 forward / modulus / inverse kernels: lab geometry, 120 positions, 4 modes,
+    two iterations."""
+    cfg = dataclasses.replace(synth.CONFIGS["mixed"], J=120, modes=4, name="mixed120")
+    sc = synth.make_scan_torch(cfg, seed=77, device="cuda")
+    params = api.fuse_params(levels=cfg.levels, clip=float(cfg.clip))
+    fused = api.fuse_stack(sc["raw"], cfg.times, params)
+    torch.cuda.synchronize()
+    fused = fused.cpu().numpy()
+    del sc["raw"]
+    (o, pr, e), (ro, rp, re) = run(api, sc, fused, 2, 0)
+    assert pr.shape == (4, 256, 256)
+    assert rel_l2(o, ro) <= 1e-5
+    assert rel_l2(pr, rp) <= 1e-5
+    np.testing.assert_allclose(e, re, rtol=1e-5)
+
+
+def test_mixed_state_stage_launches(api):
+    sc = synth.make_scan("mixed_small")
+    cfg = sc["cfg"]
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    fused = oracle.mnf_stack(sc["raw"][:10], sc["times"], p).astype(np.float32)
+    h = api.ptycho_init(torch.from_numpy(fused).cuda(), sc["pos"][:10], noisy_start(cfg.M),
+                        sc["probe"].astype(np.complex64))
+    api.ptycho_set_timing(h, True)
+    api.ptycho_iterate(h, 2)
+    _, launches = api.ptycho_stage_times(h)
+    assert launches == [6, 4, 6, 2]          # forward, modulus, inverse per iteration
+    api.ptycho_destroy(h)
