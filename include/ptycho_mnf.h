@@ -92,7 +92,28 @@ int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
 int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
                        const fuse_params *p, float *d_fused, void *cuda_stream);
 
+/*
+ * fuse_sli -- Standard Linear Integration, the linear HDR comparator the paper evaluates MNF
+ * against (§1, §2.2, "SLI"): per pixel t_max * sum_{k: I_k < clip} I_k / sum_{k: I_k < clip} t_k
+ * (count rate over the unsaturated exposures, in longest-exposure units); a pixel saturated in
+ * every exposure takes the shortest exposure's clipped rate.  Same raw / output layouts as
+ * fuse_stack, any N in [1, 4096], 1 <= K <= 8.  Allocates nothing.  Asynchronous.
+ */
+int fuse_sli(const uint16_t *d_raw, int J, int K, int N, const float *h_t, float clip, float *d_fused,
+             void *cuda_stream);
+
 typedef struct ptycho_ctx *ptycho_handle;
+
+/* Reconstruction engines (the paper cites PIE / ePIE / difference map without choosing one):
+ *   AP           full-batch alternating projections (default): all exit waves from the same
+ *                (O, P), least-squares object update, then least-squares probe update.
+ *   EPIE_COLOUR  ePIE (Maiden and Rodenburg 2009) run colour by colour: positions are coloured
+ *                greedily in index order so that patches of one colour never overlap; per
+ *                colour, every member's exit-wave update Delta = psi' - P O_j is computed from
+ *                the current (O, P), O_j += alpha conj(P) Delta / max|P|^2 is scattered without
+ *                atomics (disjoint patches), and P += (beta / n_colour) sum conj(O_j) Delta /
+ *                max|O_j|^2.  One probe mode only. */
+enum { PTYCHO_ALG_AP = 0, PTYCHO_ALG_EPIE_COLOUR = 1 };
 
 typedef struct {
     int M;                  /* object side (M x M complex64), M >= N                          */
@@ -109,6 +130,9 @@ typedef struct {
     float alpha_O;          /* object regulariser relative to max sum_j |P|^2 (>= 0)          */
     float alpha_P;          /* probe regulariser relative to max sum_j |O_j|^2 (>= 0)         */
     int probe_update_start; /* first iteration (counted from init) that updates the probe     */
+    int algorithm;          /* PTYCHO_ALG_AP (default) or PTYCHO_ALG_EPIE_COLOUR              */
+    float epie_alpha;       /* ePIE object step (> 0; 1 is standard), EPIE_COLOUR only        */
+    float epie_beta;        /* ePIE probe step (>= 0; 1 is standard), EPIE_COLOUR only        */
     void *cuda_stream;      /* stream for all work of this handle                             */
 } ptycho_desc;
 
@@ -140,6 +164,9 @@ int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err);
  * a device pointer if dst_on_device else a host pointer.  A host copy synchronises the stream. */
 int ptycho_get_object(ptycho_handle h, void *dst, int dst_on_device);
 int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device);
+
+/* EPIE_COLOUR handles: the colour of every position (host [J]) and the number of colours. */
+int ptycho_get_colouring(ptycho_handle h, int32_t *h_colour, int *n_colours);
 
 /* Release every device resource of the handle (waits for its stream).  NULL is a no-op. */
 void ptycho_destroy(ptycho_handle h);

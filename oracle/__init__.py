@@ -12,16 +12,18 @@ reconstruction on noisy fused data (time to a given NRMSE), which depends on unp
 constants and is reported, not pinned ("parity unpinned" for that figure only).
 """
 from .mnf import FuseParams, exposure_weights, radiance, blur_down, upsample, \
-    gaussian_pyramid, laplacian_pyramid, quantise, mnf_position, mnf_stack
+    gaussian_pyramid, laplacian_pyramid, quantise, mnf_position, mnf_stack, sli_position, \
+    sli_stack
 from .ptycho import fft2u, ifft2u, amplitudes, modulus_projection, reconstruct, \
     iterate_once, exit_wave_update, object_update, probe_update, illumination, nrmse, \
-    fourier_error, modes_modulus_projection, iterate_once_modes, reconstruct_modes
+    fourier_error, modes_modulus_projection, iterate_once_modes, reconstruct_modes, \
+    greedy_colouring, epie_by_colour
 
 __all__ = [
-    "FuseParams", "exposure_weights", "radiance", "blur_down", "upsample", "gaussian_pyramid",
+    "FuseParams", "sli_position", "sli_stack", "exposure_weights", "radiance", "blur_down", "upsample", "gaussian_pyramid",
     "laplacian_pyramid", "quantise", "mnf_position", "mnf_stack", "fft2u", "ifft2u",
     "amplitudes", "modulus_projection", "reconstruct", "iterate_once", "exit_wave_update",
     "object_update", "probe_update",
     "illumination", "nrmse", "fourier_error", "modes_modulus_projection", "iterate_once_modes",
-    "reconstruct_modes",
+    "reconstruct_modes", "greedy_colouring", "epie_by_colour",
 ]

@@ -166,3 +166,23 @@ def mnf_stack(raw: np.ndarray, times, p: FuseParams) -> np.ndarray:
     """Positions are independent (§3.4): fuse raw[J][K][N][N] -> I_MNF[J][N][N]."""
     raw = np.asarray(raw)
     return np.stack([mnf_position(raw[j], times, p) for j in range(raw.shape[0])])
+
+
+def sli_position(raw: np.ndarray, times, clip: float) -> np.ndarray:
+    """Standard Linear Integration, the linear HDR baseline the paper compares against (§1,
+    §2.2): per pixel, the exposure-time-weighted mean count rate over the unsaturated exposures,
+    in longest-exposure units, t_max * sum_{k: I_k < clip} I_k / sum_{k: I_k < clip} t_k.  A
+    pixel saturated in every exposure takes the shortest exposure's clipped rate."""
+    raw = np.asarray(raw, dtype=np.float64)
+    t = np.asarray(times, dtype=np.float64)
+    ok = raw < clip
+    num = np.sum(np.where(ok, raw, 0.0), axis=0)
+    den = np.sum(np.where(ok, t[:, None, None], 0.0), axis=0)
+    kmin = int(np.argmin(t))
+    fallback = raw[kmin] / t[kmin]
+    return t.max() * np.where(den > 0, num / np.where(den > 0, den, 1.0), fallback)
+
+
+def sli_stack(raw: np.ndarray, times, clip: float) -> np.ndarray:
+    raw = np.asarray(raw)
+    return np.stack([sli_position(raw[j], times, clip) for j in range(raw.shape[0])])

@@ -241,3 +241,70 @@ def reconstruct_modes(fused, pos, obj0, probes0, n_iter: int, alpha_O: float = 1
                                             it >= probe_update_start)
         errs[it] = e / norm if norm > 0 else 0.0
     return obj, probes, errs
+
+
+# ---------------------------------------------------------------------------------------------
+# ePIE by colour (the paper cites ePIE, Maiden and Rodenburg 2009, among its iterative engines;
+# it gives no schedule).  Reading used here:
+#   colouring: greedy in position order -- position j takes the smallest colour not taken by an
+#              earlier position whose N x N patch overlaps its own (|dy| < N and |dx| < N);
+#   per iteration, colours in ascending order; for every position j of the colour, from the
+#   current (O, P):
+#       psi = P O_j,  Psi = F psi,  e += sum_q (|Psi| - A_j)^2,  Delta_j = F^-1 proj(Psi) - psi
+#       O_j <- O_j + alpha conj(P) Delta_j / max |P|^2          (patches of a colour are disjoint)
+#       P   <- P + (beta / n_c) sum_{j in colour} conj(O_j) Delta_j / max |O_j|^2
+#   with O_j the patch before the colour's object update and n_c the colour's size.
+
+def greedy_colouring(pos, N: int) -> np.ndarray:
+    """Smallest colour not used by an earlier overlapping position, in position order."""
+    pos = np.asarray(pos)
+    J = len(pos)
+    colour = np.full(J, -1, dtype=np.int64)
+    for j in range(J):
+        taken = set()
+        for i in range(j):
+            if abs(int(pos[i][0]) - int(pos[j][0])) < N and abs(int(pos[i][1]) - int(pos[j][1])) < N:
+                taken.add(int(colour[i]))
+        c = 0
+        while c in taken:
+            c += 1
+        colour[j] = c
+    return colour
+
+
+def epie_by_colour(fused, pos, obj0, probe0, n_iter: int, alpha: float = 1.0, beta: float = 1.0,
+                   probe_update_start: int = 0, A=None):
+    """Returns (obj, probe, errors[n_iter]) with errors normalised by sum_j sum_q A_j^2."""
+    if A is None:
+        A = amplitudes(fused)
+    obj = np.asarray(obj0, dtype=np.complex128).copy()
+    probe = np.asarray(probe0, dtype=np.complex128).copy()
+    pos = np.asarray(pos)
+    N = probe.shape[0]
+    colour = greedy_colouring(pos, N)
+    norm = float(np.sum(A * A))
+    errs = np.empty(n_iter)
+    for it in range(n_iter):
+        err = 0.0
+        for c in range(int(colour.max()) + 1):
+            members = np.nonzero(colour == c)[0]
+            deltas, patches = [], []
+            for j in members:
+                y, x = int(pos[j][0]), int(pos[j][1])
+                oj = obj[y:y + N, x:x + N].copy()
+                psi = probe * oj
+                Psi = fft2u(psi)
+                err += fourier_error(Psi, A[j])
+                deltas.append(ifft2u(modulus_projection(Psi, A[j])) - psi)
+                patches.append(oj)
+            pmax = np.max(np.abs(probe) ** 2)
+            for j, d in zip(members, deltas):
+                y, x = int(pos[j][0]), int(pos[j][1])
+                obj[y:y + N, x:x + N] += alpha * np.conj(probe) * d / pmax
+            if it >= probe_update_start:
+                step = np.zeros_like(probe)
+                for oj, d in zip(patches, deltas):
+                    step += np.conj(oj) * d / np.max(np.abs(oj) ** 2)
+                probe = probe + (beta / len(members)) * step
+        errs[it] = err / norm if norm > 0 else 0.0
+    return obj, probe, errs

@@ -22,10 +22,11 @@ PTYCHO_ENONFINITE = -4
 PTYCHO_ETIMEDOUT = -5
 
 BASE_MODES = {"mean": 0, "sum": 1, "weighted": 2}
+ALGORITHMS = {"ap": 0, "epie_colour": 1}
 DOMAINS = {"radiance": 0, "raw": 1}
 
-EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "ptycho_init", "ptycho_iterate", "ptycho_get_object", "ptycho_get_probe",
-           "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
+EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "fuse_sli", "ptycho_init", "ptycho_iterate",
+           "ptycho_get_object", "ptycho_get_probe", "ptycho_get_colouring", "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
 
 
 class FuseParamsC(ctypes.Structure):
@@ -40,7 +41,8 @@ class PtychoDescC(ctypes.Structure):
                 ("obj0", ctypes.c_void_p), ("probe0", ctypes.c_void_p),
                 ("init_on_device", ctypes.c_int), ("alpha_O", ctypes.c_float),
                 ("alpha_P", ctypes.c_float), ("probe_update_start", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("algorithm", ctypes.c_int), ("epie_alpha", ctypes.c_float),
+                ("epie_beta", ctypes.c_float), ("cuda_stream", ctypes.c_void_p)]
 
 
 class PtychoError(RuntimeError):
@@ -71,6 +73,8 @@ def lib() -> ctypes.CDLL:
     L.fuse_stack.restype = ci
     L.fuse_stack_noalloc.argtypes = L.fuse_stack.argtypes
     L.fuse_stack_noalloc.restype = ci
+    L.fuse_sli.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp]
+    L.fuse_sli.restype = ci
     L.ptycho_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PtychoDescC)]
     L.ptycho_init.restype = ci
     L.ptycho_iterate.argtypes = [vp, ci, ctypes.POINTER(cd)]
@@ -79,6 +83,8 @@ def lib() -> ctypes.CDLL:
     L.ptycho_get_object.restype = ci
     L.ptycho_get_probe.argtypes = [vp, vp, ci]
     L.ptycho_get_probe.restype = ci
+    L.ptycho_get_colouring.argtypes = [vp, vp, ctypes.POINTER(ci)]
+    L.ptycho_get_colouring.restype = ci
     L.ptycho_destroy.argtypes = [vp]
     L.ptycho_destroy.restype = None
     L.ptycho_set_timing.argtypes = [vp, ci]
@@ -147,6 +153,20 @@ def fuse_stack_noalloc(raw, times, params: FuseParamsC, out, stream=None):
     return out
 
 
+def fuse_sli(raw, times, clip: float, out=None, stream=None):
+    """Standard Linear Integration of raw[J][K][N][N] (torch.uint16 CUDA) into out[J][N][N]."""
+    import torch
+    if raw.dtype != torch.uint16 or not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw must be a contiguous torch.uint16 CUDA tensor [J][K][N][N]")
+    J, K, N, _ = raw.shape
+    if out is None:
+        out = torch.empty((J, N, N), dtype=torch.float32, device=raw.device)
+    t = (ctypes.c_float * K)(*[float(x) for x in times])
+    _check(lib().fuse_sli(ctypes.c_void_p(raw.data_ptr()), J, K, N, t, float(clip),
+                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
 class PtychoHandle:
     """Owner of a ``ptycho_handle``; ``close()`` (or garbage collection) destroys it."""
 
@@ -167,7 +187,8 @@ class PtychoHandle:
 
 
 def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float = 1e-3,
-                probe_update_start: int = 0, stream=None) -> PtychoHandle:
+                probe_update_start: int = 0, stream=None, algorithm: str = "ap",
+                epie_alpha: float = 1.0, epie_beta: float = 1.0) -> PtychoHandle:
     """fused: float32 CUDA tensor [J][N][N]; pos: int [J][2] (y, x); obj0 / probe0: complex64,
     both numpy (host) or both torch CUDA tensors (device); probe0 is [N][N] (one mode) or
     [Q][N][N] (Q incoherent modes)."""
@@ -192,7 +213,8 @@ def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float 
     M = obj0.shape[0]
     Q = probe0.shape[0] if len(probe0.shape) == 3 else 1
     desc = PtychoDescC(M, N, J, Q, pos.ctypes.data, fused.data_ptr(), op, pp, 1 if on_dev else 0,
-                       alpha_O, alpha_P, probe_update_start, _stream_ptr(stream))
+                       alpha_O, alpha_P, probe_update_start, ALGORITHMS[algorithm], epie_alpha,
+                       epie_beta, _stream_ptr(stream))
     h = ctypes.c_void_p()
     _check(lib().ptycho_init(ctypes.byref(h), ctypes.byref(desc)))
     return PtychoHandle(h.value, M, N, J, Q)
@@ -230,6 +252,14 @@ def ptycho_get_object(h: PtychoHandle, out=None):
 def ptycho_get_probe(h: PtychoHandle, out=None):
     shape = (h.N, h.N) if h.Q == 1 else (h.Q, h.N, h.N)
     return _get(lib().ptycho_get_probe, h, shape, out)
+
+
+def ptycho_get_colouring(h: PtychoHandle):
+    """(colour per position, number of colours) of an ePIE-by-colour handle."""
+    col = np.empty(h.J, dtype=np.int32)
+    n = ctypes.c_int()
+    _check(lib().ptycho_get_colouring(h.ptr, ctypes.c_void_p(col.ctypes.data), ctypes.byref(n)))
+    return col, n.value
 
 
 def ptycho_destroy(h: PtychoHandle) -> None:

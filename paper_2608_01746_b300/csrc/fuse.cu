@@ -478,3 +478,60 @@ extern "C" int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, co
     }
     return rc;
 }
+
+// ---------------------------------------------------------------------------------------
+// Standard Linear Integration (the linear HDR comparator of §1 and §2.2): per pixel,
+// t_max * sum_{k: I_k < clip} I_k / sum_{k: I_k < clip} t_k; a pixel saturated in every
+// exposure takes the shortest exposure's clipped rate.  One thread per (position, pixel).
+namespace {
+
+struct SliDev {
+    float t[kMaxK];
+    float tmax, clip;
+    int kmin;
+};
+
+__global__ void k_sli(const uint16_t *__restrict__ raw, float *__restrict__ out, int K, size_t NN, size_t total,
+                      SliDev s) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = i / NN, p = i % NN;
+        const uint16_t *rj = raw + j * K * NN + p;
+        float num = 0.f, den = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const float v = (float)__ldg(rj + k * NN);
+            if (v < s.clip) {
+                num += v;
+                den += s.t[k];
+            }
+        }
+        out[i] = den > 0.f ? s.tmax * (num / den) : s.tmax * ((float)__ldg(rj + s.kmin * NN) / s.t[s.kmin]);
+    }
+}
+
+}  // namespace
+
+extern "C" int fuse_sli(const uint16_t *d_raw, int J, int K, int N, const float *h_t, float clip, float *d_out,
+                        void *cuda_stream) {
+    if (J < 0) return pm::fail(PTYCHO_EINVAL, "fuse_sli: J = %d < 0", J);
+    if (K < 1 || K > kMaxK) return pm::fail(PTYCHO_EINVAL, "fuse_sli: K = %d not in [1, %d]", K, kMaxK);
+    if (N < 1 || N > 4096) return pm::fail(PTYCHO_EINVAL, "fuse_sli: N = %d not in [1, 4096]", N);
+    if (!(clip > 0.f) || !std::isfinite(clip)) return pm::fail(PTYCHO_EINVAL, "fuse_sli: clip must be finite and > 0");
+    if (!h_t) return pm::fail(PTYCHO_EINVAL, "fuse_sli: exposure times pointer is NULL");
+    SliDev s{};
+    s.tmax = 0.f;
+    s.kmin = 0;
+    for (int k = 0; k < K; ++k) {
+        if (!(h_t[k] > 0.f) || !std::isfinite(h_t[k]))
+            return pm::fail(PTYCHO_EINVAL, "fuse_sli: t[%d] = %g must be finite and > 0", k, (double)h_t[k]);
+        s.t[k] = h_t[k];
+        s.tmax = std::max(s.tmax, h_t[k]);
+        if (h_t[k] < h_t[s.kmin]) s.kmin = k;
+    }
+    s.clip = clip;
+    if (J == 0) return PTYCHO_OK;
+    if (!d_raw || !d_out) return pm::fail(PTYCHO_EINVAL, "fuse_sli: NULL raw or output pointer");
+    const size_t NN = (size_t)N * N, total = (size_t)J * NN;
+    k_sli<<<grid_for(total, 256), 256, 0, (cudaStream_t)cuda_stream>>>(d_raw, d_out, K, NN, total, s);
+    PM_LAUNCHED("k_sli");
+    return PTYCHO_OK;
+}

@@ -50,6 +50,8 @@ struct ExitArgs {
     const int2 *pos;         // (y, x)
     float2 *psi;             // [J][Q][N][N] row-major
     double *err;             // [J] Fourier error per position (XM_FULL)
+    const int *list;         // XM_FULL: if not NULL, process positions list[0 .. count)
+    int count;
     int M, J, Q;
 };
 
@@ -88,9 +90,10 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     float2 *xb = xb_all + g * R * (R + 1);
     const float invN = 1.0f / (float)N;
     const int M = a.M;
-    const int units = (XM == XM_FULL) ? a.J : a.J * a.Q;
+    const int units = (XM == XM_FULL) ? (a.list ? a.count : a.J) : a.J * a.Q;
 
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
+        const int u = (XM == XM_FULL && a.list) ? a.list[iu] : iu;
         const int j = (XM == XM_FULL) ? u : u / a.Q;
         const int mode = (XM == XM_FULL) ? 0 : u % a.Q;
         float2 *psi_u = a.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
@@ -240,6 +243,8 @@ struct TmaArgs {
     const int2 *pos;
     double *err;             // [J] Fourier error per position (XM_FULL)
     int *status;             // set to 1 if a bounded wait gave up
+    const int *list;         // XM_FULL: if not NULL, process positions list[0 .. count)
+    int count;
     int M, J, Q;
 };
 
@@ -322,8 +327,9 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         }
     };
 
-    const int units = (XM == XM_FULL) ? a.J : a.J * a.Q;
-    for (int u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+    const int units = (XM == XM_FULL) ? (a.list ? a.count : a.J) : a.J * a.Q;
+    for (int iu = blockIdx.x; iu < units && !failed; iu += gridDim.x) {
+        const int u = (XM == XM_FULL && a.list) ? a.list[iu] : iu;
         const int j = (XM == XM_FULL) ? u : u / a.Q;
         const int prow0 = (XM == XM_FULL) ? 0 : (u % a.Q) * N;    // first probe row of the mode
         float err = 0.f;
@@ -592,6 +598,56 @@ __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     }
 }
 
+// ePIE by colour, object step for the positions list[0 .. n) of one colour (disjoint patches,
+// so the scatter needs no atomics): one block per position j, from psi_j' (exit-wave kernel):
+//   Delta = psi_j' - P O_j;  O_j += alpha conj(P) Delta / max |P|^2
+//   part[u] = conj(O_j) Delta / max |O_j|^2   (O_j before the step; the probe step's summand)
+__global__ void __launch_bounds__(kThreads) k_epie_object(float2 *__restrict__ obj, const float2 *__restrict__ probe,
+                                                          const float2 *__restrict__ psi, const int2 *__restrict__ pos,
+                                                          const int *__restrict__ list, float2 *__restrict__ part,
+                                                          int M, int N, float alpha) {
+    __shared__ float s_mp[kThreads / 32], s_mo[kThreads / 32];
+    const int u = blockIdx.x, j = list[u];
+    const int2 pj = pos[j];
+    const size_t NN = (size_t)N * N;
+    float mp = 0.f, mo = 0.f;
+    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
+        mp = fmaxf(mp, cabs2(probe[q]));
+        mo = fmaxf(mo, cabs2(obj[(size_t)(pj.x + q / N) * M + pj.y + q % N]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+        mo = fmaxf(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_mp[threadIdx.x >> 5] = mp; s_mo[threadIdx.x >> 5] = mo; }
+    __syncthreads();
+    mp = 0.f;
+    mo = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) { mp = fmaxf(mp, s_mp[w]); mo = fmaxf(mo, s_mo[w]); }
+    const float so = mp > 0.f ? alpha / mp : 0.f;
+    const float sp = mo > 0.f ? 1.0f / mo : 0.f;
+    const float2 *psi_j = psi + (size_t)j * NN;
+    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
+        float2 *op = obj + (size_t)(pj.x + q / N) * M + pj.y + q % N;
+        const float2 p = probe[q];
+        const float2 o = *op;
+        const float2 d = csub(psi_j[q], cmul(p, o));
+        *op = cadd(o, cscale(cmulc(p, d), so));
+        part[(size_t)u * NN + q] = cscale(cmulc(o, d), sp);
+    }
+}
+
+// ePIE by colour, probe step: P += (beta / n) sum_{u < n} part[u] (fixed order).
+__global__ void __launch_bounds__(kThreads) k_epie_probe(float2 *__restrict__ probe, const float2 *__restrict__ part,
+                                                         int n, size_t NN, float scale) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NN; q += (size_t)gridDim.x * blockDim.x) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int u = 0; u < n; ++u) acc = cadd(acc, part[(size_t)u * NN + q]);
+        probe[q] = cadd(probe[q], cscale(acc, scale));
+    }
+}
+
 __device__ float block_max(const float *v, int n) {
     __shared__ float s[kThreads / 32];
     float m = 0.f;
@@ -768,6 +824,13 @@ __global__ void k_inv_norm(const double *__restrict__ a2, int J, double *__restr
 
 struct ptycho_ctx {
     int M = 0, N = 0, J = 0, R = 0, Q = 1;
+    int algorithm = PTYCHO_ALG_AP;
+    float epie_alpha = 1.f, epie_beta = 1.f;
+    std::vector<int> colour_start, colour_of;             // ePIE: colour c = list[start[c] .. start[c+1])
+    int *d_colour_list = nullptr;
+    float2 *d_epie_part = nullptr;
+    const int *cur_list = nullptr;                        // exit-wave launches: unit list or NULL
+    int cur_count = 0;
     float alpha_O = 0.f, alpha_P = 0.f;
     int probe_update_start = 0;
     long long iter = 0;
@@ -812,7 +875,8 @@ void free_ctx(ptycho_ctx *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
-                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status, h->d_torder};
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status, h->d_torder,
+                    h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -915,6 +979,8 @@ TmaArgs tma_args(ptycho_ctx *h) {
     a.pos = h->d_pos;
     a.err = h->d_err_pos;
     a.status = h->d_status;
+    a.list = h->cur_list;
+    a.count = h->cur_count;
     a.M = h->M;
     a.J = h->J;
     a.Q = h->Q;
@@ -967,6 +1033,8 @@ int launch_exit(ptycho_ctx *h, int xm) {
     a.pos = h->d_pos;
     a.psi = h->d_psi;
     a.err = h->d_err_pos;
+    a.list = h->cur_list;
+    a.count = h->cur_count;
     a.M = h->M;
     a.J = h->J;
     a.Q = h->Q;
@@ -1023,7 +1091,47 @@ int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
     return PTYCHO_OK;
 }
 
+// ePIE by colour: colours in ascending order; per colour the fused exit-wave kernel on the
+// colour's positions, the object step (disjoint patches, no atomics) and the averaged probe
+// step.  The whole colour loop is timed as stage 0.
+int iterate_one_epie(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe) {
+    int rc;
+    if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
+    const size_t NN = (size_t)h->N * h->N;
+    const int ncol = (int)h->colour_start.size() - 1;
+    int launches = 0;
+    for (int c = 0; c < ncol; ++c) {
+        const int b = h->colour_start[c], n = h->colour_start[c + 1] - b;
+        h->cur_list = h->d_colour_list + b;
+        h->cur_count = n;
+        rc = launch_exit_pass(h, XM_FULL);
+        h->cur_list = nullptr;
+        h->cur_count = 0;
+        if (rc) return rc;
+        k_epie_object<<<n, kThreads, 0, h->st>>>(h->d_obj, h->d_probe, h->d_psi, h->d_pos, h->d_colour_list + b,
+                                                 h->d_epie_part, h->M, h->N, h->epie_alpha);
+        PM_LAUNCHED("k_epie_object");
+        launches += 2;
+        if (update_probe) {
+            const unsigned gp = (unsigned)std::min<size_t>((NN + kThreads - 1) / kThreads, 148 * 4);
+            k_epie_probe<<<gp, kThreads, 0, h->st>>>(h->d_probe, h->d_epie_part, n, NN, h->epie_beta / n);
+            PM_LAUNCHED("k_epie_probe");
+            ++launches;
+        }
+    }
+    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, launches))) return rc;
+    for (int st = ST_OBJECT; st <= ST_PROBE; ++st) {
+        if ((rc = stage_begin(h, st, ev_base + st))) return rc;
+        if ((rc = stage_end(h, st, ev_base + st, 0))) return rc;
+    }
+    if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
+    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, h->d_err + it_in_call);
+    PM_LAUNCHED("k_error_reduce");
+    return stage_end(h, ST_ERROR, ev_base + 3, 1);
+}
+
 int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe) {
+    if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) return iterate_one_epie(h, it_in_call, ev_base, update_probe);
     int rc;
     // exit waves
     if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
@@ -1091,6 +1199,13 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: regularisers must be finite and >= 0");
     if (d->probe_update_start < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_init: probe_update_start < 0");
     if (d->modes < 1 || d->modes > 8) return pm::fail(PTYCHO_EINVAL, "ptycho_init: modes = %d not in [1, 8]", d->modes);
+    if (d->algorithm != PTYCHO_ALG_AP && d->algorithm != PTYCHO_ALG_EPIE_COLOUR)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: unknown algorithm %d", d->algorithm);
+    if (d->algorithm == PTYCHO_ALG_EPIE_COLOUR && d->modes != 1)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: ePIE by colour supports one probe mode");
+    if (d->algorithm == PTYCHO_ALG_EPIE_COLOUR &&
+        (!std::isfinite(d->epie_alpha) || !std::isfinite(d->epie_beta) || !(d->epie_alpha > 0.f) || !(d->epie_beta >= 0.f)))
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: ePIE step sizes must be finite, alpha > 0, beta >= 0");
     const int M = d->M, N = d->N, J = d->J, Q = d->modes;
     for (int j = 0; j < J; ++j) {
         const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
@@ -1100,6 +1215,37 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     ptycho_ctx *h = new (std::nothrow) ptycho_ctx();
     if (!h) return pm::fail(PTYCHO_ENOMEM, "ptycho_init: host allocation failed");
     h->M = M; h->N = N; h->J = J; h->R = R; h->Q = Q;
+    h->algorithm = d->algorithm;
+    h->epie_alpha = d->epie_alpha;
+    h->epie_beta = d->epie_beta;
+    std::vector<int> colour_list;
+    int max_colour_size = 0;
+    if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
+        // greedy colouring in position order: smallest colour unused by an earlier overlapping position
+        h->colour_of.assign(J, -1);
+        int ncol = 0;
+        std::vector<char> taken;
+        for (int j = 0; j < J; ++j) {
+            taken.assign(ncol + 1, 0);
+            const int yj = d->h_pos[2 * j], xj = d->h_pos[2 * j + 1];
+            for (int i = 0; i < j; ++i)
+                if (std::abs(d->h_pos[2 * i] - yj) < N && std::abs(d->h_pos[2 * i + 1] - xj) < N)
+                    taken[h->colour_of[i]] = 1;
+            int c = 0;
+            while (taken[c]) ++c;
+            h->colour_of[j] = c;
+            ncol = std::max(ncol, c + 1);
+        }
+        h->colour_start.assign(ncol + 1, 0);
+        for (int j = 0; j < J; ++j) ++h->colour_start[h->colour_of[j] + 1];
+        for (int c = 0; c < ncol; ++c) {
+            max_colour_size = std::max(max_colour_size, h->colour_start[c + 1]);
+            h->colour_start[c + 1] += h->colour_start[c];
+        }
+        colour_list.resize(J);
+        std::vector<int> fill(h->colour_start.begin(), h->colour_start.end() - 1);
+        for (int j = 0; j < J; ++j) colour_list[fill[h->colour_of[j]]++] = j;
+    }
     h->alpha_O = d->alpha_O; h->alpha_P = d->alpha_P;
     h->probe_update_start = d->probe_update_start;
     h->st = (cudaStream_t)d->cuda_stream;
@@ -1157,6 +1303,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
     if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
     if (!rc) rc = dalloc(&h->d_torder, (size_t)h->ntiles);
+    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_colour_list, (size_t)J);
+    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_epie_part, (size_t)max_colour_size * NN);
     if (!rc && h->exit_tma) rc = encode_exit_tma(h);
     if (rc) { free_ctx(h); return rc; }
     auto fail_cuda = [&](cudaError_t e, const char *what) {
@@ -1173,6 +1321,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         return fail_cuda(e, "copy tile starts");
     if ((e = cudaMemcpyAsync(h->d_torder, torder.data(), torder.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile order");
+    if (h->d_colour_list &&
+        (e = cudaMemcpyAsync(h->d_colour_list, colour_list.data(), J * sizeof(int), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy colour lists");
     if (!tlist.empty() &&
         (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile lists");
@@ -1269,5 +1420,14 @@ extern "C" int ptycho_set_timing(ptycho_handle h, int enable) {
 extern "C" int ptycho_stage_times(ptycho_handle h, double *ms, long long *launches) {
     if (!h || !ms || !launches) return pm::fail(PTYCHO_EINVAL, "ptycho_stage_times: NULL argument");
     for (int s = 0; s < ST_COUNT; ++s) { ms[s] = h->stage_ms[s]; launches[s] = h->stage_launches[s]; }
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_get_colouring(ptycho_handle h, int32_t *h_colour, int *n_colours) {
+    if (!h || !h_colour || !n_colours) return pm::fail(PTYCHO_EINVAL, "ptycho_get_colouring: NULL argument");
+    if (h->algorithm != PTYCHO_ALG_EPIE_COLOUR)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_get_colouring: the handle does not use ePIE by colour");
+    for (int j = 0; j < h->J; ++j) h_colour[j] = h->colour_of[j];
+    *n_colours = (int)h->colour_start.size() - 1;
     return PTYCHO_OK;
 }

@@ -77,13 +77,15 @@ def test_fuse_stack_zero_positions_is_noop(L):
 def _desc(**kw):
     pos = np.zeros((4, 2), np.int32)
     d = dict(M=128, N=64, J=4, modes=1, h_pos=pos.ctypes.data, d_fused=16, obj0=16, probe0=16,
-             init_on_device=1, alpha_O=1e-3, alpha_P=1e-3, probe_update_start=0, cuda_stream=None)
+             init_on_device=1, alpha_O=1e-3, alpha_P=1e-3, probe_update_start=0, algorithm=0,
+             epie_alpha=1.0, epie_beta=1.0, cuda_stream=None)
     d.update(kw)
     return api.PtychoDescC(**d), pos
 
 
 @pytest.mark.parametrize("kw", [{"N": 32}, {"N": 128}, {"J": 0}, {"M": 32}, {"alpha_O": -1.0},
-                                {"modes": 0}, {"modes": 9},
+                                {"modes": 0}, {"modes": 9}, {"algorithm": 2},
+                                {"algorithm": 1, "modes": 2}, {"algorithm": 1, "epie_alpha": 0.0},
                                 {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None}])
 def test_ptycho_init_rejects_bad_arguments(L, kw):
     d, _pos = _desc(**kw)

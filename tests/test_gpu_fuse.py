@@ -111,3 +111,14 @@ def test_lab_scale_sampled_positions(api):
         r = raw[j].cpu().numpy()
         ref = oracle.mnf_position(r, cfg.times, p)
         assert rel_l2(out[j].cpu().numpy().astype(np.float64), ref) <= 1e-6, j
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_sli_matches_oracle(api, name):
+    sc = synth.make_scan(name)
+    cfg = sc["cfg"]
+    raw_t = torch.from_numpy(sc["raw"]).cuda()
+    got = api.fuse_sli(raw_t, cfg.times, float(cfg.clip))
+    torch.cuda.synchronize()
+    ref = oracle.sli_stack(sc["raw"], sc["times"], float(cfg.clip))
+    assert rel_l2(got.cpu().numpy().astype(np.float64), ref) <= 1e-6

@@ -148,3 +148,21 @@ def test_coefficient_ratios_returned():
 def test_rejects_too_many_levels():
     with pytest.raises(ValueError):
         oracle.mnf_position(np.zeros((1, 16, 16)), [1.0], oracle.FuseParams(levels=4))
+
+
+def test_sli_closed_forms():
+    t = [1.0, 4.0, 16.0]
+    clip = 1000.0
+    # consistent counts (rate 10 per unit time, none saturated): every exposure says 10 * t_max
+    raw = np.array([[[10.0]], [[40.0]], [[160.0]]])
+    assert oracle.sli_position(raw, t, clip)[0, 0] == pytest.approx(160.0)
+    # the long exposure saturates: only the first two count, (10 + 40) / (1 + 4) * 16
+    raw = np.array([[[10.0]], [[40.0]], [[1000.0]]])
+    assert oracle.sli_position(raw, t, clip)[0, 0] == pytest.approx(160.0)
+    # all saturated: the shortest exposure's clipped rate, 1000 * 16 / 1
+    raw = np.full((3, 1, 1), 1000.0)
+    assert oracle.sli_position(raw, t, clip)[0, 0] == pytest.approx(16000.0)
+    # single unsaturated exposure is the identity in its own units
+    rng = np.random.default_rng(0)
+    r1 = rng.integers(0, 999, (1, 8, 8)).astype(float)
+    np.testing.assert_allclose(oracle.sli_position(r1, [2.0], clip), r1[0])
