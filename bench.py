@@ -297,8 +297,15 @@ def run_ours(args, world, rank, local):
 
     conv = None
     if rank == 0 and not args.no_nrmse and Q == 1:
+        fixed = 10 ** 9
         conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
-                              probe_update_start=pus) for pus in (0, 10 ** 9)]
+                              probe_update_start=0),
+                time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
+                              probe_update_start=fixed),
+                time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
+                              probe_update_start=fixed, fusion="sli"),
+                time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, 30, chunk=5,
+                              probe_update_start=fixed, algorithm="epie_colour")]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
@@ -349,8 +356,8 @@ def nrmse_host(obj, truth, mask):
 
 
 def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, max_iters, chunk=10,
-                  target=1e-2, probe_update_start=0):
-    """Plain FP32 reconstruction of the benchmarked scan from a flat object with the known probe:
+                  target=1e-2, probe_update_start=0, fusion="mnf", algorithm="ap"):
+    """FP32 reconstruction of the benchmarked scan from a flat object with the known probe:
     NRMSE to the ground truth every `chunk` iterations.  Device time counts the fusion, set-up
     and iterations (CUDA events), not the NRMSE evaluation."""
     import torch
@@ -358,8 +365,12 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
     mask = illuminated_mask(sc["probe"], pos, M)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    api.fuse_stack(raw, cfg.times, params, out=fused, stream=stream)
-    h = api.ptycho_init(fused, pos, obj0, probe0, probe_update_start=probe_update_start, stream=stream)
+    if fusion == "mnf":
+        api.fuse_stack(raw, cfg.times, params, out=fused, stream=stream)
+    else:
+        api.fuse_sli(raw, cfg.times, float(cfg.clip), out=fused, stream=stream)
+    h = api.ptycho_init(fused, pos, obj0, probe0, probe_update_start=probe_update_start, stream=stream,
+                        algorithm=algorithm)
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
@@ -379,11 +390,12 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
     floor = min(v for _, _, v in traj)
     goal = target if floor <= target else 1.05 * floor
     hit = next((it, ms) for it, ms, v in traj if v <= goal)
-    return {"target": target, "reached_target": floor <= target, "floor": round(floor, 5),
-            "goal_used": round(goal, 5), "iterations": hit[0], "seconds": round(hit[1] / 1e3, 4),
+    return {"engine": algorithm, "fusion": fusion, "target": target, "reached_target": floor <= target,
+            "floor": round(floor, 5), "goal_used": round(goal, 5), "iterations": hit[0],
+            "seconds": round(hit[1] / 1e3, 4),
             "start": "flat object, true probe, " + ("probe updates on" if probe_update_start == 0
                                                      else "probe fixed"),
-            "trajectory_every_10": [round(v, 5) for _, _, v in traj]}
+            f"trajectory_every_{chunk}": [round(v, 5) for _, _, v in traj]}
 
 
 # ----------------------------------------------------------------------------- oracle arm

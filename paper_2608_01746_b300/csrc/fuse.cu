@@ -90,13 +90,17 @@ constexpr int kIn = 2 * kTile + 3;    // input rows/cols a tile needs
 constexpr int kInP = kIn + 1;         // padded pitch
 
 // Level 0 -> level 1 for every exposure: blockIdx.z = position, tile of 16 x 16 outputs.
+// Each input pixel's K weights (Eq. 5, normalised) and radiances are computed once into shared
+// memory, then every plane is blurred separably (rows, then columns) and decimated.
 template <int K>
 __global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ raw,
                                                  float *__restrict__ ge1, float *__restrict__ gw1,
                                                  FuseDev f) {
-    __shared__ float s_sum[kIn * kInP];
-    __shared__ float s_e[kIn * kInP];
-    __shared__ float s_w[kIn * kInP];
+    extern __shared__ float sm[];
+    float *s_e = sm;                              // [K][kIn][kInP]
+    float *s_w = s_e + K * kIn * kInP;            // [K][kIn][kInP]
+    float *h_e = s_w + K * kIn * kInP;            // [K][kIn][kTile]  row-filtered, decimated
+    float *h_w = h_e + K * kIn * kTile;
     const int N = f.N, n1 = N >> 1;
     const size_t NN = (size_t)N * N;
     const int j = blockIdx.z;
@@ -105,50 +109,52 @@ __global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ ra
     const int outs_y = min(kTile, n1 - oy0), outs_x = min(kTile, n1 - ox0);
     const int rows = 2 * outs_y + 3, cols = 2 * outs_x + 3;
     const int tid = threadIdx.x;
-    // sum_k w_k per input pixel (the normaliser of Eq. 5)
     for (int e = tid; e < rows * cols; e += blockDim.x) {
         const int a = e / cols, b = e % cols;
         const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
-        float s = 0.f;
+        float E[K], W[K];
+        level0_pixel<K>(raw_j, NN, p, f, E, W);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float d = fminf((float)__ldg(raw_j + k * NN + p), f.clip) / f.clip - f.mu;
-            s += expf(-d * d * f.inv2s2);
+            s_e[(k * kIn + a) * kInP + b] = E[k];
+            s_w[(k * kIn + a) * kInP + b] = W[k];
         }
-        s_sum[a * kInP + b] = s;
     }
-    const int ty = tid / kTile, tx = tid % kTile;
+    __syncthreads();
+    // rows: h[k][a][ox] = sum_b w[b] x[k][a][2 ox + b]
+    for (int e = tid; e < K * rows * outs_x; e += blockDim.x) {
+        const int ox = e % outs_x, a = (e / outs_x) % rows, k = e / (outs_x * rows);
+        const float *re = s_e + (k * kIn + a) * kInP + 2 * ox;
+        const float *rw = s_w + (k * kIn + a) * kInP + 2 * ox;
+        float ae = 0.f, aw = 0.f;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            ae += wg(b) * re[b];
+            aw += wg(b) * rw[b];
+        }
+        h_e[(k * kIn + a) * kTile + ox] = ae;
+        h_w[(k * kIn + a) * kTile + ox] = aw;
+    }
+    __syncthreads();
+    // columns: out[k][oy][ox] = sum_a w[a] h[k][2 oy + a][ox]
     const size_t n1n1 = (size_t)n1 * n1;
-    for (int k = 0; k < K; ++k) {
-        __syncthreads();
-        for (int e = tid; e < rows * cols; e += blockDim.x) {
-            const int a = e / cols, b = e % cols;
-            const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
-            const float v = (float)__ldg(raw_j + k * NN + p);
-            const float d = fminf(v, f.clip) / f.clip - f.mu;
-            const float s = s_sum[a * kInP + b];
-            s_e[a * kInP + b] = v * f.tscale[k];
-            s_w[a * kInP + b] = (s > 0.f) ? expf(-d * d * f.inv2s2) / s : 1.0f / K;
-        }
-        __syncthreads();
-        if (ty < outs_y && tx < outs_x) {
-            float ae = 0.f, aw = 0.f;
+    for (int e = tid; e < K * outs_y * outs_x; e += blockDim.x) {
+        const int ox = e % outs_x, oy = (e / outs_x) % outs_y, k = e / (outs_x * outs_y);
+        float ae = 0.f, aw = 0.f;
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                float re = 0.f, rw = 0.f;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) {
-                    re += wg(b) * s_e[(2 * ty + a) * kInP + 2 * tx + b];
-                    rw += wg(b) * s_w[(2 * ty + a) * kInP + 2 * tx + b];
-                }
-                ae += wg(a) * re;
-                aw += wg(a) * rw;
-            }
-            const size_t o = ((size_t)j * K + k) * n1n1 + (size_t)(oy0 + ty) * n1 + ox0 + tx;
-            ge1[o] = ae;
-            gw1[o] = aw;
+        for (int a = 0; a < 5; ++a) {
+            ae += wg(a) * h_e[(k * kIn + 2 * oy + a) * kTile + ox];
+            aw += wg(a) * h_w[(k * kIn + 2 * oy + a) * kTile + ox];
         }
+        const size_t o = ((size_t)j * K + k) * n1n1 + (size_t)(oy0 + oy) * n1 + ox0 + ox;
+        ge1[o] = ae;
+        gw1[o] = aw;
     }
+}
+
+template <int K>
+constexpr size_t reduce0_smem() {
+    return sizeof(float) * (size_t)K * (2 * kIn * kInP + 2 * kIn * kTile);
 }
 
 // Level l -> l+1 (l >= 1) for one plane pair: blockIdx.z = j * K + k.
@@ -228,36 +234,66 @@ __global__ void k_base(const float *__restrict__ ge, const float *__restrict__ g
 }
 
 // R_l = U2(R_{l+1}) + sum_k Q_l(G_l[W_k] (G_l[E_k] - U2(G_{l+1}[E_k]))); level 0 reads raw.
+// One block per 32 x 32 output tile of one position: the 18 x 18 coarse neighbourhoods of
+// R_{l+1} and G_{l+1}[E_k] are staged in shared memory with U2's border extension (coarse
+// index -1 -> 1, n -> n - 1) applied while loading.
+constexpr int kCT = 32;                 // output tile side of the collapse
+constexpr int kCC = kCT / 2 + 2;        // coarse rows / columns the tile needs
+
+__device__ __forceinline__ int coarse_ext(int i, int n) { return i < 0 ? 1 : min(i, n - 1); }
+
 template <int K>
-__global__ void k_collapse(const float *__restrict__ ge, const float *__restrict__ gw,
-                           const uint16_t *__restrict__ raw, const float *__restrict__ ge_next,
-                           const float *__restrict__ r_next, float *__restrict__ out, int n,
-                           int J, float delta, FuseDev f) {
-    const size_t nn = (size_t)n * n;
+__global__ void __launch_bounds__(256) k_collapse(const float *__restrict__ ge, const float *__restrict__ gw,
+                                                  const uint16_t *__restrict__ raw, const float *__restrict__ ge_next,
+                                                  const float *__restrict__ r_next, float *__restrict__ out, int n,
+                                                  float delta, FuseDev f) {
+    __shared__ float s_c[K + 1][kCC][kCC + 1];          // [0..K-1] G_{l+1}[E_k], [K] R_{l+1}
     const int m = n >> 1;
-    const size_t mm = (size_t)m * m;
-    const size_t total = (size_t)J * nn;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t j = i / nn, p = i % nn;
-        const int py = (int)(p / n), px = (int)(p % n);
+    const size_t nn = (size_t)n * n, mm = (size_t)m * m;
+    const int j = blockIdx.z;
+    const int oy0 = blockIdx.y * kCT, ox0 = blockIdx.x * kCT;
+    const int cy0 = oy0 / 2 - 1, cx0 = ox0 / 2 - 1;
+    for (int e = threadIdx.x; e < (K + 1) * kCC * kCC; e += blockDim.x) {
+        const int pl = e / (kCC * kCC), a = (e / kCC) % kCC, b = e % kCC;
+        const size_t src = (size_t)coarse_ext(cy0 + a, m) * m + coarse_ext(cx0 + b, m);
+        s_c[pl][a][b] = (pl < K) ? __ldg(ge_next + ((size_t)j * K + pl) * mm + src) : __ldg(r_next + (size_t)j * mm + src);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCT * kCT; e += blockDim.x) {
+        const int py = oy0 + e / kCT, px = ox0 + e % kCT;
+        if (py >= n || px >= n) continue;
+        // U2 taps: even m = 2i -> (1/8, 6/8, 1/8) at i-1, i, i+1; odd m = 2i+1 -> (1/2, 1/2) at i, i+1
+        const int ly = (py >> 1) - cy0, lx = (px >> 1) - cx0;     // local coarse index of i
+        float wy[3], wx[3];
+        int y0, x0, ny, nx;
+        if (py & 1) { y0 = ly; ny = 2; wy[0] = wy[1] = 0.5f; }
+        else { y0 = ly - 1; ny = 3; wy[0] = 0.125f; wy[1] = 0.75f; wy[2] = 0.125f; }
+        if (px & 1) { x0 = lx; nx = 2; wx[0] = wx[1] = 0.5f; }
+        else { x0 = lx - 1; nx = 3; wx[0] = 0.125f; wx[1] = 0.75f; wx[2] = 0.125f; }
+        auto up = [&](int pl) {
+            float acc = 0.f;
+            for (int a = 0; a < ny; ++a) {
+                float r = 0.f;
+                for (int b = 0; b < nx; ++b) r += wx[b] * s_c[pl][y0 + a][x0 + b];
+                acc += wy[a] * r;
+            }
+            return acc;
+        };
+        const size_t p = (size_t)py * n + px;
         float E[K], W[K];
         if (raw) {
-            level0_pixel<K>(raw + j * K * nn, nn, p, f, E, W);
+            level0_pixel<K>(raw + (size_t)j * K * nn, nn, p, f, E, W);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                E[k] = __ldg(ge + (j * K + k) * nn + p);
-                W[k] = __ldg(gw + (j * K + k) * nn + p);
+                E[k] = __ldg(ge + ((size_t)j * K + k) * nn + p);
+                W[k] = __ldg(gw + ((size_t)j * K + k) * nn + p);
             }
         }
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float ue = upsample_at(ge_next + (j * K + k) * mm, m, py, px);
-            acc += quantise(W[k] * (E[k] - ue), delta);
-        }
-        out[i] = upsample_at(r_next + j * mm, m, py, px) + acc;
+        for (int k = 0; k < K; ++k) acc += quantise(W[k] * (E[k] - up(k)), delta);
+        out[(size_t)j * nn + p] = up(K) + acc;
     }
 }
 
@@ -270,6 +306,8 @@ template <int K>
 int run_fuse(const uint16_t *d_raw, int J, int N, const FuseDev &f, float *d_fused,
              float *scratch, cudaStream_t st) {
     const int L = f.L;
+    if (reduce0_smem<K>() > 48 * 1024)
+        PM_CUDA(cudaFuncSetAttribute(k_reduce0<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)reduce0_smem<K>()));
     if (L == 1) {
         const size_t total = (size_t)J * N * N;
         k_base<K><<<grid_for(total, 256), 256, 0, st>>>(nullptr, nullptr, d_raw, d_fused, N, J, f);
@@ -288,7 +326,7 @@ int run_fuse(const uint16_t *d_raw, int J, int N, const FuseDev &f, float *d_fus
     {
         const int n1 = N >> 1;
         dim3 grid((n1 + kTile - 1) / kTile, (n1 + kTile - 1) / kTile, J);
-        k_reduce0<K><<<grid, 256, 0, st>>>(d_raw, ge[1], gw[1], f);
+        k_reduce0<K><<<grid, 256, reduce0_smem<K>(), st>>>(d_raw, ge[1], gw[1], f);
         PM_LAUNCHED("k_reduce0");
     }
     for (int l = 1; l + 1 < L; ++l) {
@@ -305,13 +343,11 @@ int run_fuse(const uint16_t *d_raw, int J, int N, const FuseDev &f, float *d_fus
     }
     for (int l = L - 2; l >= 0; --l) {
         const int n = N >> l;
-        const size_t total = (size_t)J * n * n;
+        dim3 grid((n + kCT - 1) / kCT, (n + kCT - 1) / kCT, J);
         if (l == 0) {
-            k_collapse<K><<<grid_for(total, 256), 256, 0, st>>>(nullptr, nullptr, d_raw, ge[1], rr[1],
-                                                                d_fused, n, J, f.delta[0], f);
+            k_collapse<K><<<grid, 256, 0, st>>>(nullptr, nullptr, d_raw, ge[1], rr[1], d_fused, n, f.delta[0], f);
         } else {
-            k_collapse<K><<<grid_for(total, 256), 256, 0, st>>>(ge[l], gw[l], nullptr, ge[l + 1], rr[l + 1],
-                                                                rr[l], n, J, f.delta[l], f);
+            k_collapse<K><<<grid, 256, 0, st>>>(ge[l], gw[l], nullptr, ge[l + 1], rr[l + 1], rr[l], n, f.delta[l], f);
         }
         PM_LAUNCHED("k_collapse");
     }

@@ -41,7 +41,8 @@ enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
 //   XM_FULL  unit = position j: psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] (one probe mode)
 //   XM_FWD   unit = (j, m): Psi_jm = F(P_m O_j), unitary, into psi[j][m] (row-major, DC at 0)
 //   XM_INV   unit = (j, m): psi[j][m] <- F^-1 psi[j][m] (after the mode-summed modulus step)
-enum { XM_FULL = 0, XM_FWD = 1, XM_INV = 2 };
+//   XM_LIST  as XM_FULL for the positions list[0 .. count) only (ePIE colours)
+enum { XM_FULL = 0, XM_FWD = 1, XM_INV = 2, XM_LIST = 3 };
 
 struct ExitArgs {
     const float2 *obj;
@@ -90,12 +91,13 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     float2 *xb = xb_all + g * R * (R + 1);
     const float invN = 1.0f / (float)N;
     const int M = a.M;
-    const int units = (XM == XM_FULL) ? (a.list ? a.count : a.J) : a.J * a.Q;
+    constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
+    const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
 
     for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
-        const int u = (XM == XM_FULL && a.list) ? a.list[iu] : iu;
-        const int j = (XM == XM_FULL) ? u : u / a.Q;
-        const int mode = (XM == XM_FULL) ? 0 : u % a.Q;
+        const int u = (XM == XM_LIST) ? a.list[iu] : iu;
+        const int j = kFull ? u : u / a.Q;
+        const int mode = kFull ? 0 : u % a.Q;
         float2 *psi_u = a.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
         if constexpr (XM != XM_INV) {
             // (1) psi = P_m * O_j, forward row FFTs in place
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
 #pragma unroll
                     for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
                 }
-                if constexpr (XM == XM_FULL) {
+                if constexpr (kFull) {
 #pragma unroll
                     for (int m = 0; m < R; ++m) {
                         const float2 X = d[m];
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
                 }
             }
         }
-        if constexpr (XM == XM_FULL) {
+        if constexpr (kFull) {
             // Fourier error of position j (FP64 block sum)
             double e = (double)err;
 #pragma unroll
@@ -327,11 +329,12 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         }
     };
 
-    const int units = (XM == XM_FULL) ? (a.list ? a.count : a.J) : a.J * a.Q;
+    constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
+    const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
     for (int iu = blockIdx.x; iu < units && !failed; iu += gridDim.x) {
-        const int u = (XM == XM_FULL && a.list) ? a.list[iu] : iu;
-        const int j = (XM == XM_FULL) ? u : u / a.Q;
-        const int prow0 = (XM == XM_FULL) ? 0 : (u % a.Q) * N;    // first probe row of the mode
+        const int u = (XM == XM_LIST) ? a.list[iu] : iu;
+        const int j = kFull ? u : u / a.Q;
+        const int prow0 = kFull ? 0 : (u % a.Q) * N;              // first probe row of the mode
         float err = 0.f;
         if constexpr (XM != XM_INV) {
         const int2 pj = a.pos[j];
@@ -374,7 +377,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
             const int s = b & 1;
             const int c = kTmaBatch * b + g;
             float A[R];                                   // A[k2] = |F psi| target at ky = t + 16 k2
-            if constexpr (XM == XM_FULL) {
+            if constexpr (kFull) {
                 const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c) * N + t * R);
 #pragma unroll
                 for (int v = 0; v < R / 4; ++v) {
@@ -388,7 +391,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
             pm::fft_group_xs<R, -1>(d, col, tw, t);
-            if constexpr (XM == XM_FULL) {
+            if constexpr (kFull) {
 #pragma unroll
                 for (int m = 0; m < R; ++m) {
                     const float2 X = cscale(d[m], invN);
@@ -470,7 +473,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         }
         }
         if (failed) break;
-        if constexpr (XM == XM_FULL) {
+        if constexpr (kFull) {
             double e = (double)err;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -526,6 +529,7 @@ __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const fl
 // Owner-computes object numerator and denominator, one kTR x 32 object tile per block.
 // Warp w takes every 8th position of the tile's (ascending) list; lane = tile column, and
 // each lane keeps its column's kTR pixels in registers.
+template <int QC>   // QC = 1: one probe mode (compile-time); 0: Q modes at run time
 __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
     const int *__restrict__ tstart, const int4 *__restrict__ tlist, const int *__restrict__ torder,
@@ -550,8 +554,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
         const int lx = tx0 + lane - pj.y;
         const bool okx = lx >= 0 && lx < N;
         const int lxc = min(max(lx, 0), N - 1);
-        for (int m = 0; m < Q; ++m) {                    // probe modes (one for coherent data)
-            const float2 *psi_j = psi + ((size_t)j * Q + m) * NN;
+        const int nq = QC ? QC : Q;
+        for (int m = 0; m < nq; ++m) {                   // probe modes (one for coherent data)
+            const float2 *psi_j = psi + ((size_t)j * nq + m) * NN;
             const float2 *probe_m = probe + (size_t)m * NN;
             // All loads first, from clamped (always valid) addresses, so they are in flight
             // together; pixels outside the patch are masked out afterwards.
@@ -678,6 +683,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
 
 // Probe partial sums: block (kTR x 32 probe tile, chunk of positions) -> partial[chunk][q].
 // Warp w takes every 8th position of the chunk; lane = tile column, kTR rows in registers.
+template <int QC>   // QC = 1: one probe mode (compile-time); 0: Q modes at run time
 __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
     float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk, int Q) {
@@ -697,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
     for (int j = j0 + warp; j < j1; j += kThreads / 32) {
         const int2 pj = pn;
         if (j + kThreads / 32 < j1) pn = pos[j + kThreads / 32];
-        const float2 *psi_j = psi + ((size_t)j * Q + blockIdx.z) * NN;
+        const float2 *psi_j = psi + (QC ? (size_t)j * NN : ((size_t)j * Q + blockIdx.z) * NN);
         const int qxc = min(qx, N - 1);
         float2 ov[kTR], vv[kTR];
 #pragma unroll
@@ -724,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
         const int r = threadIdx.x / kTW, c = threadIdx.x % kTW;
         const int y = qy0 + r, x = qx0 + c;
         if (y < N && x < N) {
-            const size_t o = ((size_t)chunk * Q + blockIdx.z) * NN + (size_t)y * N + x;
+            const size_t o = (QC ? (size_t)chunk * NN : ((size_t)chunk * Q + blockIdx.z) * NN) + (size_t)y * N + x;
             pnum[o] = tnum;
             pden[o] = tden;
         }
@@ -945,6 +951,9 @@ int setup_exit_tma(ptycho_ctx *h) {
         if ((rc = setup_tma_kernel<16, XM_FWD>(h, &per_sm))) return rc;
         if ((rc = setup_tma_kernel<16, XM_INV>(h, &p2))) return rc;
         per_sm = std::min(per_sm, p2);
+    } else if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
+        h->tma_batch = 16;
+        if ((rc = setup_tma_kernel<16, XM_LIST>(h, &per_sm))) return rc;
     } else if (h->tma_batch == 32) {
         if ((rc = setup_tma_kernel<32, XM_FULL>(h, &per_sm))) return rc;
     } else {
@@ -991,6 +1000,7 @@ int launch_exit_tma(ptycho_ctx *h, int xm) {
     const TmaArgs a = tma_args(h);
     if (xm == XM_FWD) k_exit_wave_tma<16, XM_FWD><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (xm == XM_INV) k_exit_wave_tma<16, XM_INV><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else if (xm == XM_LIST) k_exit_wave_tma<16, XM_LIST><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (h->tma_batch == 32) k_exit_wave_tma<32, XM_FULL><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else k_exit_wave_tma<16, XM_FULL><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     PM_LAUNCHED("k_exit_wave_tma");
@@ -1016,6 +1026,8 @@ int setup_exit_kernel(ptycho_ctx *h) {
         if ((rc = setup_small_kernel<R, XM_FWD>(h, &per_sm))) return rc;
         if ((rc = setup_small_kernel<R, XM_INV>(h, &p2))) return rc;
         per_sm = std::min(per_sm, p2);
+    } else if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
+        if ((rc = setup_small_kernel<R, XM_LIST>(h, &per_sm))) return rc;
     } else if ((rc = setup_small_kernel<R, XM_FULL>(h, &per_sm))) {
         return rc;
     }
@@ -1040,6 +1052,7 @@ int launch_exit(ptycho_ctx *h, int xm) {
     a.Q = h->Q;
     if (xm == XM_FWD) k_exit_wave<R, XM_FWD><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
     else if (xm == XM_INV) k_exit_wave<R, XM_INV><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    else if (xm == XM_LIST) k_exit_wave<R, XM_LIST><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
     else k_exit_wave<R, XM_FULL><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
     PM_LAUNCHED("k_exit_wave");
     return PTYCHO_OK;
@@ -1104,7 +1117,7 @@ int iterate_one_epie(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool u
         const int b = h->colour_start[c], n = h->colour_start[c + 1] - b;
         h->cur_list = h->d_colour_list + b;
         h->cur_count = n;
-        rc = launch_exit_pass(h, XM_FULL);
+        rc = launch_exit_pass(h, XM_LIST);
         h->cur_list = nullptr;
         h->cur_count = 0;
         if (rc) return rc;
@@ -1140,9 +1153,14 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     if ((rc = stage_end(h, ST_EXIT, ev_base + 0, exit_launches))) return rc;
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
-    k_object_gather<<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
-                                                       h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max, h->M,
-                                                       h->N, h->ntx, h->Q);
+    if (h->Q == 1)
+        k_object_gather<1><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
+                                                              h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max,
+                                                              h->M, h->N, h->ntx, 1);
+    else
+        k_object_gather<0><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
+                                                              h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max,
+                                                              h->M, h->N, h->ntx, h->Q);
     PM_LAUNCHED("k_object_gather");
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
@@ -1154,8 +1172,12 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     if ((rc = stage_begin(h, ST_PROBE, ev_base + 2))) return rc;
     if (update_probe) {
         const int NN = h->N * h->N * h->Q;                // all probe modes
-        k_probe_partial<<<dim3(h->nqt, h->nchunk, h->Q), kThreads, 0, h->st>>>(
-            h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, h->Q);
+        if (h->Q == 1)
+            k_probe_partial<1><<<dim3(h->nqt, h->nchunk, 1), kThreads, 0, h->st>>>(
+                h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, 1);
+        else
+            k_probe_partial<0><<<dim3(h->nqt, h->nchunk, h->Q), kThreads, 0, h->st>>>(
+                h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, h->Q);
         PM_LAUNCHED("k_probe_partial");
         k_probe_reduce<<<h->nred, kThreads, 0, h->st>>>(h->d_pnum, h->d_pden, h->d_num_p, h->d_den_p, h->d_pmax, NN,
                                                         h->nchunk);
