@@ -102,6 +102,23 @@ int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, const float *
 int fuse_sli(const uint16_t *d_raw, int J, int K, int N, const float *h_t, float clip, float *d_fused,
              void *cuda_stream);
 
+/*
+ * dft2_split_bf16 -- batch of unitary 2-D DFTs (the F of Eq. 3; inverse = F^-1) computed on the
+ * tensor cores as split-BF16 (3-term) DFT-by-GEMM with FP32 accumulation: every operand x is
+ * split into hi = bf16(x) and lo = bf16(x - hi), and each real GEMM takes
+ * G_hi B_hi + G_hi B_lo + G_lo B_hi (the lo x lo term is dropped).  The paper prescribes no
+ * FFT algorithm; this is the precision form offered beside the FP32 radix path.
+ *   d_in, d_out  device, complex64 [B][N][N] row-major, DC at index 0; may be the same buffer
+ *   B            transforms, >= 0 (0 is a no-op)
+ *   N            64 (other sizes: PTYCHO_EINVAL)
+ *   inverse      0 forward (exp(-2 pi i k n / N), 1/N), 1 inverse (exp(+...), 1/N)
+ *   d_status     device int, caller-owned; set to 1 if a bounded device wait gave up (never
+ *                cleared by the library)
+ * The first call on a device builds the split DFT matrix (a 64 KB array compiled into the
+ * library) and synchronises the device; make it before any stream capture.  Asynchronous.
+ */
+int dft2_split_bf16(const void *d_in, void *d_out, int B, int N, int inverse, int *d_status, void *cuda_stream);
+
 typedef struct ptycho_ctx *ptycho_handle;
 
 /* Reconstruction engines (the paper cites PIE / ePIE / difference map without choosing one):
@@ -114,6 +131,12 @@ typedef struct ptycho_ctx *ptycho_handle;
  *                atomics (disjoint patches), and P += (beta / n_colour) sum conj(O_j) Delta /
  *                max|O_j|^2.  One probe mode only. */
 enum { PTYCHO_ALG_AP = 0, PTYCHO_ALG_EPIE_COLOUR = 1 };
+
+/* FFT form of the exit-wave step (the paper prescribes none):
+ *   RADIX_FP32        FP32 radix FFTs on the CUDA cores (default; N = 16, 64, 256)
+ *   DFTGEMM_BF16X3    split-BF16 3-term DFT-by-GEMM on the tensor cores, FP32 accumulation
+ *                     (see dft2_split_bf16); N = 64, one probe mode, algorithm AP. */
+enum { PTYCHO_FFT_RADIX_FP32 = 0, PTYCHO_FFT_DFTGEMM_BF16X3 = 1 };
 
 typedef struct {
     int M;                  /* object side (M x M complex64), M >= N                          */
@@ -133,6 +156,7 @@ typedef struct {
     int algorithm;          /* PTYCHO_ALG_AP (default) or PTYCHO_ALG_EPIE_COLOUR              */
     float epie_alpha;       /* ePIE object step (> 0; 1 is standard), EPIE_COLOUR only        */
     float epie_beta;        /* ePIE probe step (>= 0; 1 is standard), EPIE_COLOUR only        */
+    int fft_path;           /* PTYCHO_FFT_RADIX_FP32 (default) or PTYCHO_FFT_DFTGEMM_BF16X3    */
     void *cuda_stream;      /* stream for all work of this handle                             */
 } ptycho_desc;
 

@@ -42,7 +42,8 @@ class PtychoDescC(ctypes.Structure):
                 ("init_on_device", ctypes.c_int), ("alpha_O", ctypes.c_float),
                 ("alpha_P", ctypes.c_float), ("probe_update_start", ctypes.c_int),
                 ("algorithm", ctypes.c_int), ("epie_alpha", ctypes.c_float),
-                ("epie_beta", ctypes.c_float), ("cuda_stream", ctypes.c_void_p)]
+                ("epie_beta", ctypes.c_float), ("fft_path", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class PtychoError(RuntimeError):
@@ -74,6 +75,8 @@ def lib() -> ctypes.CDLL:
     L.fuse_stack_noalloc.argtypes = L.fuse_stack.argtypes
     L.fuse_stack_noalloc.restype = ci
     L.fuse_sli.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp]
+    L.dft2_split_bf16.restype = ci
+    L.dft2_split_bf16.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.fuse_sli.restype = ci
     L.ptycho_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PtychoDescC)]
     L.ptycho_init.restype = ci
@@ -167,6 +170,27 @@ def fuse_sli(raw, times, clip: float, out=None, stream=None):
     return out
 
 
+def dft2_split_bf16(x, inverse: bool = False, out=None, status=None, stream=None):
+    """Unitary 2-D DFT (or inverse) of x[B][N][N] (complex64 CUDA) on the tensor cores, split-BF16
+    3-term GEMM form.  ``status`` (int32 CUDA tensor [1]) receives 1 if a device wait gave up;
+    a fresh zeroed one is used when omitted.  Returns (out, status)."""
+    import torch
+    if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous() or x.dim() != 3:
+        raise ValueError("x must be a contiguous complex64 CUDA tensor [B][N][N]")
+    B, N, _ = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    _check(lib().dft2_split_bf16(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), B, N,
+                                 1 if inverse else 0, ctypes.c_void_p(status.data_ptr()),
+                                 ctypes.c_void_p(_stream_ptr(stream))))
+    return out, status
+
+
+FFT_PATHS = {"radix_fp32": 0, "dftgemm_bf16x3": 1}
+
+
 class PtychoHandle:
     """Owner of a ``ptycho_handle``; ``close()`` (or garbage collection) destroys it."""
 
@@ -188,7 +212,8 @@ class PtychoHandle:
 
 def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float = 1e-3,
                 probe_update_start: int = 0, stream=None, algorithm: str = "ap",
-                epie_alpha: float = 1.0, epie_beta: float = 1.0) -> PtychoHandle:
+                epie_alpha: float = 1.0, epie_beta: float = 1.0,
+                fft_path: str = "radix_fp32") -> PtychoHandle:
     """fused: float32 CUDA tensor [J][N][N]; pos: int [J][2] (y, x); obj0 / probe0: complex64,
     both numpy (host) or both torch CUDA tensors (device); probe0 is [N][N] (one mode) or
     [Q][N][N] (Q incoherent modes)."""
@@ -214,7 +239,7 @@ def ptycho_init(fused, pos, obj0, probe0, alpha_O: float = 1e-3, alpha_P: float 
     Q = probe0.shape[0] if len(probe0.shape) == 3 else 1
     desc = PtychoDescC(M, N, J, Q, pos.ctypes.data, fused.data_ptr(), op, pp, 1 if on_dev else 0,
                        alpha_O, alpha_P, probe_update_start, ALGORITHMS[algorithm], epie_alpha,
-                       epie_beta, _stream_ptr(stream))
+                       epie_beta, FFT_PATHS[fft_path], _stream_ptr(stream))
     h = ctypes.c_void_p()
     _check(lib().ptycho_init(ctypes.byref(h), ctypes.byref(desc)))
     return PtychoHandle(h.value, M, N, J, Q)

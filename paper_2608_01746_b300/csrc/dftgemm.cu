@@ -1,0 +1,402 @@
+// Split-BF16 (3-term) DFT-as-GEMM on the fifth-generation tensor cores, N = 64.
+//
+// The unitary 2-D DFT of Eq. 3 (and its inverse) is computed as four real GEMMs per batch of
+// patches, each of the form D = G B^T with
+//   G  [128 x 128]  the 64-point DFT matrix F[u][r] = exp(-2 pi i u r / 64) as a real matrix
+//                   over interleaved (re, im) indices: G[2u + s'][2r + s]
+//   B  [256 x 128]  one row per transformed vector (4 patches x 64 vectors), interleaved re/im
+//   D  [128 x 256]  FP32 in tensor memory: lane 2u + s' of column n = part s' of (F b_n)[u].
+// Every operand is split x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and the product is
+// taken as G_hi B_hi + G_hi B_lo + G_lo B_hi (the lo x lo term, ~2^-18 relative, is dropped);
+// accumulation is FP32 in TMEM.
+//
+// The pass structure keeps a whole 4-patch group on chip.  Lane 2h + s of a pass's result
+// holds part s of entry h of every transformed vector, i.e. one full vector of the NEXT
+// pass's operand (which transforms along the other axis), so each epilogue reads its TMEM lane
+// and writes one contiguous operand row:
+//   pass 1  b_(p,c) = x_p[., c]            -> W_p = F x_p              (columns)
+//   pass 2  b_(p,u) = W_p[u, .]            -> Psi_p = F x_p F          (rows; Psi^T per lane)
+//   exit-wave form only:
+//   modulus Psi' = A Psi / |Psi| (Psi' = A where Psi = 0), error (|Psi| - A)^2 per position
+//   pass 3  b_(p,v) = conj(Psi')[., v]     -> V_p = F conj(Psi')
+//   pass 4  b_(p,w) = V_p[w, .]            -> F conj(Psi') F = N conj(psi')
+// so the inverse transform is the forward one applied by conjugation, and the 1/N unitary
+// scale is applied in the epilogues (a power of two, exact).
+#include <cuda_bf16.h>
+#include <mutex>
+
+#include "common.cuh"
+#include "dftgemm.h"
+#include "tcgen05.cuh"
+#include "tma.cuh"
+
+namespace {
+
+using namespace pm;
+
+constexpr int kN = 64;                     // transform length
+constexpr int kK = 2 * kN;                 // real K: interleaved (re, im)
+constexpr int kRows = 2 * kN;              // rows of G = MMA M
+constexpr int kP = 4;                      // patches per group
+constexpr int kCols = kP * kN;             // MMA N
+constexpr int kThreads = 256;
+constexpr uint32_t kLBO = 128;             // next core matrix along K
+constexpr uint32_t kSBO = (kK / 8) * 128;  // next 8-row group
+constexpr uint32_t kGBytes = kRows * kK * 2;
+constexpr uint32_t kBBytes = kCols * kK * 2;
+constexpr uint32_t kSmemBytes = 2 * kGBytes + 2 * kBBytes + 1024;   // + alignment slack
+constexpr uint32_t kTmemCols = 256;
+
+static_assert(kCols <= 256 && kCols % 16 == 0, "MMA N");
+static_assert(kTmemCols >= kCols, "accumulator columns");
+
+// G_hi then G_lo in the core-matrix layout; filled once per device by k_fill_dft64.
+__device__ uint4 g_dft64[2 * kGBytes / 16];
+
+enum { MODE_EXIT = 0, MODE_DFT = 1 };
+
+struct Args {
+    const float2 *obj;      // exit: object [M][M]
+    const float2 *probe;    // exit: probe [N][N]
+    const float *amp;       // exit: amplitudes [J][kx][ky] (DC at 0)
+    const int2 *pos;        // exit: (row, column) of each patch
+    float2 *psi;            // exit: psi' [J][N][N]
+    double *err;            // exit: Fourier error per position
+    const float2 *in;       // dft: [J][N][N]
+    float2 *out;            // dft: [J][N][N]
+    int inverse;            // dft: 1 = unitary inverse
+    int *status;            // set to 1 when a bounded wait gives up
+    int M, J;               // object side; number of patches / transforms
+};
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+
+// (re, im) -> packed hi word and lo word (re in the low half: the lower K index).
+__device__ __forceinline__ void split2(float2 z, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
+    const float2 r = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(z.x - r.x, z.y - r.y);
+    hi = bf2_bits(h);
+    lo = bf2_bits(l);
+}
+
+__global__ void k_fill_dft64() {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kRows * kK) return;
+    const int m = i / kK, k = i % kK;
+    const int u = m >> 1, sp = m & 1, r = k >> 1, s = k & 1;
+    double sn, cs;
+    sincospi(2.0 * (double)((u * r) % kN) / (double)kN, &sn, &cs);
+    // Re y = cos Re x + sin Im x,  Im y = -sin Re x + cos Im x   (y = e^{-i theta} x)
+    const double g = (sp == s) ? cs : (sp == 0 ? sn : -sn);
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)g);
+    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(g - (double)__bfloat162float(hi)));
+    uint16_t *gw = reinterpret_cast<uint16_t *>(g_dft64);
+    const uint32_t off = tc::core_offset(m, k, kK) / 2;
+    gw[off] = __bfloat16_as_ushort(hi);
+    gw[kGBytes / 2 + off] = __bfloat16_as_ushort(lo);
+}
+
+// Operand of pass 1: B[p N + c][2 r + s] = x_p[r][c], 4 rows (16 bytes) per store.
+template <int MODE>
+__device__ __forceinline__ void fill_input(const Args &a, int j0, int np, uint8_t *bh, uint8_t *bl) {
+    const int tid = threadIdx.x;
+    const int p = tid >> 6, c = tid & (kN - 1);
+    const int n = p * kN + c;
+    const bool live = p < np;
+    const float2 *x0 = nullptr, *x1 = nullptr;
+    if (live) {
+        if constexpr (MODE == MODE_EXIT) {
+            const int2 pj = a.pos[j0 + p];
+            x0 = a.obj + (size_t)pj.x * a.M + pj.y + c;
+            x1 = a.probe + c;
+        } else {
+            x0 = a.in + (size_t)(j0 + p) * kN * kN + c;
+        }
+    }
+#pragma unroll 2
+    for (int rq = 0; rq < kN / 4; ++rq) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = 4 * rq + q;
+            float2 z = make_float2(0.f, 0.f);
+            if (live) {
+                if constexpr (MODE == MODE_EXIT) {
+                    z = cmul(__ldg(x1 + (size_t)r * kN), __ldg(x0 + (size_t)r * a.M));
+                } else {
+                    z = __ldg(x0 + (size_t)r * kN);
+                    if (a.inverse) z.y = -z.y;
+                }
+            }
+            split2(z, h[q], l[q]);
+        }
+        const uint32_t off = tc::core_offset(n, 8 * rq, kK);
+        *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Two consecutive entries (c, c + 1), c even, of operand row n.
+__device__ __forceinline__ void put_pair(uint8_t *bh, uint8_t *bl, int n, int c, float2 z0, float2 z1) {
+    uint32_t h0, l0, h1, l1;
+    split2(z0, h0, l0);
+    split2(z1, h1, l1);
+    const uint32_t off = tc::core_offset(n, 2 * c, kK);
+    *reinterpret_cast<uint2 *>(bh + off) = make_uint2(h0, h1);
+    *reinterpret_cast<uint2 *>(bl + off) = make_uint2(l0, l1);
+}
+
+// Reads the 64 accumulator columns of patch p in this thread's lane and hands the thread the
+// complex entries c, c + 1 (c = 4 i + 2 part) of its lane pair's vector: lanes 2h and 2h + 1
+// hold the real and imaginary rows of the same index h, and swap halves with one shuffle per
+// two entries.
+template <typename F>
+__device__ __forceinline__ void for_pairs(uint32_t lane_addr, int p, int part, F &&f) {
+#pragma unroll 1
+    for (int ch = 0; ch < 2; ++ch) {
+        uint32_t v[32];
+        tc::ld_32cols(lane_addr + (uint32_t)(p * kN + ch * 32), v);
+        tc::wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+            const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+            const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+            const float y0 = __shfl_xor_sync(0xffffffffu, part ? a0 : a2, 1);
+            const float y1 = __shfl_xor_sync(0xffffffffu, part ? a1 : a3, 1);
+            const float2 z0 = part ? make_float2(y0, a2) : make_float2(a0, y0);
+            const float2 z1 = part ? make_float2(y1, a3) : make_float2(a1, y1);
+            f(ch * 32 + i + 2 * part, z0, z1);
+        }
+    }
+}
+
+// One GEMM pass D = G_hi B_hi + G_hi B_lo + G_lo B_hi.  Every thread calls it; returns false
+// (for all threads) when the completion wait gave up.
+__device__ __forceinline__ bool mma_pass(uint32_t tmem, uint32_t gh, uint32_t bh, uint64_t *bar,
+                                         uint32_t &phase) {
+    tma::fence_async_smem();          // operand writes -> visible to the tensor core
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after();
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kCols);
+        const uint32_t gl = gh + kGBytes, bl = bh + kBBytes;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const uint32_t ab = (t == 2) ? gl : gh;
+            const uint32_t bb = (t == 1) ? bl : bh;
+#pragma unroll
+            for (int ks = 0; ks < kK / 16; ++ks)
+                tc::mma_bf16(tmem, tc::smem_desc(ab + ks * 256, kLBO, kSBO), tc::smem_desc(bb + ks * 256, kLBO, kSBO),
+                             idesc, (uint32_t)((t | ks) != 0));
+        }
+        tc::commit(bar);
+    }
+    const bool ok = tma::mbar_wait(bar, phase);
+    tc::fence_after();
+    const bool all = __syncthreads_and(ok) != 0;
+    if (all) phase ^= 1;
+    return all;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sG = sm;
+    uint8_t *sBh = sm + 2 * kGBytes;
+    uint8_t *sBl = sBh + kBBytes;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double s_err[kThreads / 32][2];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < (int)(2 * kGBytes / 16); i += kThreads) reinterpret_cast<uint4 *>(sG)[i] = g_dft64[i];
+    if (warp == 0) tc::alloc(&tmem_slot, kTmemCols);
+    if (tid == 0) {
+        tma::mbar_init(&bar, 1);
+        tma::fence_barrier_init();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t gh = tc::smem_addr(sG), bh = tc::smem_addr(sBh);
+    uint32_t phase = 0;
+
+    const int row = 32 * (warp & 3) + lane;        // accumulator lane 2 h + part
+    const int half = row >> 1, part = row & 1;
+    const int pbase = (warp >> 2) * 2;             // this warp's patches: pbase, pbase + 1
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const float invN = 1.0f / (float)kN;
+    const int ngroups = (a.J + kP - 1) / kP;
+    bool failed = false;
+
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int j0 = grp * kP;
+        const int np = min(kP, a.J - j0);
+        fill_input<MODE>(a, j0, np, sBh, sBl);
+        if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        // pass-2 operand: rows of W_p
+#pragma unroll 1
+        for (int pp = 0; pp < 2; ++pp) {
+            const int p = pbase + pp;
+            if (p >= np) continue;
+            for_pairs(lane_addr, p, part,
+                      [&](int c, float2 z0, float2 z1) { put_pair(sBh, sBl, p * kN + half, c, z0, z1); });
+        }
+        if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        if constexpr (MODE == MODE_DFT) {
+            // lane (v, part) holds part of Psi_p[u][v] for every u
+#pragma unroll 1
+            for (int pp = 0; pp < 2; ++pp) {
+                const int p = pbase + pp;
+                if (p >= np) continue;
+                float2 *o = a.out + (size_t)(j0 + p) * kN * kN + half;
+                const float sy = a.inverse ? -invN : invN;
+                for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
+                    o[(size_t)c * kN] = make_float2(z0.x * invN, z0.y * sy);
+                    o[(size_t)(c + 1) * kN] = make_float2(z1.x * invN, z1.y * sy);
+                });
+            }
+        } else {
+            // modulus constraint against A_j[v][u], then conj(Psi') as the pass-3 operand
+            float e[2] = {0.f, 0.f};
+#pragma unroll 1
+            for (int pp = 0; pp < 2; ++pp) {
+                const int p = pbase + pp;
+                if (p >= np) continue;
+                const float *amp = a.amp + (size_t)(j0 + p) * kN * kN + (size_t)half * kN;
+                float ep = 0.f;
+                for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
+                    const float2 A2 = __ldg(reinterpret_cast<const float2 *>(amp + c));
+                    float2 z[2] = {cscale(z0, invN), cscale(z1, invN)};
+                    const float A[2] = {A2.x, A2.y};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const float mag = sqrtf(cabs2(z[q]));
+                        const float dm = mag - A[q];
+                        ep += dm * dm;
+                        z[q] = mag > 0.f ? cscale(z[q], A[q] / mag) : make_float2(A[q], 0.f);
+                        z[q].y = -z[q].y;
+                    }
+                    put_pair(sBh, sBl, p * kN + half, c, z[0], z[1]);
+                });
+                e[pp] = ep;
+            }
+            if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+#pragma unroll 1
+            for (int pp = 0; pp < 2; ++pp) {
+                const int p = pbase + pp;
+                if (p >= np) continue;
+                for_pairs(lane_addr, p, part,
+                          [&](int c, float2 z0, float2 z1) { put_pair(sBh, sBl, p * kN + half, c, z0, z1); });
+            }
+            if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+            // lane (x, part) holds part of N conj(psi'_p)[w][x] for every w
+#pragma unroll 1
+            for (int pp = 0; pp < 2; ++pp) {
+                const int p = pbase + pp;
+                if (p >= np) continue;
+                float2 *o = a.psi + (size_t)(j0 + p) * kN * kN + half;
+                for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
+                    o[(size_t)c * kN] = make_float2(z0.x * invN, -z0.y * invN);
+                    o[(size_t)(c + 1) * kN] = make_float2(z1.x * invN, -z1.y * invN);
+                });
+            }
+            // Fourier error per position: fixed-order sums over lanes, then over the 4 warps
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                double d = (double)e[pp];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (lane == 0) s_err[warp][pp] = d;
+            }
+            __syncthreads();
+            if (tid < np) {
+                const int w0 = (tid >> 1) * 4, pp = tid & 1;
+                a.err[j0 + tid] = ((s_err[w0][pp] + s_err[w0 + 1][pp]) + s_err[w0 + 2][pp]) + s_err[w0 + 3][pp];
+            }
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(a.status, 1);
+        tma::mbar_wait(&bar, phase);          // let MMAs still in flight finish (bounded)
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tmem, kTmemCols);
+    }
+}
+
+std::mutex g_mu;
+bool g_ready[64] = {};
+
+int launch(const Args &a, int mode, int sm_count, cudaStream_t st) {
+    if (a.J <= 0) return PTYCHO_OK;
+    const int ngroups = (a.J + kP - 1) / kP;
+    const int grid = ngroups < sm_count ? ngroups : sm_count;
+    if (mode == MODE_EXIT)
+        k_dft64_gemm<MODE_EXIT><<<grid, kThreads, kSmemBytes, st>>>(a);
+    else
+        k_dft64_gemm<MODE_DFT><<<grid, kThreads, kSmemBytes, st>>>(a);
+    PM_LAUNCHED("k_dft64_gemm");
+    return PTYCHO_OK;
+}
+
+}  // namespace
+
+namespace pm {
+
+int dft64_prepare(int *sm_count) {
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(sm_count, cudaDevAttrMultiProcessorCount, dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev >= 0 && dev < 64 && g_ready[dev]) return PTYCHO_OK;
+    PM_CUDA(cudaFuncSetAttribute(k_dft64_gemm<MODE_EXIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    PM_CUDA(cudaFuncSetAttribute(k_dft64_gemm<MODE_DFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    k_fill_dft64<<<(kRows * kK + 255) / 256, 256>>>();
+    PM_LAUNCHED("k_fill_dft64");
+    PM_CUDA(cudaDeviceSynchronize());
+    if (dev >= 0 && dev < 64) g_ready[dev] = true;
+    return PTYCHO_OK;
+}
+
+int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st) {
+    Args a{};
+    a.obj = e.obj;
+    a.probe = e.probe;
+    a.amp = e.amp;
+    a.pos = e.pos;
+    a.psi = e.psi;
+    a.err = e.err;
+    a.status = e.status;
+    a.M = e.M;
+    a.J = e.J;
+    return launch(a, MODE_EXIT, sm_count, st);
+}
+
+}  // namespace pm
+
+extern "C" int dft2_split_bf16(const void *d_in, void *d_out, int B, int N, int inverse, int *d_status,
+                               void *cuda_stream) {
+    if (N != 64) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: N = %d unsupported (64 only)", N);
+    if (B < 0) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: B = %d < 0", B);
+    if (inverse != 0 && inverse != 1) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: inverse must be 0 or 1");
+    if (B == 0) return PTYCHO_OK;
+    if (!d_in || !d_out || !d_status) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: NULL pointer");
+    int sms = 0;
+    int rc = pm::dft64_prepare(&sms);
+    if (rc) return rc;
+    Args a{};
+    a.in = static_cast<const float2 *>(d_in);
+    a.out = static_cast<float2 *>(d_out);
+    a.inverse = inverse;
+    a.status = d_status;
+    a.J = B;
+    return launch(a, MODE_DFT, sms, static_cast<cudaStream_t>(cuda_stream));
+}

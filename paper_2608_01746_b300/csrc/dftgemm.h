@@ -1,0 +1,27 @@
+// Internal interface between the reconstruction engine and the split-BF16 tensor-core DFT
+// (N = 64), see dftgemm.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pm {
+
+struct Dft64Exit {
+    const float2 *obj;      // object [M][M]
+    const float2 *probe;    // probe [64][64]
+    const float *amp;       // amplitudes [J][kx][ky], DC at index 0
+    const int2 *pos;        // (row, column) of each patch's top-left corner
+    float2 *psi;            // out: psi' [J][64][64] row-major
+    double *err;            // out: Fourier error per position
+    int *status;            // set to 1 if a bounded wait gave up
+    int M, J;
+};
+
+// Once per device (synchronises the device the first time): builds the split DFT matrix and
+// sets the kernels' shared-memory limit.  Returns the device's SM count.
+int dft64_prepare(int *sm_count);
+
+// psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] for every j, tensor-core DFTs; one launch.
+int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
+
+}  // namespace pm

@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "dftgemm.h"
 #include "fft.cuh"
 #include "tma.cuh"
 
@@ -855,6 +856,8 @@ struct ptycho_ctx {
     int *d_status = nullptr;
     TmaMaps tm;
     bool exit_tma = false;
+    bool fft_gemm = false;                                // split-BF16 tensor-core DFTs (N = 64)
+    int gemm_sms = 0;
     int tma_batch = 32;
     int grid_exit = 0, nchunk = 0, per_chunk = 0, nqt = 0, nred = 0;
     size_t exit_smem = 0;
@@ -1067,6 +1070,10 @@ int setup_exit(ptycho_ctx *h) {
 }
 
 int launch_exit_pass(ptycho_ctx *h, int xm) {
+    if (h->fft_gemm) {
+        pm::Dft64Exit e{h->d_obj, h->d_probe, h->d_amp, h->d_pos, h->d_psi, h->d_err_pos, h->d_status, h->M, h->J};
+        return pm::dft64_exit_launch(e, h->gemm_sms, h->st);
+    }
     switch (h->R) {
         case 4: return launch_exit<4>(h, xm);
         case 8: return launch_exit<8>(h, xm);
@@ -1228,6 +1235,11 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (d->algorithm == PTYCHO_ALG_EPIE_COLOUR &&
         (!std::isfinite(d->epie_alpha) || !std::isfinite(d->epie_beta) || !(d->epie_alpha > 0.f) || !(d->epie_beta >= 0.f)))
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: ePIE step sizes must be finite, alpha > 0, beta >= 0");
+    if (d->fft_path != PTYCHO_FFT_RADIX_FP32 && d->fft_path != PTYCHO_FFT_DFTGEMM_BF16X3)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: unknown fft_path %d", d->fft_path);
+    if (d->fft_path == PTYCHO_FFT_DFTGEMM_BF16X3 &&
+        (d->N != 64 || d->modes != 1 || d->algorithm != PTYCHO_ALG_AP))
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: the DFT-GEMM path needs N = 64, one mode and algorithm AP");
     const int M = d->M, N = d->N, J = d->J, Q = d->modes;
     for (int j = 0; j < J; ++j) {
         const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
@@ -1240,6 +1252,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->algorithm = d->algorithm;
     h->epie_alpha = d->epie_alpha;
     h->epie_beta = d->epie_beta;
+    h->fft_gemm = d->fft_path == PTYCHO_FFT_DFTGEMM_BF16X3;
     std::vector<int> colour_list;
     int max_colour_size = 0;
     if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
@@ -1303,6 +1316,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->nred = (int)((NN * Q + kThreads - 1) / kThreads);
 
     rc = setup_exit(h);
+    if (!rc && h->fft_gemm) rc = pm::dft64_prepare(&h->gemm_sms);
     if (!rc) rc = dalloc(&h->d_pos, J);
     if (!rc) rc = dalloc(&h->d_obj, MM);
     if (!rc) rc = dalloc(&h->d_probe, NN * Q);

@@ -78,7 +78,7 @@ def _desc(**kw):
     pos = np.zeros((4, 2), np.int32)
     d = dict(M=128, N=64, J=4, modes=1, h_pos=pos.ctypes.data, d_fused=16, obj0=16, probe0=16,
              init_on_device=1, alpha_O=1e-3, alpha_P=1e-3, probe_update_start=0, algorithm=0,
-             epie_alpha=1.0, epie_beta=1.0, cuda_stream=None)
+             epie_alpha=1.0, epie_beta=1.0, fft_path=0, cuda_stream=None)
     d.update(kw)
     return api.PtychoDescC(**d), pos
 
@@ -86,7 +86,9 @@ def _desc(**kw):
 @pytest.mark.parametrize("kw", [{"N": 32}, {"N": 128}, {"J": 0}, {"M": 32}, {"alpha_O": -1.0},
                                 {"modes": 0}, {"modes": 9}, {"algorithm": 2},
                                 {"algorithm": 1, "modes": 2}, {"algorithm": 1, "epie_alpha": 0.0},
-                                {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None}])
+                                {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None},
+                                {"fft_path": 2}, {"fft_path": 1, "N": 16, "M": 64},
+                                {"fft_path": 1, "modes": 2}, {"fft_path": 1, "algorithm": 1}])
 def test_ptycho_init_rejects_bad_arguments(L, kw):
     d, _pos = _desc(**kw)
     h = ctypes.c_void_p(1234)
@@ -109,3 +111,14 @@ def test_null_handles(L):
     assert L.ptycho_get_probe(None, ctypes.c_void_p(16), 0) == api.PTYCHO_EINVAL
     assert L.ptycho_set_timing(None, 1) == api.PTYCHO_EINVAL
     L.ptycho_destroy(None)
+
+
+@pytest.mark.parametrize("B,N,inv", [(1, 32, 0), (1, 256, 0), (-1, 64, 0), (1, 64, 2)])
+def test_dft2_split_bf16_rejects_bad_arguments(L, B, N, inv):
+    rc = L.dft2_split_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), B, N, inv, ctypes.c_void_p(16), None)
+    assert rc == api.PTYCHO_EINVAL
+    assert api.last_error().startswith("dft2_split_bf16")
+
+
+def test_dft2_split_bf16_empty_batch_is_noop(L):
+    assert L.dft2_split_bf16(None, None, 0, 64, 0, None, None) == api.PTYCHO_OK
