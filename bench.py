@@ -39,9 +39,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["lab", "mixed"], default="lab",
+    ap.add_argument("--workload", choices=["lab", "mixed", "wide64"], default="lab",
                     help="lab: coherent lab-scale scan (the headline); mixed: the same scan with "
-                         "8 incoherent probe modes, 100 iterations")
+                         "8 incoherent probe modes, 100 iterations; wide64: 64^2 probe, 9216 "
+                         "raster positions on a 1024^2 object, 50 iterations")
+    ap.add_argument("--fft", choices=["radix_fp32", "dftgemm_bf16x3"], default="radix_fp32",
+                    help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64)")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration count (profiling runs only; not a bench value)")
     ap.add_argument("--positions", type=int, default=None,
@@ -154,6 +157,19 @@ def exit_wave_flops_per_position(N: int) -> float:
     return 2 * 5.0 * n * np.log2(n) + 20.0 * n
 
 
+def dftgemm_flops_per_position(N: int) -> float:
+    """Tensor-core flops of the split-BF16 exit wave: 4 real GEMM passes (2N x 2N DFT matrix
+    times 2N x N interleaved operand), 3 split terms each."""
+    return 4 * 3 * 2.0 * (2 * N) * (2 * N) * N
+
+
+def bf16_peak_tflops():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    return 1800.0, "fallback"
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     """148 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -202,7 +218,7 @@ def run_ours(args, world, rank, local):
 
     def step(timing=False):
         api.fuse_stack(raw, cfg.times, params, out=fused, stream=stream)
-        h = api.ptycho_init(fused, pos, obj0, probe0, stream=stream)
+        h = api.ptycho_init(fused, pos, obj0, probe0, stream=stream, fft_path=args.fft)
         if timing:
             api.ptycho_set_timing(h, True)
         api.ptycho_iterate(h, n_iter, errors=False)
@@ -249,7 +265,7 @@ def run_ours(args, world, rank, local):
         def e2e_step():
             raw_d.copy_(raw_h, non_blocking=True)
             api.fuse_stack(raw_d, cfg.times, params, out=fused, stream=stream)
-            h = api.ptycho_init(fused, pos, obj_h, probe_h, stream=stream)
+            h = api.ptycho_init(fused, pos, obj_h, probe_h, stream=stream, fft_path=args.fft)
             api.ptycho_iterate(h, n_iter, errors=False)
             api.ptycho_get_object(h, out_o)
             api.ptycho_get_probe(h, out_p)
@@ -292,11 +308,28 @@ def run_ours(args, world, rank, local):
             "hbm_view": {"achieved_gbs": round(hbm_algo, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                          "frac": round(hbm_algo / hbm_peak, 4),
                          "bytes_per_position": exit_wave_bytes_per_position(N)}}
+    if args.fft == "dftgemm_bf16x3":
+        tflops = dftgemm_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
+        bf16_peak, bf16_kind = bf16_peak_tflops()
+        roof = {"kernel": "k_dft64_gemm<exit> (tcgen05 split-BF16 DFT-GEMM)", "bound": "tensor",
+                "achieved": round(tflops, 2), "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": round(tflops / bf16_peak, 4), "peak_kind": bf16_kind,
+                "flops_per_position": dftgemm_flops_per_position(N),
+                "traffic": None, "avg_launch_ms": round(exit_ms, 4),
+                "fp32_fft_equivalent_tflops": round(flops, 2),
+                "hbm_view": {"achieved_gbs": round(hbm_algo, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                             "frac": round(hbm_algo / hbm_peak, 4),
+                             "bytes_per_position": exit_wave_bytes_per_position(N)}}
     fuse_n = fuse_launches(cfg.levels)
     launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
 
     conv = None
-    if rank == 0 and not args.no_nrmse and Q == 1:
+    if rank == 0 and not args.no_nrmse and Q == 1 and args.workload == "wide64":
+        fixed = 10 ** 9
+        conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, 200,
+                              probe_update_start=fixed, fft_path=f)
+                for f in ("radix_fp32", "dftgemm_bf16x3")]
+    elif rank == 0 and not args.no_nrmse and Q == 1:
         fixed = 10 ** 9
         conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, args.nrmse_iters,
                               probe_update_start=0),
@@ -314,16 +347,16 @@ def run_ours(args, world, rank, local):
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded Fermat-spiral scan, Poisson counts, 16-bit clip)",
-        "config": {"workload": ("lab-scale MNF + reconstruction: object 1024x1024 c64, probe 256x256, "
-                                "1600 positions, 5 exposures (1/4/16/64/256), 6-level pyramid, "
-                                f"{n_iter} iterations per step") if Q == 1 else
-                               ("mixed-state: the lab scan with 8 incoherent probe modes (+-10% "
-                                f"bandwidth), modulus per mode, {n_iter} iterations per step"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate",
+        "data": ("synthetic (seeded Fermat-spiral scan, Poisson counts, 16-bit clip)" if N == 256 else
+                 "synthetic (seeded jittered raster scan, Poisson counts, 12-bit clip)"),
+        "config": {"workload": workload_text(args.workload, n_iter),
+                   "fft": args.fft,
                    "modes": Q,
                    "positions": J, "exposures": K, "detector": N, "object": M, "levels": cfg.levels,
-                   "iterations": n_iter, "l2": "inputs larger than L2 (raw stack 1.05 GB per step)",
+                   "iterations": n_iter,
+                   "l2": f"inputs larger than L2 (raw stack {raw.numel() * 2 / 1e9:.2f} GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms_per_step": {n: round(float(m) / args.steps, 3) for n, m in zip(names, stage_ms)},
         "dominant_stage": names[dom],
@@ -335,6 +368,17 @@ def run_ours(args, world, rank, local):
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def workload_text(name: str, n_iter: int) -> str:
+    if name == "lab":
+        return ("lab-scale MNF + reconstruction: object 1024x1024 c64, probe 256x256, 1600 positions, "
+                f"5 exposures (1/4/16/64/256), 6-level pyramid, {n_iter} iterations per step")
+    if name == "mixed":
+        return ("mixed-state: the lab scan with 8 incoherent probe modes (+-10% bandwidth), modulus per "
+                f"mode, {n_iter} iterations per step")
+    return ("wide 64^2-probe scan: object 1024x1024 c64, probe 64x64, 96x96 raster (9216 positions), "
+            f"3 exposures (1/10/100), 4-level pyramid, {n_iter} iterations per step")
 
 
 # ----------------------------------------------------------------------------- convergence
@@ -356,7 +400,7 @@ def nrmse_host(obj, truth, mask):
 
 
 def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, max_iters, chunk=10,
-                  target=1e-2, probe_update_start=0, fusion="mnf", algorithm="ap"):
+                  target=1e-2, probe_update_start=0, fusion="mnf", algorithm="ap", fft_path="radix_fp32"):
     """FP32 reconstruction of the benchmarked scan from a flat object with the known probe:
     NRMSE to the ground truth every `chunk` iterations.  Device time counts the fusion, set-up
     and iterations (CUDA events), not the NRMSE evaluation."""
@@ -370,7 +414,7 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
     else:
         api.fuse_sli(raw, cfg.times, float(cfg.clip), out=fused, stream=stream)
     h = api.ptycho_init(fused, pos, obj0, probe0, probe_update_start=probe_update_start, stream=stream,
-                        algorithm=algorithm)
+                        algorithm=algorithm, fft_path=fft_path)
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
@@ -390,7 +434,8 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
     floor = min(v for _, _, v in traj)
     goal = target if floor <= target else 1.05 * floor
     hit = next((it, ms) for it, ms, v in traj if v <= goal)
-    return {"engine": algorithm, "fusion": fusion, "target": target, "reached_target": floor <= target,
+    return {"engine": algorithm, "fft": fft_path, "fusion": fusion, "target": target,
+            "reached_target": floor <= target,
             "floor": round(floor, 5), "goal_used": round(goal, 5), "iterations": hit[0],
             "seconds": round(hit[1] / 1e3, 4),
             "start": "flat object, true probe, " + ("probe updates on" if probe_update_start == 0

@@ -4,13 +4,16 @@
 // patches, each of the form D = G B^T with
 //   G  [128 x 128]  the 64-point DFT matrix F[u][r] = exp(-2 pi i u r / 64) as a real matrix
 //                   over interleaved (re, im) indices: G[2u + s'][2r + s]
-//   B  [256 x 128]  one row per transformed vector (4 patches x 64 vectors), interleaved re/im
-//   D  [128 x 256]  FP32 in tensor memory: lane 2u + s' of column n = part s' of (F b_n)[u].
+//   B  [128 x 128]  one row per transformed vector (2 patches x 64 vectors), interleaved re/im
+//   D  [128 x 128]  FP32 in tensor memory: lane 2u + s' of column n = part s' of (F b_n)[u].
 // Every operand is split x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and the product is
 // taken as G_hi B_hi + G_hi B_lo + G_lo B_hi (the lo x lo term, ~2^-18 relative, is dropped);
 // accumulation is FP32 in TMEM.
 //
-// The pass structure keeps a whole 4-patch group on chip.  Lane 2h + s of a pass's result
+// A CTA runs two independent pipelines of 256 threads (named barriers 1 and 2), each with its
+// own 2-patch group, operand buffers, 128 TMEM columns and mbarrier, sharing the DFT matrix:
+// while one pipeline's warps convert a pass result into the next operand, the other's MMAs
+// keep the tensor core busy.  The pass structure keeps a whole group on chip.  Lane 2h + s of a pass's result
 // holds part s of entry h of every transformed vector, i.e. one full vector of the NEXT
 // pass's operand (which transforms along the other axis), so each epilogue reads its TMEM lane
 // and writes one contiguous operand row:
@@ -37,18 +40,20 @@ using namespace pm;
 constexpr int kN = 64;                     // transform length
 constexpr int kK = 2 * kN;                 // real K: interleaved (re, im)
 constexpr int kRows = 2 * kN;              // rows of G = MMA M
-constexpr int kP = 4;                      // patches per group
+constexpr int kP = 2;                      // patches per pipeline group
 constexpr int kCols = kP * kN;             // MMA N
-constexpr int kThreads = 256;
+constexpr int kPipes = 2;                  // independent pipelines per CTA
+constexpr int kPipeThreads = 256;          // 8 warps: (TMEM lane quarter) x (patch)
+constexpr int kThreads = kPipes * kPipeThreads;
 constexpr uint32_t kLBO = 128;             // next core matrix along K
 constexpr uint32_t kSBO = (kK / 8) * 128;  // next 8-row group
 constexpr uint32_t kGBytes = kRows * kK * 2;
 constexpr uint32_t kBBytes = kCols * kK * 2;
-constexpr uint32_t kSmemBytes = 2 * kGBytes + 2 * kBBytes + 1024;   // + alignment slack
+constexpr uint32_t kSmemBytes = 2 * kGBytes + kPipes * 2 * kBBytes + 1024;   // + alignment slack
 constexpr uint32_t kTmemCols = 256;
 
 static_assert(kCols <= 256 && kCols % 16 == 0, "MMA N");
-static_assert(kTmemCols >= kCols, "accumulator columns");
+static_assert(kTmemCols >= kPipes * kCols, "accumulator columns");
 
 // G_hi then G_lo in the core-matrix layout; filled once per device by k_fill_dft64.
 __device__ uint4 g_dft64[2 * kGBytes / 16];
@@ -97,11 +102,13 @@ __global__ void k_fill_dft64() {
     gw[kGBytes / 2 + off] = __bfloat16_as_ushort(lo);
 }
 
-// Operand of pass 1: B[p N + c][2 r + s] = x_p[r][c], 4 rows (16 bytes) per store.
+// Operand of pass 1: B[p N + c][2 r + s] = x_p[r][c], 4 rows (16 bytes) per store; thread
+// (p, c) of each half of the block takes half of the row quads.
 template <int MODE>
 __device__ __forceinline__ void fill_input(const Args &a, int j0, int np, uint8_t *bh, uint8_t *bl) {
-    const int tid = threadIdx.x;
-    const int p = tid >> 6, c = tid & (kN - 1);
+    const int tid = threadIdx.x & (kPipeThreads - 1);
+    const int pc = tid & (kCols - 1), rhalf = tid / kCols;
+    const int p = pc >> 6, c = pc & (kN - 1);
     const int n = p * kN + c;
     const bool live = p < np;
     const float2 *x0 = nullptr, *x1 = nullptr;
@@ -114,8 +121,9 @@ __device__ __forceinline__ void fill_input(const Args &a, int j0, int np, uint8_
             x0 = a.in + (size_t)(j0 + p) * kN * kN + c;
         }
     }
+    constexpr int kRq = kN / 4 / (kPipeThreads / kCols);
 #pragma unroll 2
-    for (int rq = 0; rq < kN / 4; ++rq) {
+    for (int rq = rhalf * kRq; rq < (rhalf + 1) * kRq; ++rq) {
         uint32_t h[4], l[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -153,15 +161,16 @@ __device__ __forceinline__ void put_pair(uint8_t *bh, uint8_t *bl, int n, int c,
 // two entries.
 template <typename F>
 __device__ __forceinline__ void for_pairs(uint32_t lane_addr, int p, int part, F &&f) {
-#pragma unroll 1
+    uint32_t v[2][32];
+    tc::ld_32cols(lane_addr + (uint32_t)(p * kN), v[0]);
+    tc::ld_32cols(lane_addr + (uint32_t)(p * kN + 32), v[1]);
+    tc::wait_ld();
+#pragma unroll
     for (int ch = 0; ch < 2; ++ch) {
-        uint32_t v[32];
-        tc::ld_32cols(lane_addr + (uint32_t)(p * kN + ch * 32), v);
-        tc::wait_ld();
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
-            const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
-            const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
+            const float a0 = __uint_as_float(v[ch][i]), a1 = __uint_as_float(v[ch][i + 1]);
+            const float a2 = __uint_as_float(v[ch][i + 2]), a3 = __uint_as_float(v[ch][i + 3]);
             const float y0 = __shfl_xor_sync(0xffffffffu, part ? a0 : a2, 1);
             const float y1 = __shfl_xor_sync(0xffffffffu, part ? a1 : a3, 1);
             const float2 z0 = part ? make_float2(y0, a2) : make_float2(a0, y0);
@@ -171,14 +180,39 @@ __device__ __forceinline__ void for_pairs(uint32_t lane_addr, int p, int part, F
     }
 }
 
-// One GEMM pass D = G_hi B_hi + G_hi B_lo + G_lo B_hi.  Every thread calls it; returns false
-// (for all threads) when the completion wait gave up.
-__device__ __forceinline__ bool mma_pass(uint32_t tmem, uint32_t gh, uint32_t bh, uint64_t *bar,
+// Named barrier of one pipeline (ids 1, 2; id 0 is __syncthreads).
+__device__ __forceinline__ void pipe_sync(int pipe) {
+    asm volatile("bar.sync %0, %1;" ::"r"(pipe + 1), "r"(kPipeThreads) : "memory");
+}
+
+// Barrier of one pipeline that also returns the AND of `v` over its threads.
+__device__ __forceinline__ bool pipe_and(int pipe, bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred q, r;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred r, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, r;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)v), "r"(pipe + 1), "r"(kPipeThreads)
+        : "memory");
+    return out != 0;
+}
+
+// One GEMM pass D = G_hi B_hi + G_hi B_lo + G_lo B_hi of one pipeline.  Every thread of the
+// pipeline calls it; returns false (for all of them) when the completion wait gave up.
+__device__ __forceinline__ bool mma_pass(int pipe, uint32_t tmem, uint32_t gh, uint32_t bh, uint64_t *bar,
                                          uint32_t &phase) {
     tma::fence_async_smem();          // operand writes -> visible to the tensor core
     tc::fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    pipe_sync(pipe);
+    // Warp 0 of the pipeline issues the MMAs and polls their completion; the other warps sleep
+    // in the closing barrier instead of spinning (spinning warps would take issue slots from
+    // the other pipeline's epilogue).
+    const bool waiter = ((threadIdx.x & (kPipeThreads - 1)) >> 5) == 0;
+    bool ok = true;
+    if (waiter) {
+      if ((threadIdx.x & (kPipeThreads - 1)) == 0) {
         tc::fence_after();
         constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kCols);
         const uint32_t gl = gh + kGBytes, bl = bh + kBBytes;
@@ -192,10 +226,13 @@ __device__ __forceinline__ bool mma_pass(uint32_t tmem, uint32_t gh, uint32_t bh
                              idesc, (uint32_t)((t | ks) != 0));
         }
         tc::commit(bar);
+      }
+      __syncwarp();
+      ok = tma::mbar_wait(bar, phase);
+      tc::fence_before();
     }
-    const bool ok = tma::mbar_wait(bar, phase);
+    const bool all = pipe_and(pipe, ok);
     tc::fence_after();
-    const bool all = __syncthreads_and(ok) != 0;
     if (all) phase ^= 1;
     return all;
 }
@@ -204,55 +241,51 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sG = sm;
-    uint8_t *sBh = sm + 2 * kGBytes;
-    uint8_t *sBl = sBh + kBBytes;
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bars[kPipes];
     __shared__ uint32_t tmem_slot;
-    __shared__ double s_err[kThreads / 32][2];
+    __shared__ double s_err[kThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int pipe = tid / kPipeThreads, ptid = tid & (kPipeThreads - 1);
+    uint8_t *sG = sm;
+    uint8_t *sBh = sm + 2 * kGBytes + pipe * 2 * kBBytes;
+    uint8_t *sBl = sBh + kBBytes;
+    uint64_t *bar = &bars[pipe];
     for (int i = tid; i < (int)(2 * kGBytes / 16); i += kThreads) reinterpret_cast<uint4 *>(sG)[i] = g_dft64[i];
     if (warp == 0) tc::alloc(&tmem_slot, kTmemCols);
     if (tid == 0) {
-        tma::mbar_init(&bar, 1);
+        for (int q = 0; q < kPipes; ++q) tma::mbar_init(&bars[q], 1);
         tma::fence_barrier_init();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const uint32_t tmem = tmem_slot;
+    const uint32_t tmem = tmem_slot + (uint32_t)(pipe * kCols);   // this pipeline's columns
     const uint32_t gh = tc::smem_addr(sG), bh = tc::smem_addr(sBh);
     uint32_t phase = 0;
 
     const int row = 32 * (warp & 3) + lane;        // accumulator lane 2 h + part
     const int half = row >> 1, part = row & 1;
-    const int pbase = (warp >> 2) * 2;             // this warp's patches: pbase, pbase + 1
+    const int p = (warp >> 2) & (kP - 1);          // this warp's patch in the group
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float invN = 1.0f / (float)kN;
     const int ngroups = (a.J + kP - 1) / kP;
     bool failed = false;
 
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    for (int grp = blockIdx.x * kPipes + pipe; grp < ngroups; grp += gridDim.x * kPipes) {
         const int j0 = grp * kP;
         const int np = min(kP, a.J - j0);
         fill_input<MODE>(a, j0, np, sBh, sBl);
-        if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
+        const bool live = p < np;                  // warp-uniform
         // pass-2 operand: rows of W_p
-#pragma unroll 1
-        for (int pp = 0; pp < 2; ++pp) {
-            const int p = pbase + pp;
-            if (p >= np) continue;
+        if (live)
             for_pairs(lane_addr, p, part,
                       [&](int c, float2 z0, float2 z1) { put_pair(sBh, sBl, p * kN + half, c, z0, z1); });
-        }
-        if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
         if constexpr (MODE == MODE_DFT) {
             // lane (v, part) holds part of Psi_p[u][v] for every u
-#pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int p = pbase + pp;
-                if (p >= np) continue;
+            if (live) {
                 float2 *o = a.out + (size_t)(j0 + p) * kN * kN + half;
                 const float sy = a.inverse ? -invN : invN;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
@@ -262,13 +295,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
             }
         } else {
             // modulus constraint against A_j[v][u], then conj(Psi') as the pass-3 operand
-            float e[2] = {0.f, 0.f};
-#pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int p = pbase + pp;
-                if (p >= np) continue;
+            float ep = 0.f;
+            if (live) {
                 const float *amp = a.amp + (size_t)(j0 + p) * kN * kN + (size_t)half * kN;
-                float ep = 0.f;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     const float2 A2 = __ldg(reinterpret_cast<const float2 *>(amp + c));
                     float2 z[2] = {cscale(z0, invN), cscale(z1, invN)};
@@ -283,22 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
                     }
                     put_pair(sBh, sBl, p * kN + half, c, z[0], z[1]);
                 });
-                e[pp] = ep;
             }
-            if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
-#pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int p = pbase + pp;
-                if (p >= np) continue;
+            if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
+            if (live)
                 for_pairs(lane_addr, p, part,
                           [&](int c, float2 z0, float2 z1) { put_pair(sBh, sBl, p * kN + half, c, z0, z1); });
-            }
-            if (!mma_pass(tmem, gh, bh, &bar, phase)) { failed = true; break; }
+            if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
             // lane (x, part) holds part of N conj(psi'_p)[w][x] for every w
-#pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int p = pbase + pp;
-                if (p >= np) continue;
+            if (live) {
                 float2 *o = a.psi + (size_t)(j0 + p) * kN * kN + half;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     o[(size_t)c * kN] = make_float2(z0.x * invN, -z0.y * invN);
@@ -306,23 +327,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
                 });
             }
             // Fourier error per position: fixed-order sums over lanes, then over the 4 warps
+            double d = (double)ep;
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                double d = (double)e[pp];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                if (lane == 0) s_err[warp][pp] = d;
-            }
-            __syncthreads();
-            if (tid < np) {
-                const int w0 = (tid >> 1) * 4, pp = tid & 1;
-                a.err[j0 + tid] = ((s_err[w0][pp] + s_err[w0 + 1][pp]) + s_err[w0 + 2][pp]) + s_err[w0 + 3][pp];
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) s_err[warp] = d;
+            pipe_sync(pipe);
+            if (ptid < np) {
+                const double *se = s_err + pipe * (kPipeThreads / 32) + 4 * ptid;
+                a.err[j0 + ptid] = ((se[0] + se[1]) + se[2]) + se[3];
             }
         }
     }
     if (failed) {
-        if (tid == 0) atomicExch(a.status, 1);
-        tma::mbar_wait(&bar, phase);          // let MMAs still in flight finish (bounded)
+        if (ptid == 0) atomicExch(a.status, 1);
+        tma::mbar_wait(bar, phase);           // let MMAs still in flight finish (bounded)
     }
     tc::fence_before();
     __syncthreads();
@@ -338,7 +356,8 @@ bool g_ready[64] = {};
 int launch(const Args &a, int mode, int sm_count, cudaStream_t st) {
     if (a.J <= 0) return PTYCHO_OK;
     const int ngroups = (a.J + kP - 1) / kP;
-    const int grid = ngroups < sm_count ? ngroups : sm_count;
+    const int ctas = (ngroups + kPipes - 1) / kPipes;
+    const int grid = ctas < sm_count ? ctas : sm_count;
     if (mode == MODE_EXIT)
         k_dft64_gemm<MODE_EXIT><<<grid, kThreads, kSmemBytes, st>>>(a);
     else

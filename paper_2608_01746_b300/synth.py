@@ -73,6 +73,10 @@ CONFIGS = {
     "mixed_small": ScanConfig("mixed_small", M=256, N=64, scan="raster", radius=20.0,
                               times=(1.0, 10.0, 100.0), peak=1e4, clip=4095, levels=4, n_iter=20,
                               n_side=10, step=8, jitter=1, modes=8),
+    # The small scan's construction (64^2 probe, 3 exposures, 12-bit clip, 4 levels) on a
+    # 1024^2 object with a 96 x 96 raster, step 10: 9216 positions, enough to fill the GPU.
+    "wide64": ScanConfig("wide64", M=1024, N=64, scan="raster", radius=20.0, times=(1.0, 10.0, 100.0),
+                         peak=1e4, clip=4095, levels=4, n_iter=50, n_side=96, step=10, jitter=1),
     # Reduced cases for the CPU tests (same construction, smaller sizes).
     "tiny": ScanConfig("tiny", M=64, N=16, scan="raster", radius=5.0, times=(1.0, 10.0, 100.0),
                        peak=1e4, clip=4095, levels=3, n_iter=30, n_side=5, step=4, jitter=1,
@@ -83,7 +87,7 @@ CONFIGS = {
 
 
 def seed_for(name: str) -> int:
-    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small"]
+    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small", "wide64"]
     return 1000 + (order.index(name) if name in order else 99)
 
 
