@@ -203,6 +203,38 @@ void ptycho_destroy(ptycho_handle h);
 int ptycho_set_timing(ptycho_handle h, int enable);
 int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches /*[4]*/);
 
+/*
+ * Batches of independent reconstructions: many datasets of uneven sizes (positions, object and
+ * probe sides) advanced together, iteration by iteration.  The paper reconstructs one scan at a
+ * time; batching is a throughput form of the same iteration for many scans.
+ *   ptycho_batch_create  groups n existing full-batch (AP) handles (any N, modes, fft_path;
+ *                        stage timing off; each handle at most once).  Datasets of one probe
+ *                        size and FFT form with N <= 64 share one persistent exit-wave launch per
+ *                        iteration; every dataset's other kernels run on its own branch, and the
+ *                        branches run concurrently.  flags: PTYCHO_BATCH_GRAPH captures an
+ *                        iteration as a CUDA graph and replays it (re-captured when the set of
+ *                        datasets updating their probe changes); PTYCHO_BATCH_AUTOTUNE times
+ *                        candidate launch shapes (persistent grid sizes; rows per TMA stage at
+ *                        N = 256) on the datasets themselves, keeps the fastest and restores
+ *                        every object and probe (results are unaffected).  The handles stay
+ *                        owned by the caller, must outlive the batch, and must not be iterated
+ *                        while a batch call is in flight.  The batch runs on a stream of its
+ *                        own, ordered after `cuda_stream` and the handles' streams at each
+ *                        call and before their later work.  Synchronises `cuda_stream`.
+ *   ptycho_batch_iterate n_iter iterations of every dataset, the same arithmetic as
+ *                        ptycho_iterate on each handle.  h_err: host [n] or NULL, each dataset's
+ *                        Fourier error of the last iteration (then the call synchronises and
+ *                        reports PTYCHO_ENONFINITE / PTYCHO_ETIMEDOUT).  Later calls on a handle
+ *                        are ordered after the batch's work.
+ *   ptycho_batch_describe  the autotuner's choices and timings as a JSON object text.
+ */
+typedef struct ptycho_batch_ctx *ptycho_batch;
+enum { PTYCHO_BATCH_GRAPH = 1, PTYCHO_BATCH_AUTOTUNE = 2 };
+int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handles, int n, int flags, void *cuda_stream);
+int ptycho_batch_iterate(ptycho_batch b, int n_iter, double *h_err);
+int ptycho_batch_describe(ptycho_batch b, char *buf, int len);
+void ptycho_batch_destroy(ptycho_batch b);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *ptycho_last_error(void);
 

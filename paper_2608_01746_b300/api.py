@@ -75,6 +75,14 @@ def lib() -> ctypes.CDLL:
     L.fuse_stack_noalloc.argtypes = L.fuse_stack.argtypes
     L.fuse_stack_noalloc.restype = ci
     L.fuse_sli.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp]
+    L.ptycho_batch_create.restype = ci
+    L.ptycho_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ci, ci, vp]
+    L.ptycho_batch_iterate.restype = ci
+    L.ptycho_batch_iterate.argtypes = [vp, ci, ctypes.POINTER(cd)]
+    L.ptycho_batch_describe.restype = ci
+    L.ptycho_batch_describe.argtypes = [vp, ctypes.c_char_p, ci]
+    L.ptycho_batch_destroy.restype = None
+    L.ptycho_batch_destroy.argtypes = [vp]
     L.dft2_split_bf16.restype = ci
     L.dft2_split_bf16.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.fuse_sli.restype = ci
@@ -301,3 +309,55 @@ def ptycho_stage_times(h: PtychoHandle):
     n = (ctypes.c_longlong * 4)()
     _check(lib().ptycho_stage_times(h.ptr, ms, n))
     return list(ms), list(n)
+
+
+BATCH_GRAPH = 1
+BATCH_AUTOTUNE = 2
+
+
+class PtychoBatch:
+    """Owner of a ``ptycho_batch`` over existing handles (which it does not own)."""
+
+    def __init__(self, ptr: int, handles):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.handles = list(handles)
+
+    def close(self) -> None:
+        if self.ptr:
+            lib().ptycho_batch_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ptycho_batch_create(handles, graph: bool = False, autotune: bool = False, stream=None) -> PtychoBatch:
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    b = ctypes.c_void_p()
+    flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+    _check(lib().ptycho_batch_create(ctypes.byref(b), arr, n, flags, ctypes.c_void_p(_stream_ptr(stream))))
+    return PtychoBatch(b.value, handles)
+
+
+def ptycho_batch_iterate(b: PtychoBatch, n_iter: int, errors: bool = True):
+    """Run n_iter iterations of every dataset; returns each dataset's last-iteration error."""
+    if errors:
+        err = np.zeros(len(b.handles), dtype=np.float64)
+        _check(lib().ptycho_batch_iterate(b.ptr, n_iter, err.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return err
+    _check(lib().ptycho_batch_iterate(b.ptr, n_iter, None))
+    return None
+
+
+def ptycho_batch_describe(b: PtychoBatch) -> str:
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib().ptycho_batch_describe(b.ptr, buf, len(buf)))
+    return buf.value.decode()
+
+
+def ptycho_batch_destroy(b: PtychoBatch) -> None:
+    b.close()

@@ -72,6 +72,10 @@ struct Args {
     int inverse;            // dft: 1 = unitary inverse
     int *status;            // set to 1 when a bounded wait gives up
     int M, J;               // object side; number of patches / transforms
+    // exit, several datasets: group g belongs to dataset d with gstart[d] <= g < gstart[d + 1]
+    const pm::Dft64Exit *table;
+    const int *gstart;
+    int ntable;
 };
 
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
@@ -269,13 +273,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
     const int p = (warp >> 2) & (kP - 1);          // this warp's patch in the group
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const float invN = 1.0f / (float)kN;
-    const int ngroups = (a.J + kP - 1) / kP;
+    const int ngroups = a.table ? __ldg(a.gstart + a.ntable) : (a.J + kP - 1) / kP;
     bool failed = false;
 
     for (int grp = blockIdx.x * kPipes + pipe; grp < ngroups; grp += gridDim.x * kPipes) {
-        const int j0 = grp * kP;
-        const int np = min(kP, a.J - j0);
-        fill_input<MODE>(a, j0, np, sBh, sBl);
+        Args c = a;
+        int lg = grp;
+        if (a.table) {
+            int lo = 0, hi = a.ntable - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.gstart + mid) <= grp) lo = mid;
+                else hi = mid - 1;
+            }
+            const pm::Dft64Exit &e = a.table[lo];
+            c.obj = e.obj;
+            c.probe = e.probe;
+            c.amp = e.amp;
+            c.pos = e.pos;
+            c.psi = e.psi;
+            c.err = e.err;
+            c.M = e.M;
+            c.J = e.J;
+            lg = grp - __ldg(a.gstart + lo);
+        }
+        const int j0 = lg * kP;
+        const int np = min(kP, c.J - j0);
+        fill_input<MODE>(c, j0, np, sBh, sBl);
         if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
         const bool live = p < np;                  // warp-uniform
         // pass-2 operand: rows of W_p
@@ -286,8 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
         if constexpr (MODE == MODE_DFT) {
             // lane (v, part) holds part of Psi_p[u][v] for every u
             if (live) {
-                float2 *o = a.out + (size_t)(j0 + p) * kN * kN + half;
-                const float sy = a.inverse ? -invN : invN;
+                float2 *o = c.out + (size_t)(j0 + p) * kN * kN + half;
+                const float sy = c.inverse ? -invN : invN;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     o[(size_t)c * kN] = make_float2(z0.x * invN, z0.y * sy);
                     o[(size_t)(c + 1) * kN] = make_float2(z1.x * invN, z1.y * sy);
@@ -297,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
             // modulus constraint against A_j[v][u], then conj(Psi') as the pass-3 operand
             float ep = 0.f;
             if (live) {
-                const float *amp = a.amp + (size_t)(j0 + p) * kN * kN + (size_t)half * kN;
+                const float *amp = c.amp + (size_t)(j0 + p) * kN * kN + (size_t)half * kN;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     const float2 A2 = __ldg(reinterpret_cast<const float2 *>(amp + c));
                     float2 z[2] = {cscale(z0, invN), cscale(z1, invN)};
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
             if (!mma_pass(pipe, tmem, gh, bh, bar, phase)) { failed = true; break; }
             // lane (x, part) holds part of N conj(psi'_p)[w][x] for every w
             if (live) {
-                float2 *o = a.psi + (size_t)(j0 + p) * kN * kN + half;
+                float2 *o = c.psi + (size_t)(j0 + p) * kN * kN + half;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     o[(size_t)c * kN] = make_float2(z0.x * invN, -z0.y * invN);
                     o[(size_t)(c + 1) * kN] = make_float2(z1.x * invN, -z1.y * invN);
@@ -334,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
             pipe_sync(pipe);
             if (ptid < np) {
                 const double *se = s_err + pipe * (kPipeThreads / 32) + 4 * ptid;
-                a.err[j0 + ptid] = ((se[0] + se[1]) + se[2]) + se[3];
+                c.err[j0 + ptid] = ((se[0] + se[1]) + se[2]) + se[3];
             }
         }
     }
@@ -353,9 +377,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
 std::mutex g_mu;
 bool g_ready[64] = {};
 
-int launch(const Args &a, int mode, int sm_count, cudaStream_t st) {
-    if (a.J <= 0) return PTYCHO_OK;
-    const int ngroups = (a.J + kP - 1) / kP;
+int launch(const Args &a, int mode, int sm_count, cudaStream_t st, int total_groups = -1) {
+    const int ngroups = total_groups >= 0 ? total_groups : (a.J + kP - 1) / kP;
+    if (ngroups <= 0) return PTYCHO_OK;
     const int ctas = (ngroups + kPipes - 1) / kPipes;
     const int grid = ctas < sm_count ? ctas : sm_count;
     if (mode == MODE_EXIT)
@@ -397,6 +421,18 @@ int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st) {
     a.M = e.M;
     a.J = e.J;
     return launch(a, MODE_EXIT, sm_count, st);
+}
+
+int dft64_groups(int J) { return (J + kP - 1) / kP; }
+
+int dft64_exit_multi_launch(const Dft64Exit *d_table, const int *d_gstart, int ntable, int total_groups,
+                            int *d_status, int grid_cap, cudaStream_t st) {
+    Args a{};
+    a.table = d_table;
+    a.gstart = d_gstart;
+    a.ntable = ntable;
+    a.status = d_status;
+    return launch(a, MODE_EXIT, grid_cap, st, total_groups);
 }
 
 }  // namespace pm

@@ -24,4 +24,13 @@ int dft64_prepare(int *sm_count);
 // psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] for every j, tensor-core DFTs; one launch.
 int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
 
+// Patch groups the kernel makes of J positions (the unit of work of one pipeline).
+int dft64_groups(int J);
+
+// One launch over several datasets: d_table[d] (device) describes dataset d, whose groups are
+// d_gstart[d] .. d_gstart[d + 1] - 1 (device prefix, d_gstart[ntable] = total_groups).  At most
+// grid_cap CTAs.
+int dft64_exit_multi_launch(const Dft64Exit *d_table, const int *d_gstart, int ntable, int total_groups,
+                            int *d_status, int grid_cap, cudaStream_t st);
+
 }  // namespace pm

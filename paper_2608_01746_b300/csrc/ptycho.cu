@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include <cuda.h>
@@ -46,6 +47,11 @@ enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
 enum { XM_FULL = 0, XM_FWD = 1, XM_INV = 2, XM_LIST = 3 };
 
 struct ExitArgs {
+    // XM_FULL only: when `table` is set, the launch serves several datasets of the same N: unit
+    // iu belongs to the dataset d with ustart[d] <= iu < ustart[d + 1] and uses table[d].
+    const ExitArgs *table;
+    const int *ustart;
+    int ntable;
     const float2 *obj;
     const float2 *probe;     // [Q][N][N]
     const float *amp;        // [J][N][N] column-major per position: amp[j][kx][ky]
@@ -91,24 +97,35 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     __syncthreads();
     float2 *xb = xb_all + g * R * (R + 1);
     const float invN = 1.0f / (float)N;
-    const int M = a.M;
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
 
     for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
-        const int u = (XM == XM_LIST) ? a.list[iu] : iu;
+        int u = (XM == XM_LIST) ? a.list[iu] : iu;
+        ExitArgs c = a;
+        if (XM == XM_FULL && a.table) {
+            int lo = 0, hi = a.ntable - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.ustart + mid) <= iu) lo = mid;
+                else hi = mid - 1;
+            }
+            c = a.table[lo];
+            u = iu - __ldg(a.ustart + lo);
+        }
+        const int M = c.M;
         const int j = kFull ? u : u / a.Q;
         const int mode = kFull ? 0 : u % a.Q;
-        float2 *psi_u = a.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
+        float2 *psi_u = c.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
         if constexpr (XM != XM_INV) {
             // (1) psi = P_m * O_j, forward row FFTs in place
-            const int2 pj = a.pos[j];
+            const int2 pj = c.pos[j];
             for (int r0 = 0; r0 < N; r0 += G) {
                 const int r = r0 + g;
                 if (r < N) {                                 // warp-uniform (see fft.cuh)
                     float2 d[R];
-                    const float2 *orow = a.obj + (size_t)(pj.x + r) * M + pj.y;
-                    const float2 *prow = a.probe + (size_t)mode * N * N + (size_t)r * N;
+                    const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
+                    const float2 *prow = c.probe + (size_t)mode * N * N + (size_t)r * N;
 #pragma unroll
                     for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
                     pm::fft_group<R, -1>(d, xb, tw, t);
@@ -122,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
         __syncthreads();
         // (2) column FFTs: forward (+ modulus + inverse in XM_FULL) or inverse (XM_INV)
         float err = 0.f;
-        const float *amp_j = a.amp + (size_t)j * N * N;
+        const float *amp_j = c.amp + (size_t)j * N * N;
         for (int c0 = 0; c0 < N; c0 += G) {
             const int c = c0 + g;
             if (c < N) {
@@ -179,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
             if (tid == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
-                a.err[j] = sum;
+                c.err[j] = sum;
             }
         }
         __syncthreads();          // the next unit's first pass overwrites the tile
@@ -1041,7 +1058,7 @@ int setup_exit_kernel(ptycho_ctx *h) {
 
 template <int R>
 int launch_exit(ptycho_ctx *h, int xm) {
-    ExitArgs a;
+    ExitArgs a{};
     a.obj = h->d_obj;
     a.probe = h->d_probe;
     a.amp = h->d_amp;
@@ -1150,14 +1167,17 @@ int iterate_one_epie(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool u
     return stage_end(h, ST_ERROR, ev_base + 3, 1);
 }
 
-int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe) {
+// exit_done: the exit waves of this iteration were already computed by a multi-dataset launch.
+int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe, bool exit_done = false) {
     if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) return iterate_one_epie(h, it_in_call, ev_base, update_probe);
     int rc;
     // exit waves
-    if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
-    int exit_launches = 1;
-    if ((rc = launch_exit_any(h, &exit_launches))) return rc;
-    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, exit_launches))) return rc;
+    if (!exit_done) {
+        if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
+        int exit_launches = 1;
+        if ((rc = launch_exit_any(h, &exit_launches))) return rc;
+        if ((rc = stage_end(h, ST_EXIT, ev_base + 0, exit_launches))) return rc;
+    }
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
     if (h->Q == 1)
@@ -1467,3 +1487,436 @@ extern "C" int ptycho_get_colouring(ptycho_handle h, int32_t *h_colour, int *n_c
     *n_colours = (int)h->colour_start.size() - 1;
     return PTYCHO_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Batches of independent reconstructions (many datasets of uneven sizes).  One iteration of a
+// batch = one exit-wave launch per class of small datasets (N = 16 or 64 radix, or N = 64
+// tensor-core DFT), whose persistent CTAs walk the concatenated positions of every dataset of
+// the class, plus, per dataset, the N = 256 exit-wave kernel (if any), the object update, the
+// probe update and the error reduction on the dataset's own branch (stream); branches run
+// concurrently and join on the batch stream.  With PTYCHO_BATCH_GRAPH the iteration is
+// captured once as a CUDA graph and replayed.  PTYCHO_BATCH_AUTOTUNE times candidate launch
+// shapes on the batch's own data (state restored afterwards) and keeps the fastest.
+struct ptycho_batch_ctx {
+    struct Class {
+        int kind = 0;                         // 4 or 8: radix kernel of that R; 64: tensor-core DFT
+        std::vector<int> members;
+        ExitArgs *d_table = nullptr;
+        pm::Dft64Exit *d_gtable = nullptr;
+        int *d_start = nullptr;               // prefix of positions (radix) or patch groups (tensor)
+        int units = 0;
+        int grid = 0, grid_max = 0;
+        size_t smem = 0;
+    };
+    std::vector<ptycho_ctx *> hs;
+    cudaStream_t user_st = nullptr;           // the caller's stream (may be the legacy default stream)
+    cudaStream_t st = nullptr;                // the batch's own stream (capturable)
+    cudaEvent_t ev_user = nullptr;
+    int flags = 0;
+    int sms = 0;
+    std::vector<cudaStream_t> side, cls_st;
+    cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> ev_join, ev_cls, ev_in;
+    std::vector<Class> cls;
+    std::vector<int> cls_of;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<char> cap_mask;
+    int *d_status = nullptr;
+    std::string describe;
+};
+
+namespace {
+
+void free_batch(ptycho_batch_ctx *b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto &c : b->cls) {
+        if (c.d_table) cudaFree(c.d_table);
+        if (c.d_gtable) cudaFree(c.d_gtable);
+        if (c.d_start) cudaFree(c.d_start);
+    }
+    for (cudaStream_t s : b->side) if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : b->cls_st) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev_join) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_cls) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_in) if (e) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_user) cudaEventDestroy(b->ev_user);
+    if (b->st) cudaStreamDestroy(b->st);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->d_status) cudaFree(b->d_status);
+    delete b;
+}
+
+int launch_class(ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c, cudaStream_t s) {
+    if (c.kind == 64)
+        return pm::dft64_exit_multi_launch(c.d_gtable, c.d_start, (int)c.members.size(), c.units, b->d_status, c.grid,
+                                           s);
+    ExitArgs a{};
+    a.table = c.d_table;
+    a.ustart = c.d_start;
+    a.ntable = (int)c.members.size();
+    a.J = c.units;
+    a.Q = 1;
+    if (c.kind == 4) k_exit_wave<4, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
+    else k_exit_wave<8, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
+    PM_LAUNCHED("k_exit_wave (datasets)");
+    return PTYCHO_OK;
+}
+
+// Enqueue one iteration of every dataset on the batch stream (fork / join over side streams).
+int enqueue_iteration(ptycho_batch_ctx *b, const std::vector<char> &upd) {
+    PM_CUDA(cudaEventRecord(b->ev_fork, b->st));
+    for (size_t c = 0; c < b->cls.size(); ++c) {
+        PM_CUDA(cudaStreamWaitEvent(b->cls_st[c], b->ev_fork, 0));
+        int rc = launch_class(b, b->cls[c], b->cls_st[c]);
+        if (rc) return rc;
+        PM_CUDA(cudaEventRecord(b->ev_cls[c], b->cls_st[c]));
+    }
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        ptycho_ctx *h = b->hs[i];
+        cudaStream_t s = b->side[i];
+        PM_CUDA(cudaStreamWaitEvent(s, b->ev_fork, 0));
+        const int c = b->cls_of[i];
+        if (c >= 0) PM_CUDA(cudaStreamWaitEvent(s, b->ev_cls[c], 0));
+        cudaStream_t saved = h->st;
+        h->st = s;
+        const int rc = iterate_one(h, 0, 0, upd[i] != 0, c >= 0);
+        h->st = saved;
+        if (rc) return rc;
+        PM_CUDA(cudaEventRecord(b->ev_join[i], s));
+        PM_CUDA(cudaStreamWaitEvent(b->st, b->ev_join[i], 0));
+    }
+    return PTYCHO_OK;
+}
+
+std::vector<char> update_mask(const ptycho_batch_ctx *b) {
+    std::vector<char> m(b->hs.size());
+    for (size_t i = 0; i < b->hs.size(); ++i) m[i] = b->hs[i]->iter >= b->hs[i]->probe_update_start;
+    return m;
+}
+
+// n_iter iterations; graph mode re-captures when the set of probe-updating datasets changes.
+int run_iterations(ptycho_batch_ctx *b, int n_iter, bool graph) {
+    for (int it = 0; it < n_iter; ++it) {
+        const std::vector<char> m = update_mask(b);
+        int rc;
+        if (graph) {
+            if (!b->exec || m != b->cap_mask) {
+                if (b->exec) { PM_CUDA(cudaGraphExecDestroy(b->exec)); b->exec = nullptr; }
+                PM_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+                rc = enqueue_iteration(b, m);
+                cudaGraph_t g = nullptr;
+                const cudaError_t e = cudaStreamEndCapture(b->st, &g);
+                if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+                if (e != cudaSuccess) return pm::cuda_fail(e, "cudaStreamEndCapture");
+                const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e2 != cudaSuccess) { b->exec = nullptr; return pm::cuda_fail(e2, "cudaGraphInstantiate"); }
+                b->cap_mask = m;
+            }
+            PM_CUDA(cudaGraphLaunch(b->exec, b->st));
+        } else if ((rc = enqueue_iteration(b, m))) {
+            return rc;
+        }
+        for (ptycho_ctx *h : b->hs) ++h->iter;
+    }
+    return PTYCHO_OK;
+}
+
+// N = 256 kernels: rows per TMA stage (16 or 32); re-derives the grid, slot buffer and maps.
+int retune_tma(ptycho_ctx *h, int B) {
+    int per_sm = 0, sms = 0, dev = 0, rc;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (B == 32) rc = setup_tma_kernel<32, XM_FULL>(h, &per_sm);
+    else rc = setup_tma_kernel<16, XM_FULL>(h, &per_sm);
+    if (rc) return rc;
+    h->tma_batch = B;
+    const int grid = std::max(1, std::min(h->J, sms * per_sm));
+    if (grid != h->grid_exit) {
+        PM_CUDA(cudaStreamSynchronize(h->st));
+        if (h->d_slot) PM_CUDA(cudaFree(h->d_slot));
+        h->d_slot = nullptr;
+        h->grid_exit = grid;
+        if ((rc = dalloc(&h->d_slot, (size_t)grid * h->N * h->N))) return rc;
+    }
+    return encode_exit_tma(h);
+}
+
+double time_iterations(ptycho_batch_ctx *b, int n, int *rc) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    *rc = run_iterations(b, 1, false);                     // warm-up
+    if (!*rc) cudaEventRecord(e0, b->st);
+    if (!*rc) *rc = run_iterations(b, n, false);
+    float ms = 0.f;
+    if (!*rc) {
+        cudaEventRecord(e1, b->st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+// Coordinate search over the launch shapes, on the batch's own data; object, probe and
+// iteration counters are restored afterwards.
+int autotune(ptycho_batch_ctx *b) {
+    const int reps = 3;
+    std::vector<float2 *> so(b->hs.size()), sp(b->hs.size());
+    std::vector<long long> sit(b->hs.size());
+    int rc = PTYCHO_OK;
+    for (size_t i = 0; i < b->hs.size() && !rc; ++i) {
+        ptycho_ctx *h = b->hs[i];
+        rc = dalloc(&so[i], (size_t)h->M * h->M);
+        if (!rc) rc = dalloc(&sp[i], (size_t)h->Q * h->N * h->N);
+        if (!rc) {
+            cudaMemcpyAsync(so[i], h->d_obj, (size_t)h->M * h->M * sizeof(float2), cudaMemcpyDeviceToDevice, b->st);
+            cudaMemcpyAsync(sp[i], h->d_probe, (size_t)h->Q * h->N * h->N * sizeof(float2), cudaMemcpyDeviceToDevice,
+                            b->st);
+        }
+        sit[i] = h->iter;
+    }
+    std::string rep = "{";
+    char buf[256];
+    // grids of the multi-dataset classes
+    for (size_t c = 0; c < b->cls.size() && !rc; ++c) {
+        auto &k = b->cls[c];
+        std::vector<int> cand;
+        for (int m : {1, 2, 3, 4, 6, 8}) {
+            const int g = std::min(k.units, std::min(k.grid_max, m * b->sms));
+            if (g >= 1 && std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+        }
+        if (k.kind == 64) cand = {std::min(k.units, b->sms / 2), std::min(k.units, b->sms)};
+        int best = k.grid;
+        double best_ms = 1e30;
+        std::string tried;
+        for (int g : cand) {
+            if (g < 1) continue;
+            k.grid = g;
+            const double ms = time_iterations(b, reps, &rc);
+            if (rc) break;
+            std::snprintf(buf, sizeof buf, "%s%d:%.3f", tried.empty() ? "" : ",", g, ms / reps);
+            tried += buf;
+            if (ms < best_ms) { best_ms = ms; best = g; }
+        }
+        k.grid = best;
+        std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d, \"class_%s_tried_ms\": \"%s\"",
+                      rep.size() > 1 ? ", " : "", k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"),
+                      best, k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"), tried.c_str());
+        rep += buf;
+    }
+    // rows per TMA stage of the N = 256 datasets (all together)
+    std::vector<ptycho_ctx *> big;
+    for (ptycho_ctx *h : b->hs)
+        if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP) big.push_back(h);
+    if (!big.empty() && !rc) {
+        int best = 16;
+        double best_ms = 1e30;
+        std::string tried;
+        for (int B : {16, 32}) {
+            for (ptycho_ctx *h : big)
+                if (!rc) rc = retune_tma(h, B);
+            if (rc) break;
+            const double ms = time_iterations(b, reps, &rc);
+            if (rc) break;
+            std::snprintf(buf, sizeof buf, "%s%d:%.3f", tried.empty() ? "" : ",", B, ms / reps);
+            tried += buf;
+            if (ms < best_ms) { best_ms = ms; best = B; }
+        }
+        for (ptycho_ctx *h : big)
+            if (!rc) rc = retune_tma(h, best);
+        std::snprintf(buf, sizeof buf, "%s\"tma_rows_n256\": %d, \"tma_rows_tried_ms\": \"%s\"",
+                      rep.size() > 1 ? ", " : "", best, tried.c_str());
+        rep += buf;
+    }
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        ptycho_ctx *h = b->hs[i];
+        if (so[i]) cudaMemcpyAsync(h->d_obj, so[i], (size_t)h->M * h->M * sizeof(float2), cudaMemcpyDeviceToDevice, b->st);
+        if (sp[i])
+            cudaMemcpyAsync(h->d_probe, sp[i], (size_t)h->Q * h->N * h->N * sizeof(float2), cudaMemcpyDeviceToDevice,
+                            b->st);
+        h->iter = sit[i];
+    }
+    cudaStreamSynchronize(b->st);
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        if (so[i]) cudaFree(so[i]);
+        if (sp[i]) cudaFree(sp[i]);
+    }
+    b->describe = rep + "}";
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handles, int n, int flags,
+                                   void *cuda_stream) {
+    if (!out) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: out is NULL");
+    *out = nullptr;
+    if (!handles || n < 1) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: need n >= 1 handles");
+    if (flags & ~(PTYCHO_BATCH_GRAPH | PTYCHO_BATCH_AUTOTUNE))
+        return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: unknown flags 0x%x", flags);
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i]) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: handle %d is NULL", i);
+        if (handles[i]->algorithm != PTYCHO_ALG_AP)
+            return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: handle %d is not a full-batch (AP) handle", i);
+        if (handles[i]->timing)
+            return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: handle %d has stage timing enabled", i);
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == handles[i])
+                return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: handle %d appears twice", i);
+    }
+    ptycho_batch_ctx *b = new (std::nothrow) ptycho_batch_ctx();
+    if (!b) return pm::fail(PTYCHO_ENOMEM, "ptycho_batch_create: host allocation failed");
+    b->user_st = (cudaStream_t)cuda_stream;
+    b->flags = flags;
+    int rc = PTYCHO_OK, dev = 0;
+    auto bail = [&](int r) { free_batch(b); return r; };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming)) ||
+        (e = cudaEventRecord(b->ev_user, b->user_st)) || (e = cudaStreamWaitEvent(b->st, b->ev_user, 0)))
+        return bail(pm::cuda_fail(e, "ptycho_batch_create: stream"));
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)))
+        return bail(pm::cuda_fail(e, "ptycho_batch_create: device query"));
+    b->hs.assign(handles, handles + n);
+    b->cls_of.assign(n, -1);
+    // classes of datasets served by one multi-dataset exit-wave launch
+    for (int i = 0; i < n; ++i) {
+        ptycho_ctx *h = b->hs[i];
+        if (h->Q != 1 || h->exit_tma) continue;
+        const int kind = h->fft_gemm ? 64 : h->R;
+        int c = -1;
+        for (size_t k = 0; k < b->cls.size(); ++k)
+            if (b->cls[k].kind == kind) c = (int)k;
+        if (c < 0) {
+            b->cls.emplace_back();
+            b->cls.back().kind = kind;
+            c = (int)b->cls.size() - 1;
+        }
+        b->cls[c].members.push_back(i);
+        b->cls_of[i] = c;
+    }
+    if ((rc = dalloc(&b->d_status, 1))) return bail(rc);
+    if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->st))) return bail(pm::cuda_fail(e, "clear status"));
+    for (auto &c : b->cls) {
+        const int nm = (int)c.members.size();
+        std::vector<int> start(nm + 1, 0);
+        if (c.kind == 64) {
+            std::vector<pm::Dft64Exit> t(nm);
+            for (int m = 0; m < nm; ++m) {
+                ptycho_ctx *h = b->hs[c.members[m]];
+                t[m] = pm::Dft64Exit{h->d_obj, h->d_probe, h->d_amp, h->d_pos, h->d_psi, h->d_err_pos, b->d_status, h->M,
+                                     h->J};
+                start[m + 1] = start[m] + pm::dft64_groups(h->J);
+            }
+            if ((rc = dalloc(&c.d_gtable, nm))) return bail(rc);
+            if ((e = cudaMemcpy(c.d_gtable, t.data(), nm * sizeof(pm::Dft64Exit), cudaMemcpyHostToDevice)))
+                return bail(pm::cuda_fail(e, "copy dataset table"));
+            c.grid_max = b->sms;
+        } else {
+            std::vector<ExitArgs> t(nm);
+            for (int m = 0; m < nm; ++m) {
+                ptycho_ctx *h = b->hs[c.members[m]];
+                ExitArgs a{};
+                a.obj = h->d_obj; a.probe = h->d_probe; a.amp = h->d_amp; a.pos = h->d_pos; a.psi = h->d_psi;
+                a.err = h->d_err_pos; a.M = h->M; a.J = h->J; a.Q = 1;
+                t[m] = a;
+                start[m + 1] = start[m] + h->J;
+            }
+            if ((rc = dalloc(&c.d_table, nm))) return bail(rc);
+            if ((e = cudaMemcpy(c.d_table, t.data(), nm * sizeof(ExitArgs), cudaMemcpyHostToDevice)))
+                return bail(pm::cuda_fail(e, "copy dataset table"));
+            int per_sm = 0;
+            c.smem = b->hs[c.members[0]]->exit_smem;
+            if (c.kind == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<4, XM_FULL>, kThreads, c.smem);
+            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<8, XM_FULL>, kThreads, c.smem);
+            if (e) return bail(pm::cuda_fail(e, "occupancy query"));
+            c.grid_max = std::max(1, per_sm) * b->sms;
+        }
+        c.units = start[nm];
+        c.grid = std::max(1, std::min(c.units, c.grid_max));
+        if ((rc = dalloc(&c.d_start, nm + 1))) return bail(rc);
+        if ((e = cudaMemcpy(c.d_start, start.data(), (nm + 1) * sizeof(int), cudaMemcpyHostToDevice)))
+            return bail(pm::cuda_fail(e, "copy dataset prefix"));
+    }
+    // every dataset's error slot for the batch's iterations
+    for (ptycho_ctx *h : b->hs)
+        if (h->err_cap < 1) {
+            if ((rc = dalloc(&h->d_err, 1))) return bail(rc);
+            h->err_cap = 1;
+        }
+    b->side.assign(n, nullptr);
+    b->ev_join.assign(n, nullptr);
+    b->ev_in.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&b->ev_in[i], cudaEventDisableTiming)))
+            return bail(pm::cuda_fail(e, "ptycho_batch_create: streams"));
+    }
+    b->cls_st.assign(b->cls.size(), nullptr);
+    b->ev_cls.assign(b->cls.size(), nullptr);
+    for (size_t c = 0; c < b->cls.size(); ++c)
+        if ((e = cudaStreamCreateWithFlags(&b->cls_st[c], cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&b->ev_cls[c], cudaEventDisableTiming)))
+            return bail(pm::cuda_fail(e, "ptycho_batch_create: streams"));
+    if ((e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming)))
+        return bail(pm::cuda_fail(e, "ptycho_batch_create: events"));
+    // order after the handles' own pending work
+    for (int i = 0; i < n; ++i) {
+        if ((e = cudaEventRecord(b->ev_in[i], b->hs[i]->st)) || (e = cudaStreamWaitEvent(b->st, b->ev_in[i], 0)))
+            return bail(pm::cuda_fail(e, "ptycho_batch_create: ordering"));
+    }
+    if (flags & PTYCHO_BATCH_AUTOTUNE) {
+        if ((rc = autotune(b))) return bail(rc);
+    } else {
+        b->describe = "{}";
+    }
+    if ((e = cudaStreamSynchronize(b->st))) return bail(pm::cuda_fail(e, "ptycho_batch_create: synchronise"));
+    if ((e = cudaStreamSynchronize(b->user_st))) return bail(pm::cuda_fail(e, "ptycho_batch_create: synchronise"));
+    *out = b;
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_batch_iterate(ptycho_batch b, int n_iter, double *h_err) {
+    if (!b) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_iterate: NULL batch");
+    if (n_iter < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_iterate: n_iter = %d < 0", n_iter);
+    if (n_iter == 0) return PTYCHO_OK;
+    PM_CUDA(cudaEventRecord(b->ev_user, b->user_st));
+    PM_CUDA(cudaStreamWaitEvent(b->st, b->ev_user, 0));
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        PM_CUDA(cudaEventRecord(b->ev_in[i], b->hs[i]->st));
+        PM_CUDA(cudaStreamWaitEvent(b->st, b->ev_in[i], 0));
+    }
+    int rc = run_iterations(b, n_iter, (b->flags & PTYCHO_BATCH_GRAPH) != 0);
+    if (rc) return rc;
+    PM_CUDA(cudaEventRecord(b->ev_done, b->st));
+    PM_CUDA(cudaStreamWaitEvent(b->user_st, b->ev_done, 0));
+    for (ptycho_ctx *h : b->hs) PM_CUDA(cudaStreamWaitEvent(h->st, b->ev_done, 0));
+    if (h_err) {
+        int status = 0;
+        for (size_t i = 0; i < b->hs.size(); ++i)
+            PM_CUDA(cudaMemcpyAsync(h_err + i, b->hs[i]->d_err, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+        PM_CUDA(cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+        PM_CUDA(cudaStreamSynchronize(b->st));
+        if (status) return pm::fail(PTYCHO_ETIMEDOUT, "ptycho_batch_iterate: a bounded device wait gave up");
+        for (size_t i = 0; i < b->hs.size(); ++i)
+            if (!std::isfinite(h_err[i]))
+                return pm::fail(PTYCHO_ENONFINITE, "ptycho_batch_iterate: error of dataset %zu is not finite", i);
+    }
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_batch_describe(ptycho_batch b, char *buf, int len) {
+    if (!b || !buf || len < 1) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_describe: NULL argument");
+    std::snprintf(buf, (size_t)len, "%s", b->describe.c_str());
+    return PTYCHO_OK;
+}
+
+extern "C" void ptycho_batch_destroy(ptycho_batch b) { free_batch(b); }

@@ -122,3 +122,21 @@ def test_dft2_split_bf16_rejects_bad_arguments(L, B, N, inv):
 
 def test_dft2_split_bf16_empty_batch_is_noop(L):
     assert L.dft2_split_bf16(None, None, 0, 64, 0, None, None) == api.PTYCHO_OK
+
+
+@pytest.mark.parametrize("n,flags", [(0, 0), (-1, 0), (1, 4)])
+def test_batch_create_rejects_bad_arguments(L, n, flags):
+    arr = (ctypes.c_void_p * 1)(None)
+    b = ctypes.c_void_p(1234)
+    assert L.ptycho_batch_create(ctypes.byref(b), arr, n, flags, None) == api.PTYCHO_EINVAL
+    assert b.value is None
+    assert api.last_error().startswith("ptycho_batch_create")
+
+
+def test_batch_create_rejects_null_handle(L):
+    arr = (ctypes.c_void_p * 2)(None, None)
+    b = ctypes.c_void_p()
+    assert L.ptycho_batch_create(ctypes.byref(b), arr, 2, 0, None) == api.PTYCHO_EINVAL
+    assert "handle 0 is NULL" in api.last_error()
+    assert L.ptycho_batch_iterate(None, 1, None) == api.PTYCHO_EINVAL
+    L.ptycho_batch_destroy(None)
