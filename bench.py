@@ -39,10 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["lab", "mixed", "wide64"], default="lab",
+    ap.add_argument("--workload", choices=["lab", "mixed", "wide64", "batched"], default="lab",
                     help="lab: coherent lab-scale scan (the headline); mixed: the same scan with "
                          "8 incoherent probe modes, 100 iterations; wide64: 64^2 probe, 9216 "
-                         "raster positions on a 1024^2 object, 50 iterations")
+                         "raster positions on a 1024^2 object, 50 iterations; batched: 64 uneven "
+                         "datasets (N in {64, 256}, 49-900 positions) in one batch, 50 iterations")
     ap.add_argument("--fft", choices=["radix_fp32", "dftgemm_bf16x3"], default="radix_fp32",
                     help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64)")
     ap.add_argument("--iters", type=int, default=None,
@@ -184,6 +185,178 @@ def profiled_traffic_per_position():
         if line.startswith("traffic_bytes_per_position:"):
             return int(line.split(":")[1])
     return None
+
+
+# ----------------------------------------------------------------------------- batched arm
+def run_batched(args, world, rank, local):
+    """64 uneven datasets advanced together (ptycho_batch_*: multi-dataset exit-wave launches,
+    concurrent per-dataset branches, CUDA graph, autotuned launch shapes).  One step = fusion of
+    every dataset + ptycho_init of every dataset + batch creation + 50 iterations + teardown."""
+    import torch
+    from paper_2608_01746_b300 import api, synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    base = rank_seed(synth.seed_for("batched"), rank)
+    cfgs = synth.batched_configs(seed=base)
+    n_iter = args.iters or cfgs[0].n_iter
+    scans = [synth.make_scan_torch(c, seed=base * 1000 + d, device=dev) for d, c in enumerate(cfgs)]
+    params = [api.fuse_params(levels=c.levels, clip=float(c.clip)) for c in cfgs]
+    fused = [torch.empty((c.n_pos, c.N, c.N), dtype=torch.float32, device=dev) for c in cfgs]
+    obj0 = [torch.ones((c.M, c.M), dtype=torch.complex64, device=dev) for c in cfgs]
+    probe0 = [torch.from_numpy(sc["probe"].astype(np.complex64)).to(dev) for sc in scans]
+    stream = torch.cuda.current_stream(dev)
+    J_all = [c.n_pos for c in cfgs]
+    updates_per_iter = sum(J_all)
+
+    def fft_for(c, fft):
+        return fft if c.N == 64 else "radix_fp32"
+
+    def make_handles(fft, raws=None):
+        for d, c in enumerate(cfgs):
+            api.fuse_stack(scans[d]["raw"] if raws is None else raws[d], c.times, params[d], out=fused[d],
+                           stream=stream)
+        return [api.ptycho_init(fused[d], scans[d]["pos"], obj0[d], probe0[d], stream=stream,
+                                fft_path=fft_for(c, fft)) for d, c in enumerate(cfgs)]
+
+    def step(fft=args.fft, raws=None):
+        hs = make_handles(fft, raws)
+        b = api.ptycho_batch_create(hs, graph=True, autotune=True, stream=stream)
+        api.ptycho_batch_iterate(b, n_iter, errors=False)
+        api.ptycho_batch_destroy(b)
+        return hs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        for h in step():
+            api.ptycho_destroy(h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        for h in step():
+            api.ptycho_destroy(h)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(t0.elapsed_time(t1), dist, dev)
+    updates = updates_per_iter * n_iter * args.steps * world
+    value = updates / (ms_total / 1e3)
+
+    # iterations only, per form: serial handles, plain batch, graph + autotune, other FFT form
+    def iter_ms(mode, fft):
+        hs = make_handles(fft)
+        b = None
+        if mode != "serial":
+            b = api.ptycho_batch_create(hs, graph=mode == "tuned", autotune=mode == "tuned", stream=stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if b is None:
+            for h in hs:
+                api.ptycho_iterate(h, n_iter, errors=False)
+            # each handle works on its own stream, ordered after `stream` only through init
+            torch.cuda.synchronize(dev)
+            e1.record(stream)
+        else:
+            api.ptycho_batch_iterate(b, n_iter, errors=False)
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        desc = api.ptycho_batch_describe(b) if b is not None else None
+        if b is not None:
+            api.ptycho_batch_destroy(b)
+        for h in hs:
+            api.ptycho_destroy(h)
+        return e0.elapsed_time(e1), desc
+
+    variants = None
+    if rank == 0:
+        other = "dftgemm_bf16x3" if args.fft == "radix_fp32" else "radix_fp32"
+        variants = {}
+        for name, mode, fft in [("serial_handles", "serial", args.fft), ("batch_plain", "plain", args.fft),
+                                ("batch_graph_autotuned", "tuned", args.fft),
+                                (f"batch_graph_autotuned_{other}", "tuned", other)]:
+            ms, desc = iter_ms(mode, fft)
+            variants[name] = {"ms_per_iteration": round(ms / n_iter, 4),
+                              "position_updates_per_s": round(updates_per_iter * n_iter / (ms / 1e3), 1)}
+            if desc:
+                variants[name]["autotune"] = json.loads(desc)
+
+    e2e = None
+    if not args.no_e2e:
+        raws_h = [sc["raw"].cpu().pin_memory() for sc in scans]
+        raws_d = [torch.empty_like(sc["raw"]) for sc in scans]
+        outs = [np.empty((c.M, c.M), np.complex64) for c in cfgs]
+
+        def e2e_step():
+            for d in range(len(cfgs)):
+                raws_d[d].copy_(raws_h[d], non_blocking=True)
+            hs = step(raws=raws_d)
+            for d, h in enumerate(hs):
+                api.ptycho_get_object(h, outs[d])
+                api.ptycho_destroy(h)
+
+        e2e_step()
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - w0, dist, dev)
+        e2e = {"value": round(updates / e2e_s, 1), "unit": METRIC,
+               "h2d_bytes_per_step": int(sum(r.numel() * 2 for r in raws_h) + sum(sc["pos"].nbytes for sc in scans)
+                                         + sum(o.nbytes for o in outs) + sum(p.numel() * 8 for p in probe0)),
+               "d2h_bytes_per_step": int(sum(o.nbytes for o in outs))}
+
+    # whole-iteration ALU roofline (every kernel of the batched iteration together): the exit-wave
+    # FFT flops of every position against the FP32 lanes at the maximum clock
+    it_ms = variants["batch_graph_autotuned"]["ms_per_iteration"] if variants else ms_total / args.steps / n_iter
+    flops = sum(exit_wave_flops_per_position(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e12
+    alu_peak = fp32_peak_tflops(2032.0)
+    hbm_peak, peak_kind = peaks()
+    hbm = sum(exit_wave_bytes_per_position(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e9
+    roof = {"kernel": "whole batched iteration (all kernels; per-kernel events are not available inside the graph)",
+            "bound": "alu", "achieved": round(flops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+            "frac": round(flops / alu_peak, 4), "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
+            "traffic": None, "avg_iteration_ms": round(it_ms, 4),
+            "hbm_view": {"achieved_gbs": round(hbm, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                         "frac": round(hbm / hbm_peak, 4)}}
+    n64 = sum(1 for c in cfgs if c.N == 64)
+    launches_per_iter = (1 + sum(1 for c in cfgs if c.N == 256)  # one multi-dataset exit launch + N=256 exits
+                         + 2 * len(cfgs) + 3 * len(cfgs) + len(cfgs))   # object (2), probe (3), error (1)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate for N = 64, f32 for N = 256",
+        "data": "synthetic (seeded jittered raster scans, Poisson counts, 12-bit clip)",
+        "config": {"workload": (f"batched: 64 uneven datasets ({n64} with 64^2 probes, {len(cfgs) - n64} with 256^2), "
+                                f"{updates_per_iter} positions in all, objects {min(c.M for c in cfgs)}-"
+                                f"{max(c.M for c in cfgs)} px, 3 exposures, 4-level pyramid, {n_iter} iterations "
+                                "per step, one batch (CUDA graph, autotuned)"),
+                   "fft": args.fft, "datasets": len(cfgs), "positions": updates_per_iter,
+                   "iterations": n_iter,
+                   "l2": f"inputs larger than L2 (raw stacks {sum(sc['raw'].numel() for sc in scans) * 2 / 1e9:.2f} GB per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "variants_iterations_only": variants,
+        "roofline": roof, "clocks": clk,
+        "gpu_launches": int(args.steps * (len(cfgs) * (2 * cfgs[0].levels - 1 + 2) + n_iter * launches_per_iter)),
+        "e2e": e2e, "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -503,6 +676,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1663,6 +1665,17 @@ double time_iterations(ptycho_batch_ctx *b, int n, int *rc) {
     return ms;
 }
 
+// Autotuner results by problem shape (class kind + dataset sizes), kept for the process: a
+// later batch of the same shapes reuses the choice without timing again.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+std::string class_key(const ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c) {
+    std::string k = "k" + std::to_string(c.kind) + ":";
+    for (int m : c.members) k += std::to_string(b->hs[m]->J) + "/" + std::to_string(b->hs[m]->M) + ",";
+    return k;
+}
+
 // Coordinate search over the launch shapes, on the batch's own data; object, probe and
 // iteration counters are restored afterwards.
 int autotune(ptycho_batch_ctx *b) {
@@ -1670,7 +1683,20 @@ int autotune(ptycho_batch_ctx *b) {
     std::vector<float2 *> so(b->hs.size()), sp(b->hs.size());
     std::vector<long long> sit(b->hs.size());
     int rc = PTYCHO_OK;
-    for (size_t i = 0; i < b->hs.size() && !rc; ++i) {
+    bool need = false;                     // anything not in the cache?  (else no snapshot)
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &c : b->cls) need = need || !g_tune_cache.count(class_key(b, c));
+        std::string bkey = "tma:";
+        bool any = false;
+        for (ptycho_ctx *h : b->hs)
+            if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP) {
+                bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
+                any = true;
+            }
+        need = need || (any && !g_tune_cache.count(bkey));
+    }
+    for (size_t i = 0; i < b->hs.size() && !rc && need; ++i) {
         ptycho_ctx *h = b->hs[i];
         rc = dalloc(&so[i], (size_t)h->M * h->M);
         if (!rc) rc = dalloc(&sp[i], (size_t)h->Q * h->N * h->N);
@@ -1683,9 +1709,24 @@ int autotune(ptycho_batch_ctx *b) {
     }
     std::string rep = "{";
     char buf[256];
+    int cached = 0;
     // grids of the multi-dataset classes
     for (size_t c = 0; c < b->cls.size() && !rc; ++c) {
         auto &k = b->cls[c];
+        const std::string key = class_key(b, k);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                k.grid = it->second;
+                ++cached;
+                std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d",
+                              rep.size() > 1 ? ", " : "", k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"),
+                              k.grid);
+                rep += buf;
+                continue;
+            }
+        }
         std::vector<int> cand;
         for (int m : {1, 2, 3, 4, 6, 8}) {
             const int g = std::min(k.units, std::min(k.grid_max, m * b->sms));
@@ -1705,6 +1746,10 @@ int autotune(ptycho_batch_ctx *b) {
             if (ms < best_ms) { best_ms = ms; best = g; }
         }
         k.grid = best;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
         std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d, \"class_%s_tried_ms\": \"%s\"",
                       rep.size() > 1 ? ", " : "", k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"),
                       best, k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"), tried.c_str());
@@ -1714,7 +1759,21 @@ int autotune(ptycho_batch_ctx *b) {
     std::vector<ptycho_ctx *> big;
     for (ptycho_ctx *h : b->hs)
         if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP) big.push_back(h);
-    if (!big.empty() && !rc) {
+    std::string bkey = "tma:";
+    for (ptycho_ctx *h : big) bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
+    int bcached = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(bkey);
+        if (it != g_tune_cache.end()) bcached = it->second;
+    }
+    if (!big.empty() && !rc && bcached) {
+        for (ptycho_ctx *h : big)
+            if (!rc && h->tma_batch != bcached) rc = retune_tma(h, bcached);
+        ++cached;
+        std::snprintf(buf, sizeof buf, "%s\"tma_rows_n256\": %d", rep.size() > 1 ? ", " : "", bcached);
+        rep += buf;
+    } else if (!big.empty() && !rc) {
         int best = 16;
         double best_ms = 1e30;
         std::string tried;
@@ -1730,6 +1789,10 @@ int autotune(ptycho_batch_ctx *b) {
         }
         for (ptycho_ctx *h : big)
             if (!rc) rc = retune_tma(h, best);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[bkey] = best;
+        }
         std::snprintf(buf, sizeof buf, "%s\"tma_rows_n256\": %d, \"tma_rows_tried_ms\": \"%s\"",
                       rep.size() > 1 ? ", " : "", best, tried.c_str());
         rep += buf;
@@ -1740,14 +1803,15 @@ int autotune(ptycho_batch_ctx *b) {
         if (sp[i])
             cudaMemcpyAsync(h->d_probe, sp[i], (size_t)h->Q * h->N * h->N * sizeof(float2), cudaMemcpyDeviceToDevice,
                             b->st);
-        h->iter = sit[i];
+        if (need) h->iter = sit[i];
     }
     cudaStreamSynchronize(b->st);
     for (size_t i = 0; i < b->hs.size(); ++i) {
         if (so[i]) cudaFree(so[i]);
         if (sp[i]) cudaFree(sp[i]);
     }
-    b->describe = rep + "}";
+    std::snprintf(buf, sizeof buf, "%s\"from_cache\": %d", rep.size() > 1 ? ", " : "", cached);
+    b->describe = rep + buf + "}";
     return rc;
 }
 

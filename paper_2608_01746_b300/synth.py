@@ -23,7 +23,8 @@ import math
 import numpy as np
 
 __all__ = ["ScanConfig", "CONFIGS", "make_object", "make_probe", "make_probe_modes",
-           "raster_positions", "spiral_positions", "make_scan", "make_scan_torch", "seed_for"]
+           "raster_positions", "spiral_positions", "make_scan", "make_scan_torch", "seed_for",
+           "batched_configs"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -84,6 +85,27 @@ CONFIGS = {
     "mid": ScanConfig("mid", M=160, N=64, scan="raster", radius=20.0, times=(1.0, 10.0, 100.0),
                       peak=1e4, clip=4095, levels=4, n_iter=20, n_side=5, step=16, jitter=1),
 }
+
+
+def batched_configs(seed: int | None = None, count: int = 64) -> list:
+    """The uneven multi-dataset workload: ``count`` scans built like the small scan (exposures
+    1/10/100, 1e4 peak counts, 12-bit clip, 4 pyramid levels, 50 iterations), each with its own
+    probe side N drawn from {64, 256} (aperture radius 5N/16), an n x n raster with n drawn from
+    [7, 30] (capped so the scan fits a 1024-pixel object; step N/8, +-1 px jitter) and the
+    smallest object side M in [256, 1024], a multiple of 32, that holds it."""
+    rng = np.random.default_rng(seed_for("batched") if seed is None else seed)
+    out = []
+    for d in range(count):
+        N = int(rng.choice([64, 256]))
+        step = N // 8
+        n_max = min(30, (1024 - N - 2) // step + 1)
+        n = int(rng.integers(7, n_max + 1))
+        span = N + (n - 1) * step + 2
+        M = max(256, -(-span // 32) * 32)
+        out.append(ScanConfig(f"batched{d}", M=M, N=N, scan="raster", radius=5.0 * N / 16.0,
+                              times=(1.0, 10.0, 100.0), peak=1e4, clip=4095, levels=4, n_iter=50,
+                              n_side=n, step=step, jitter=1))
+    return out
 
 
 def seed_for(name: str) -> int:
