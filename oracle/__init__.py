@@ -1,5 +1,6 @@
 """FP64 CPU oracle for the paper's hot path: Multi-Scale Non-Linear Fusion (§3.4) and the
-iterative ptychographic reconstruction that consumes the fused patterns (§3.3).
+iterative ptychographic reconstruction that consumes the fused patterns (§3.3), plus the learned
+warm start's network, gradients, optimiser and patch stitching (``oracle.cnn``).
 
 TEST INFRASTRUCTURE ONLY.  This package is the slow, plain, obviously-correct statement of what
 the CUDA library computes.  Only the test suite, the smoke check and the benchmark's CPU-baseline
@@ -18,6 +19,7 @@ from .ptycho import fft2u, ifft2u, amplitudes, modulus_projection, reconstruct, 
     iterate_once, exit_wave_update, object_update, probe_update, illumination, nrmse, \
     fourier_error, modes_modulus_projection, iterate_once_modes, reconstruct_modes, \
     greedy_colouring, epie_by_colour
+from . import cnn
 
 __all__ = [
     "FuseParams", "sli_position", "sli_stack", "exposure_weights", "radiance", "blur_down", "upsample", "gaussian_pyramid",
@@ -25,5 +27,5 @@ __all__ = [
     "amplitudes", "modulus_projection", "reconstruct", "iterate_once", "exit_wave_update",
     "object_update", "probe_update",
     "illumination", "nrmse", "fourier_error", "modes_modulus_projection", "iterate_once_modes",
-    "reconstruct_modes", "greedy_colouring", "epie_by_colour",
+    "reconstruct_modes", "greedy_colouring", "epie_by_colour", "cnn",
 ]

@@ -1,0 +1,164 @@
+// Generic BF16 GEMM on the fifth-generation tensor cores: C[M][N] (FP32, row-major) =
+// A[M][K] B[N][K]^T with A and B BF16 row-major (K contiguous).  The convolution layers of the
+// warm-start network (forward, data gradient, weight gradient) are all of this form after
+// im2col.  M % 128 == 0, N % 64 == 0, K % 64 == 0 (callers pad with zeros).
+//
+// One CTA per 128 x 64 tile of C, 128 threads (thread r owns row r of the tile = TMEM lane r).
+// K is consumed in chunks of 64 through two shared-memory stages in the no-swizzle core-matrix
+// layout: while the tensor core multiplies one chunk, the threads load the next.  Every wait is
+// bounded; a timeout sets *status.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "gemm.h"
+#include "tcgen05.cuh"
+#include "tma.cuh"
+
+namespace {
+
+using namespace pm;
+
+constexpr int kBM = 128, kBN = 64, kBK = 64;
+constexpr int kThreads = 128;
+constexpr uint32_t kABytes = kBM * kBK * 2;     // 16 KB
+constexpr uint32_t kBBytes = kBN * kBK * 2;     // 8 KB
+constexpr uint32_t kStage = kABytes + kBBytes;
+constexpr uint32_t kSmem = 2 * kStage + 1024;
+constexpr uint32_t kLBO = 128, kSBO = (kBK / 8) * 128;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_bf16(const uint4 *__restrict__ A, const uint4 *__restrict__ B, float *__restrict__ C, int M, int N, int K,
+                int *status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+    if (warp == 0) tc::alloc(&tmem_slot, 64);
+    if (tid == 0) {
+        tma::mbar_init(&bar[0], 1);
+        tma::mbar_init(&bar[1], 1);
+        tma::fence_barrier_init();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int kchunks = K / kBK;
+    const int k16 = K / 8;                       // uint4 per row
+    uint32_t phase[2] = {0, 0};
+    bool ok = true;
+    for (int kc = 0; kc < kchunks && ok; ++kc) {
+        const int s = kc & 1;
+        uint8_t *sa = sm + s * kStage, *sb = sa + kABytes;
+        if (kc >= 2) {                           // the MMAs that read this stage are done?
+            bool w = true;
+            if (warp == 0) w = tma::mbar_wait(&bar[s], phase[s]);
+            ok = __syncthreads_and(w) != 0;
+            if (!ok) break;
+            phase[s] ^= 1;
+            tc::fence_after();
+        }
+        // A rows: thread tid loads row m0 + tid, chunk columns [kc * 64, kc * 64 + 64)
+        const uint4 *arow = A + (size_t)(m0 + tid) * k16 + kc * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint4 v = __ldg(arow + q);
+            *reinterpret_cast<uint4 *>(sa + ((tid >> 3) * 8 + q) * 128 + (tid & 7) * 16) = v;
+        }
+        // B rows: 64 rows x 8 uint4, two rows per thread pair
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + q * kThreads;  // 0 .. 511
+            const int r = idx >> 3, c = idx & 7;
+            const uint4 v = __ldg(B + (size_t)(n0 + r) * k16 + kc * 8 + c);
+            *reinterpret_cast<uint4 *>(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = v;
+        }
+        tma::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
+            const uint32_t a0 = tc::smem_addr(sa), b0 = tc::smem_addr(sb);
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks)
+                tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 256, kLBO, kSBO), tc::smem_desc(b0 + ks * 256, kLBO, kSBO),
+                             idesc, (uint32_t)((kc | ks) != 0));
+            tc::commit(&bar[s]);
+        }
+    }
+    if (ok && kchunks > 0) {
+        // the last commit covers every MMA issued before it
+        const int s = (kchunks - 1) & 1;
+        bool w = true;
+        if (warp == 0) w = tma::mbar_wait(&bar[s], phase[s]);
+        ok = __syncthreads_and(w) != 0;
+        tc::fence_after();
+    }
+    if (ok) {
+        float *crow = C + (size_t)(m0 + tid) * N + n0;
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int ch = 0; ch < kBN / 32; ++ch) {
+            uint32_t v[32];
+            tc::ld_32cols(lane_addr + ch * 32, v);
+            tc::wait_ld();
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                reinterpret_cast<float4 *>(crow + ch * 32)[q] =
+                    make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                                __uint_as_float(v[4 * q + 3]));
+        }
+    } else {
+        if (tid == 0) atomicExch(status, 1);
+        // let MMAs still in flight finish before the columns are released (bounded)
+        if (warp == 0) {
+            tma::mbar_wait(&bar[0], phase[0]);
+            tma::mbar_wait(&bar[1], phase[1]);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tmem, 64);
+    }
+}
+
+bool g_attr_set[64] = {};
+
+}  // namespace
+
+namespace pm {
+
+int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K, int *d_status, cudaStream_t st) {
+    if (M % kBM || N % kBN || K % kBK || M < 0 || N < 0 || K < 0)
+        return fail(PTYCHO_EINVAL, "gemm_bf16: M %% 128, N %% 64, K %% 64 must be 0 (M=%d N=%d K=%d)", M, N, K);
+    if (M == 0 || N == 0) return PTYCHO_OK;
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !g_attr_set[dev]) {
+        PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+        g_attr_set[dev] = true;
+    }
+    if (K == 0) {
+        PM_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
+        return PTYCHO_OK;
+    }
+    dim3 grid(M / kBM, N / kBN);
+    k_gemm_bf16<<<grid, kThreads, kSmem, st>>>(static_cast<const uint4 *>(A), static_cast<const uint4 *>(B), C, M, N,
+                                                K, d_status);
+    PM_LAUNCHED("k_gemm_bf16");
+    return PTYCHO_OK;
+}
+
+}  // namespace pm
+
+extern "C" int gemm_bf16(const void *d_A, const void *d_B, float *d_C, int M, int N, int K, int *d_status,
+                         void *cuda_stream) {
+    if ((M > 0 && N > 0 && K > 0) && (!d_A || !d_B || !d_C || !d_status))
+        return pm::fail(PTYCHO_EINVAL, "gemm_bf16: NULL pointer");
+    return pm::gemm_bf16_launch(d_A, d_B, d_C, M, N, K, d_status, static_cast<cudaStream_t>(cuda_stream));
+}

@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = ["ScanConfig", "CONFIGS", "make_object", "make_probe", "make_probe_modes",
            "raster_positions", "spiral_positions", "make_scan", "make_scan_torch", "seed_for",
-           "batched_configs"]
+           "batched_configs", "WARM_NET"]
 
 
 @dataclasses.dataclass(frozen=True)
@@ -85,6 +85,15 @@ CONFIGS = {
     "mid": ScanConfig("mid", M=160, N=64, scan="raster", radius=20.0, times=(1.0, 10.0, 100.0),
                       peak=1e4, clip=4095, levels=4, n_iter=20, n_side=5, step=16, jitter=1),
 }
+
+
+# The warm-start network of the learned-initialisation workload: 8 convolution layers (3 x 3
+# kernels) as (input channels, output channels, mode), mode "s1" stride 1, "s2" stride 2, "up"
+# nearest 2x up-sampling then stride 1; ReLU after every layer but the last.  Input: the fused
+# pattern binned to (N/2)^2, one channel; output: the (N/4)^2 coarse object patch, two channels
+# (real, imaginary).  1.35 M weights.
+WARM_NET = ((1, 32, "s1"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (256, 256, "s1"),
+            (256, 128, "up"), (128, 64, "up"), (64, 2, "s1"))
 
 
 def batched_configs(seed: int | None = None, count: int = 64) -> list:
