@@ -14,6 +14,12 @@ reconstruction of §3.3).  Plain numpy in float64, written from the definitions:
   Adam         m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
                w -= lr (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps)   (step k = 1, 2, ...)
 
+Storage precision: the workload fixes BF16 storage for the network (weights, activations), so
+``network_forward`` / ``network_backward`` take an optional ``store`` function applied where the
+stored form is what later arithmetic reads: every activation after its ReLU, and every dL/dz
+that enters a contraction (the weight and input gradients; the bias gradient sums dL/dz as
+computed).  ``store=None`` is exact FP64 throughout.
+
 Readings (the workload names the network, not its data transforms):
   * input   x = log(1 + 2x2-binned fused intensity, clipped at 0) / 10, the DC-centred pattern as
             fused (N x N -> N/2 x N/2)
@@ -86,7 +92,7 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def network_forward(layers, params, x):
+def network_forward(layers, params, x, store=None):
     """layers: [(cin, cout, mode)]; params: [(w, b)].  Returns the output and the per-layer inputs
     and pre-activations needed by the backward pass."""
     acts, pre = [np.asarray(x, np.float64)], []
@@ -94,7 +100,12 @@ def network_forward(layers, params, x):
     for i, ((cin, cout, mode), (w, b)) in enumerate(zip(layers, params)):
         z = conv_forward(h, w, b, mode)
         pre.append(z)
-        h = z if i == len(layers) - 1 else relu(z)
+        if i == len(layers) - 1:
+            h = z
+        else:
+            h = relu(z)
+            if store is not None:
+                h = store(h)
         acts.append(h)
     return h, acts, pre
 
@@ -105,14 +116,16 @@ def mse(y, t):
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
-def network_backward(layers, params, acts, pre, dout):
+def network_backward(layers, params, acts, pre, dout, store=None):
     """Parameter gradients [(dw, db)] and the input gradient, by the chain rule layer by layer."""
     grads = [None] * len(layers)
     g = dout
     for i in range(len(layers) - 1, -1, -1):
         if i != len(layers) - 1:
             g = g * (pre[i] > 0.0)
-        dx, dw, db = conv_backward(acts[i], params[i][0], g, layers[i][2])
+        db = g.sum(axis=(0, 2, 3))
+        gs = g if store is None else store(g)
+        dx, dw, _ = conv_backward(acts[i], params[i][0], gs, layers[i][2])
         grads[i] = (dw, db)
         g = dx
     return grads, g

@@ -83,6 +83,31 @@ def lib() -> ctypes.CDLL:
     L.ptycho_batch_describe.argtypes = [vp, ctypes.c_char_p, ci]
     L.ptycho_batch_destroy.restype = None
     L.ptycho_batch_destroy.argtypes = [vp]
+    L.gemm_bf16.restype = ci
+    L.gemm_bf16.argtypes = [vp, vp, vp, ci, ci, ci, vp, vp]
+    ip = ctypes.POINTER(ci)
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.wsnet_create.restype = ci
+    L.wsnet_create.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ci, ci, ci, ctypes.c_ulonglong, vp]
+    for name in ("wsnet_set_params", "wsnet_get_params", "wsnet_get_grads"):
+        getattr(L, name).restype = ci
+        getattr(L, name).argtypes = [vp, ci, fp, fp]
+    L.wsnet_forward.restype = ci
+    L.wsnet_forward.argtypes = [vp, vp, ci, vp]
+    L.wsnet_backward.restype = ci
+    L.wsnet_backward.argtypes = [vp, vp, vp, ci, ctypes.POINTER(cd)]
+    L.wsnet_adam.restype = ci
+    L.wsnet_adam.argtypes = [vp, ctypes.c_float]
+    L.wsnet_train_step.restype = ci
+    L.wsnet_train_step.argtypes = [vp, vp, vp, ci, ctypes.c_float, ctypes.POINTER(cd)]
+    L.wsnet_destroy.restype = None
+    L.wsnet_destroy.argtypes = [vp]
+    L.ws_preprocess.restype = ci
+    L.ws_preprocess.argtypes = [vp, ci, ci, vp, vp]
+    L.ws_targets.restype = ci
+    L.ws_targets.argtypes = [vp, ci, vp, ci, ci, vp, vp]
+    L.ws_stitch.restype = ci
+    L.ws_stitch.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp]
     L.dft2_split_bf16.restype = ci
     L.dft2_split_bf16.argtypes = [vp, vp, ci, ci, ci, vp, vp]
     L.fuse_sli.restype = ci
@@ -361,3 +386,152 @@ def ptycho_batch_describe(b: PtychoBatch) -> str:
 
 def ptycho_batch_destroy(b: PtychoBatch) -> None:
     b.close()
+
+
+# ----------------------------------------------------------------------------- warm start
+WS_MODES = {"s1": 0, "s2": 1, "up": 2}
+
+
+def gemm_bf16(A, B, status=None, stream=None):
+    """C = A B^T on the tensor cores; A [M][K], B [N][K] bfloat16 CUDA tensors -> float32 [M][N]."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().gemm_bf16(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                           M, N, K, ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return C
+
+
+class WsNet:
+    """Owner of a ``wsnet`` (the warm-start network)."""
+
+    def __init__(self, ptr, layers, in_side, max_batch):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.layers = [tuple(l) for l in layers]
+        self.in_side = in_side
+        self.max_batch = max_batch
+        side = in_side
+        for _, _, m in self.layers:
+            side = side // 2 if m == "s2" else (side * 2 if m == "up" else side)
+        self.out_side = side
+        self.out_channels = self.layers[-1][1]
+
+    def close(self):
+        if self.ptr:
+            lib().wsnet_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wsnet_create(layers, in_side: int, max_batch: int, seed: int = 0, stream=None) -> WsNet:
+    n = len(layers)
+    ci = ctypes.c_int * n
+    cin = ci(*[l[0] for l in layers])
+    cout = ci(*[l[1] for l in layers])
+    mode = ci(*[WS_MODES[l[2]] for l in layers])
+    p = ctypes.c_void_p()
+    _check(lib().wsnet_create(ctypes.byref(p), cin, cout, mode, n, in_side, max_batch, seed,
+                              ctypes.c_void_p(_stream_ptr(stream))))
+    return WsNet(p.value, layers, in_side, max_batch)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def wsnet_set_params(net: WsNet, layer: int, w, b):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    _check(lib().wsnet_set_params(net.ptr, layer, _fptr(w), _fptr(b)))
+
+
+def _get2(fn, net: WsNet, layer: int):
+    cin, cout, _ = net.layers[layer]
+    w = np.empty((cout, cin, 3, 3), np.float32)
+    b = np.empty(cout, np.float32)
+    _check(fn(net.ptr, layer, _fptr(w), _fptr(b)))
+    return w, b
+
+
+def wsnet_get_params(net: WsNet, layer: int):
+    return _get2(lib().wsnet_get_params, net, layer)
+
+
+def wsnet_get_grads(net: WsNet, layer: int):
+    return _get2(lib().wsnet_get_grads, net, layer)
+
+
+def wsnet_forward(net: WsNet, x, out=None):
+    """x: bfloat16 CUDA tensor [B][cin][s][s] -> float32 [B][cout][s'][s']."""
+    import torch
+    B = x.shape[0]
+    if out is None:
+        out = torch.empty((B, net.out_channels, net.out_side, net.out_side), dtype=torch.float32, device=x.device)
+    _check(lib().wsnet_forward(net.ptr, ctypes.c_void_p(x.data_ptr()), B, ctypes.c_void_p(out.data_ptr())))
+    return out
+
+
+def wsnet_backward(net: WsNet, x, t, loss: bool = True):
+    v = ctypes.c_double()
+    _check(lib().wsnet_backward(net.ptr, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                ctypes.byref(v) if loss else None))
+    return v.value if loss else None
+
+
+def wsnet_adam(net: WsNet, lr: float):
+    _check(lib().wsnet_adam(net.ptr, lr))
+
+
+def wsnet_train_step(net: WsNet, x, t, lr: float, loss: bool = False):
+    v = ctypes.c_double()
+    _check(lib().wsnet_train_step(net.ptr, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                  lr, ctypes.byref(v) if loss else None))
+    return v.value if loss else None
+
+
+def wsnet_destroy(net: WsNet):
+    net.close()
+
+
+def ws_preprocess(fused, out=None, stream=None):
+    """float32 CUDA [J][N][N] fused patterns -> bfloat16 [J][1][N/2][N/2] network input."""
+    import torch
+    J, N, _ = fused.shape
+    if out is None:
+        out = torch.empty((J, 1, N // 2, N // 2), dtype=torch.bfloat16, device=fused.device)
+    _check(lib().ws_preprocess(ctypes.c_void_p(fused.data_ptr()), J, N, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def ws_targets(obj, pos, N: int, out=None, stream=None):
+    """obj complex64 CUDA [M][M], pos int32 CUDA [J][2] -> float32 [J][2][N/4][N/4]."""
+    import torch
+    J = pos.shape[0]
+    if out is None:
+        out = torch.empty((J, 2, N // 4, N // 4), dtype=torch.float32, device=obj.device)
+    _check(lib().ws_targets(ctypes.c_void_p(obj.data_ptr()), obj.shape[0], ctypes.c_void_p(pos.data_ptr()), J, N,
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def ws_stitch(pred, pos, probe, M: int, out=None, stream=None):
+    """pred float32 CUDA [J][2][N/4][N/4], pos int32 CUDA [J][2], probe complex64 CUDA [N][N]
+    -> complex64 [M][M] initial object."""
+    import torch
+    J = pred.shape[0]
+    N = probe.shape[0]
+    if out is None:
+        out = torch.empty((M, M), dtype=torch.complex64, device=pred.device)
+    _check(lib().ws_stitch(ctypes.c_void_p(pred.data_ptr()), ctypes.c_void_p(pos.data_ptr()), J,
+                           ctypes.c_void_p(probe.data_ptr()), N, M, ctypes.c_void_p(out.data_ptr()),
+                           ctypes.c_void_p(_stream_ptr(stream))))
+    return out

@@ -1,0 +1,186 @@
+"""Warm-start network kernels (tensor-core GEMM, convolution layers forward / backward, Adam,
+input / target transforms, stitching) against the FP64 oracle, through the C ABI.
+
+Tolerances follow the storage precision.  The oracle is given the same BF16-rounded weights and
+inputs the GPU uses, so what remains is (a) FP32 accumulation order (~1e-6 relative) and (b) the
+BF16 rounding (unit roundoff u = 2^-9) of every activation the GPU stores and of every gradient
+it feeds to a GEMM.  One- and two-layer results pass through r <= 4 such roundings and are held
+to r u.  Through all 8 layers the first-order bound fails (ReLU masks flip where a pre-activation
+is within rounding of zero, and the 4 x 4 bottleneck sums few terms), so the 8-layer test runs
+the oracle with the same BF16 storage points (``store``); then only FP32-vs-FP64 accumulation
+and its occasional one-ulp (2^-8) rounding flips remain, held to 4 u.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+from paper_2608_01746_b300 import synth
+from tests.parity_helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+U = 2.0 ** -9
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_01746_b300 import api as a
+    a.lib()
+    return a
+
+
+def bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def to_dev_bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 128, 192), (384, 192, 1152)])
+def test_gemm_matches_fp64(api, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = bf16(rng.standard_normal((M, K)))
+    B = bf16(rng.standard_normal((N, K)))
+    C = api.gemm_bf16(to_dev_bf16(A), to_dev_bf16(B)).cpu().numpy()
+    ref = A @ B.T
+    assert rel_l2(C, ref) <= K * 2.0 ** -24          # FP32 accumulation of K exact products
+
+
+def _one_layer(api, mode, relu_follow=False, second="s1"):
+    layers = [(3, 5, mode)] + ([(5, 4, second)] if relu_follow else [])
+    net = api.wsnet_create(layers, in_side=8, max_batch=4, seed=1)
+    rng = np.random.default_rng(7)
+    params = [(bf16(0.4 * rng.standard_normal((o, c, 3, 3))), 0.1 * rng.standard_normal(o)) for c, o, _ in layers]
+    for i, (w, b) in enumerate(params):
+        api.wsnet_set_params(net, i, w, b.astype(np.float32))
+    params = [(w, b.astype(np.float32).astype(np.float64)) for w, b in params]
+    x = bf16(rng.standard_normal((2, 3, 8, 8)))
+    return net, layers, params, x
+
+
+@pytest.mark.parametrize("mode", ["s1", "s2", "up"])
+def test_one_layer_forward_and_gradients(api, mode):
+    net, layers, params, x = _one_layer(api, mode)
+    y = api.wsnet_forward(net, to_dev_bf16(x)).cpu().numpy()
+    ry, acts, pre = cnn.network_forward(layers, params, x)
+    assert rel_l2(y, ry) <= 1e-6                     # last layer: FP32 output, no rounding
+    t = np.random.default_rng(3).standard_normal(ry.shape)
+    loss = api.wsnet_backward(net, to_dev_bf16(x), torch.from_numpy(t.astype(np.float32)).cuda())
+    rl, dout = cnn.mse(ry, t.astype(np.float32))
+    grads, _ = cnn.network_backward(layers, params, acts, pre, dout)
+    assert loss == pytest.approx(rl, rel=1e-5)
+    dw, db = api.wsnet_get_grads(net, 0)
+    assert rel_l2(dw, grads[0][0]) <= U               # dZ rounded to BF16 once
+    assert rel_l2(db, grads[0][1]) <= 1e-5            # bias gradient from the FP32 dZ
+    api.wsnet_destroy(net)
+
+
+@pytest.mark.parametrize("mode,second", [(m, s) for m in ("s1", "s2", "up") for s in ("s1", "s2", "up")])
+def test_two_layers_input_gradient_path(api, mode, second):
+    """The data gradient (GEMM + col2im) of layer 1 reaches layer 0's weight gradient."""
+    net, layers, params, x = _one_layer(api, mode, relu_follow=True, second=second)
+    ry, acts, pre = cnn.network_forward(layers, params, x)
+    y = api.wsnet_forward(net, to_dev_bf16(x)).cpu().numpy()
+    assert rel_l2(y, ry) <= 2 * U
+    t = np.random.default_rng(4).standard_normal(ry.shape).astype(np.float32)
+    api.wsnet_backward(net, to_dev_bf16(x), torch.from_numpy(t).cuda())
+    _, dout = cnn.mse(ry, t)
+    grads, _ = cnn.network_backward(layers, params, acts, pre, dout)
+    for i in range(2):
+        dw, db = api.wsnet_get_grads(net, i)
+        assert rel_l2(dw, grads[i][0]) <= 4 * U, i
+        assert rel_l2(db, grads[i][1]) <= 4 * U, i
+    api.wsnet_destroy(net)
+
+
+def test_warm_network_matches_oracle(api):
+    """The 8-layer warm-start network (32 x 32 input, batch 2): output and every gradient."""
+    layers = list(synth.WARM_NET)
+    net = api.wsnet_create(layers, in_side=32, max_batch=2, seed=5)
+    params = []
+    for i in range(len(layers)):
+        w, b = api.wsnet_get_params(net, i)
+        b = np.random.default_rng(i).uniform(-0.05, 0.05, b.shape).astype(np.float32)
+        api.wsnet_set_params(net, i, w, b)
+        params.append((bf16(w), b.astype(np.float64)))
+    x = bf16(np.abs(np.random.default_rng(11).standard_normal((2, 1, 32, 32))))
+    y = api.wsnet_forward(net, to_dev_bf16(x)).cpu().numpy()
+    exact, _, _ = cnn.network_forward(layers, params, x)
+    print(f"8-layer output vs exact FP64: rel L2 {rel_l2(y, exact):.2e} (first-order bound {8 * U:.2e})")
+    assert rel_l2(y, exact) <= 8 * U
+    ry, acts, pre = cnn.network_forward(layers, params, x, store=bf16)
+    assert rel_l2(y, ry) <= 4 * U
+    t = np.random.default_rng(12).standard_normal(ry.shape).astype(np.float32)
+    loss = api.wsnet_backward(net, to_dev_bf16(x), torch.from_numpy(t).cuda())
+    rl, dout = cnn.mse(ry, t)
+    assert loss == pytest.approx(rl, rel=8 * U)
+    grads, _ = cnn.network_backward(layers, params, acts, pre, dout, store=bf16)
+    errs = []
+    for i in range(len(layers)):
+        dw, db = api.wsnet_get_grads(net, i)
+        errs.append((rel_l2(dw, grads[i][0]), rel_l2(db, grads[i][1])))
+    print("per-layer gradient rel L2 (w, b):", [(f"{a:.1e}", f"{b:.1e}") for a, b in errs])
+    worst = max(max(e) for e in errs)
+    for i, e in enumerate(errs):
+        assert max(e) <= 4 * U, (i, e)
+    print(f"worst gradient rel L2 {worst:.2e} (bound {4 * U:.2e})")
+    api.wsnet_destroy(net)
+
+
+def test_adam_matches_oracle(api):
+    net, layers, params, x = _one_layer(api, "s2")
+    t = torch.from_numpy(np.random.default_rng(5).standard_normal((2, 5, 4, 4)).astype(np.float32)).cuda()
+    w = params[0][0].copy()
+    b = params[0][1].copy()
+    m = [np.zeros_like(w), np.zeros_like(b)]
+    v = [np.zeros_like(w), np.zeros_like(b)]
+    for k in (1, 2):
+        api.wsnet_backward(net, to_dev_bf16(x), t)
+        gw, gb = api.wsnet_get_grads(net, 0)
+        api.wsnet_adam(net, 1e-2)
+        w, m[0], v[0] = cnn.adam_step(w, gw.astype(np.float64), m[0], v[0], k, 1e-2)
+        b, m[1], v[1] = cnn.adam_step(b, gb.astype(np.float64), m[1], v[1], k, 1e-2)
+        nw, nb = api.wsnet_get_params(net, 0)
+        np.testing.assert_allclose(nw, w, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(nb, b, rtol=1e-5, atol=1e-6)
+    api.wsnet_destroy(net)
+
+
+def test_training_reduces_loss(api):
+    layers = list(synth.WARM_NET)
+    net = api.wsnet_create(layers, in_side=32, max_batch=8, seed=2)
+    rng = np.random.default_rng(6)
+    x = to_dev_bf16(np.abs(rng.standard_normal((8, 1, 32, 32))))
+    t = torch.from_numpy(rng.standard_normal((8, 2, 8, 8)).astype(np.float32)).cuda()
+    first = api.wsnet_backward(net, x, t)
+    for _ in range(150):
+        api.wsnet_train_step(net, x, t, 1e-3)
+    last = api.wsnet_backward(net, x, t)
+    print(f"loss {first:.4f} -> {last:.4f}")
+    assert last < 0.5 * first
+    api.wsnet_destroy(net)
+
+
+def test_transforms_and_stitch_match_oracle(api):
+    sc = synth.make_scan("small")
+    cfg = sc["cfg"]
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    fused = oracle.mnf_stack(sc["raw"][:12], sc["times"], p).astype(np.float32)
+    x = api.ws_preprocess(torch.from_numpy(fused).cuda()).float().cpu().numpy()
+    assert rel_l2(x, cnn.preprocess(fused)) <= U
+    pos = sc["pos"].astype(np.int32)
+    pos_d = torch.from_numpy(pos).cuda()
+    obj_d = torch.from_numpy(sc["obj"].astype(np.complex64)).cuda()
+    t = api.ws_targets(obj_d, pos_d, cfg.N).cpu().numpy()
+    assert rel_l2(t, cnn.targets(sc["obj"].astype(np.complex64).astype(np.complex128), pos, cfg.N)) <= 1e-6
+    pred = t + 0.05 * np.random.default_rng(1).standard_normal(t.shape).astype(np.float32)
+    probe = sc["probe"].astype(np.complex64)
+    o = api.ws_stitch(torch.from_numpy(pred).cuda(), pos_d, torch.from_numpy(probe).cuda(), cfg.M).cpu().numpy()
+    ro = cnn.stitch(pred.astype(np.float64), pos, probe.astype(np.complex128), cfg.M)
+    assert rel_l2(o, ro) <= 1e-5
