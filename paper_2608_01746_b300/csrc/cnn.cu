@@ -342,6 +342,8 @@ struct wsnet_ctx {
     cudaStream_t st = nullptr;
     bf16 *col = nullptr;
     float *cbuf = nullptr, *pred = nullptr, *g0 = nullptr, *g1 = nullptr, *dpred = nullptr;
+    float *work = nullptr;                     // split-K partial products of the weight gradients
+    size_t work_floats = 0;
     bf16 *dz = nullptr, *dzt = nullptr;
     double *part = nullptr;
     int *status = nullptr;
@@ -420,7 +422,9 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
         k_im2col<<<nblk((size_t)Pp * l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 1,
                                                             n->col);
         PM_LAUNCHED("k_im2col");
-        if ((rc = pm::gemm_bf16_launch(n->dzt, n->col, n->cbuf, l.Coutp128, l.Kp, Pp, n->status, n->st))) return rc;
+        if ((rc = pm::gemm_bf16_launch(n->dzt, n->col, n->cbuf, l.Coutp128, l.Kp, Pp, n->status, n->st, n->work,
+                                       n->work_floats)))
+            return rc;
         k_copy_wgrad<<<nblk((size_t)l.cout * l.K), kT, 0, n->st>>>(n->cbuf, l.Kp, l.cout, l.K, l.gw);
         PM_LAUNCHED("k_copy_wgrad");
         if (li == 0) break;                      // no gradient for the network input
@@ -500,6 +504,7 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
     auto bail = [&](int r) { free_net(n); return r; };
     int rc;
     size_t max_col = 0, max_c = 0, max_dz = 0, max_act = (size_t)max_batch * cin[0] * in_side * in_side;
+    size_t max_w = 0;
     side = in_side;
     std::mt19937_64 rng(seed);
     for (int i = 0; i < nlayers; ++i) {
@@ -519,6 +524,7 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
         max_col = std::max(max_col, Pp * l.Kp);
         max_c = std::max(std::max(max_c, Pp * (size_t)l.Coutp), std::max(Pp * (size_t)l.Kp, (size_t)l.Coutp128 * l.Kp));
         max_dz = std::max(max_dz, Pp * l.Coutp128);
+        max_w = std::max(max_w, (size_t)l.Coutp128 * l.Kp);
         max_act = std::max(max_act, (size_t)max_batch * l.cout * l.hout * l.hout);
         const size_t nw = (size_t)l.cout * l.K;
         if ((rc = nalloc(n, &l.w, nw)) || (rc = nalloc(n, &l.b, l.cout)) || (rc = nalloc(n, &l.mw, nw)) ||
@@ -547,6 +553,8 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
         (rc = nalloc(n, &n->pred, nout)) || (rc = nalloc(n, &n->dpred, nout)) || (rc = nalloc(n, &n->part, 1024)) ||
         (rc = nalloc(n, &n->status, 1)))
         return bail(rc);
+    n->work_floats = 64 * max_w;
+    if ((rc = nalloc(n, &n->work, n->work_floats))) return bail(rc);
     cudaError_t e;
     if ((e = cudaMemset(n->status, 0, sizeof(int)))) return bail(pm::cuda_fail(e, "wsnet_create: status"));
     *out = n;

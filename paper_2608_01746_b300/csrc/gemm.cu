@@ -9,6 +9,8 @@
 // bounded; a timeout sets *status.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "gemm.h"
 #include "tcgen05.cuh"
@@ -26,9 +28,11 @@ constexpr uint32_t kStage = kABytes + kBBytes;
 constexpr uint32_t kSmem = 2 * kStage + 1024;
 constexpr uint32_t kLBO = 128, kSBO = (kBK / 8) * 128;
 
+// blockIdx.z selects a slice of K (split-K): chunks [z cps, min((z + 1) cps, K / 64)), written to
+// C + z M N (a partial product; the caller sums the slices).
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_bf16(const uint4 *__restrict__ A, const uint4 *__restrict__ B, float *__restrict__ C, int M, int N, int K,
-                int *status) {
+                int cps, int *status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t bar[2];
@@ -45,8 +49,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
-    const int kchunks = K / kBK;
+    const int kc0 = blockIdx.z * cps;
+    const int kchunks = min(K / kBK, kc0 + cps) - kc0;
     const int k16 = K / 8;                       // uint4 per row
+    C += (size_t)blockIdx.z * M * N;
     uint32_t phase[2] = {0, 0};
     bool ok = true;
     for (int kc = 0; kc < kchunks && ok; ++kc) {
@@ -61,7 +67,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::fence_after();
         }
         // A rows: thread tid loads row m0 + tid, chunk columns [kc * 64, kc * 64 + 64)
-        const uint4 *arow = A + (size_t)(m0 + tid) * k16 + kc * 8;
+        const uint4 *arow = A + (size_t)(m0 + tid) * k16 + (kc0 + kc) * 8;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const uint4 v = __ldg(arow + q);
@@ -72,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int q = 0; q < 4; ++q) {
             const int idx = tid + q * kThreads;  // 0 .. 511
             const int r = idx >> 3, c = idx & 7;
-            const uint4 v = __ldg(B + (size_t)(n0 + r) * k16 + kc * 8 + c);
+            const uint4 v = __ldg(B + (size_t)(n0 + r) * k16 + (kc0 + kc) * 8 + c);
             *reinterpret_cast<uint4 *>(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = v;
         }
         tma::fence_async_smem();
@@ -89,7 +95,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::commit(&bar[s]);
         }
     }
-    if (ok && kchunks > 0) {
+    if (kchunks <= 0) {                          // empty slice: a zero partial
+        float *crow = C + (size_t)(m0 + tid) * N + n0;
+        for (int q = 0; q < kBN; ++q) crow[q] = 0.f;
+    } else if (ok) {
         // the last commit covers every MMA issued before it
         const int s = (kchunks - 1) & 1;
         bool w = true;
@@ -97,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __syncthreads_and(w) != 0;
         tc::fence_after();
     }
-    if (ok) {
+    if (ok && kchunks > 0) {
         float *crow = C + (size_t)(m0 + tid) * N + n0;
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
@@ -111,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
                                 __uint_as_float(v[4 * q + 3]));
         }
-    } else {
+    } else if (!ok) {
         if (tid == 0) atomicExch(status, 1);
         // let MMAs still in flight finish before the columns are released (bounded)
         if (warp == 0) {
@@ -127,13 +136,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// C[e] = sum over the slices, in slice order (deterministic).
+__global__ void k_sum_slices(const float *__restrict__ part, int slices, size_t n, float *__restrict__ C) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < slices; ++z) s += part[(size_t)z * n + e];
+        C[e] = s;
+    }
+}
+
 bool g_attr_set[64] = {};
 
 }  // namespace
 
 namespace pm {
 
-int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K, int *d_status, cudaStream_t st) {
+int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K, int *d_status, cudaStream_t st,
+                     float *work, size_t work_floats) {
     if (M % kBM || N % kBN || K % kBK || M < 0 || N < 0 || K < 0)
         return fail(PTYCHO_EINVAL, "gemm_bf16: M %% 128, N %% 64, K %% 64 must be 0 (M=%d N=%d K=%d)", M, N, K);
     if (M == 0 || N == 0) return PTYCHO_OK;
@@ -147,10 +166,24 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
         PM_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
         return PTYCHO_OK;
     }
-    dim3 grid(M / kBM, N / kBN);
-    k_gemm_bf16<<<grid, kThreads, kSmem, st>>>(static_cast<const uint4 *>(A), static_cast<const uint4 *>(B), C, M, N,
-                                                K, d_status);
+    // split K when the output tiles alone cannot fill the GPU (weight gradients: small M x N,
+    // K = every pixel of the batch)
+    const int tiles = (M / kBM) * (N / kBN), kch = K / kBK;
+    int slices = 1;
+    if (work && tiles < 296 && kch >= 8) {
+        slices = std::min(std::min((296 + tiles - 1) / tiles, kch / 4), 64);
+        while (slices > 1 && (size_t)slices * M * N > work_floats) --slices;
+    }
+    const int cps = (kch + slices - 1) / slices;
+    dim3 grid(M / kBM, N / kBN, slices);
+    k_gemm_bf16<<<grid, kThreads, kSmem, st>>>(static_cast<const uint4 *>(A), static_cast<const uint4 *>(B),
+                                                slices > 1 ? work : C, M, N, K, cps, d_status);
     PM_LAUNCHED("k_gemm_bf16");
+    if (slices > 1) {
+        const size_t n = (size_t)M * N;
+        k_sum_slices<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(work, slices, n, C);
+        PM_LAUNCHED("k_sum_slices");
+    }
     return PTYCHO_OK;
 }
 

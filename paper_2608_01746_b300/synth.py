@@ -89,11 +89,13 @@ CONFIGS = {
 
 # The warm-start network of the learned-initialisation workload: 8 convolution layers (3 x 3
 # kernels) as (input channels, output channels, mode), mode "s1" stride 1, "s2" stride 2, "up"
-# nearest 2x up-sampling then stride 1; ReLU after every layer but the last.  Input: the fused
+# nearest 2x up-sampling then stride 1; ReLU after every layer but the last.  Four stride-2
+# layers bring a 128^2 input to an 8^2 bottleneck, so the bottleneck sees most of the pattern
+# (a far-field pattern mixes every object pixel into every detector pixel).  Input: the fused
 # pattern binned to (N/2)^2, one channel; output: the (N/4)^2 coarse object patch, two channels
 # (real, imaginary).  1.35 M weights.
-WARM_NET = ((1, 32, "s1"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (256, 256, "s1"),
-            (256, 128, "up"), (128, 64, "up"), (64, 2, "s1"))
+WARM_NET = ((1, 32, "s2"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (256, 256, "s1"),
+            (256, 128, "up"), (128, 64, "up"), (64, 2, "up"))
 
 
 def batched_configs(seed: int | None = None, count: int = 64) -> list:
