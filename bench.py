@@ -51,6 +51,10 @@ def parse():
                     help="override the iteration count (profiling runs only; not a bench value)")
     ap.add_argument("--positions", type=int, default=None,
                     help="use only the first N scan positions (profiling runs only; not a bench value)")
+    ap.add_argument("--warm-objects", type=int, default=None,
+                    help="warm workload: training objects per scale (profiling runs only)")
+    ap.add_argument("--warm-epochs", type=int, default=None,
+                    help="warm workload: epochs per scale (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nrmse", action="store_true")
@@ -382,7 +386,8 @@ def run_warm(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     layers = list(synth.WARM_NET)
-    scales = [("lab", 16, 8, 64), ("small", 40, 20, 32)]
+    scales = [("lab", args.warm_objects or 16, args.warm_epochs or 8, 64),
+              ("small", args.warm_objects or 40, args.warm_epochs or 20, 32)]
     results = {}
     clocks = ClockSampler(local)
     clocks.start()

@@ -34,55 +34,58 @@ unsigned nblk(size_t n) { return (unsigned)std::min<size_t>((n + kT - 1) / kT, (
 // ---------------------------------------------------------------------------------------------
 // im2col: element (p, k), p = (b, i, j) output pixel, k = c * 9 + u * 3 + v, of the conv input
 // x_in[b][c][s i + u - 1][s j + v - 1] (zero outside; for "up", x_in = nearest up-sampling).
+// Index arithmetic is 32-bit (every buffer holds fewer than 2^31 elements).
 __device__ __forceinline__ float im2col_value(const bf16 *__restrict__ x, int cin, int hin, int mode, int hout,
                                               int P, int K, int p, int k) {
     if (p >= P || k >= K) return 0.f;
-    const int c = k / 9, r = k % 9, u = r / 3, v = r % 3;
-    const int hw = hout * hout;
-    const int b = p / hw, q = p % hw, i = q / hout, j = q % hout;
+    const unsigned c = (unsigned)k / 9u, r = (unsigned)k - 9u * c, u = r / 3u, v = r - 3u * u;
+    const unsigned hw = (unsigned)(hout * hout);
+    const unsigned b = (unsigned)p / hw, q = (unsigned)p - b * hw, i = q / (unsigned)hout, j = q - i * (unsigned)hout;
     int yi, xi;
     if (mode == WS_MODE_S2) {
-        yi = 2 * i + u - 1;
-        xi = 2 * j + v - 1;
+        yi = 2 * (int)i + (int)u - 1;
+        xi = 2 * (int)j + (int)v - 1;
         if (yi < 0 || xi < 0 || yi >= hin || xi >= hin) return 0.f;
     } else if (mode == WS_MODE_UP) {
-        const int yu = i + u - 1, xu = j + v - 1;
+        const int yu = (int)i + (int)u - 1, xu = (int)j + (int)v - 1;
         if (yu < 0 || xu < 0 || yu >= 2 * hin || xu >= 2 * hin) return 0.f;
         yi = yu >> 1;
         xi = xu >> 1;
     } else {
-        yi = i + u - 1;
-        xi = j + v - 1;
+        yi = (int)i + (int)u - 1;
+        xi = (int)j + (int)v - 1;
         if (yi < 0 || xi < 0 || yi >= hin || xi >= hin) return 0.f;
     }
-    return __bfloat162float(x[(((size_t)b * cin + c) * hin + yi) * hin + xi]);
+    return __bfloat162float(x[(((unsigned)b * cin + c) * hin + yi) * hin + xi]);
 }
 
-// Row layout out[p][k] (Pp x Kp, consecutive threads along k) or transposed out[k][p].
+// Row layout out[p][k] (Pp x Kp): blockIdx.x = p, threads along k (64 per block, Kp % 64 == 0).
+// Transposed out[k][p] (Kp x Pp): blockIdx.x = k, threads along p.  The long dimension is on x
+// (grid y is limited to 65535).
 __global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int mode, int hout, int P, int K, int Pp,
                          int Kp, int transposed, bf16 *__restrict__ out) {
-    const size_t n = (size_t)Pp * Kp;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        int p, k;
-        if (transposed) { k = (int)(e / Pp); p = (int)(e % Pp); }
-        else { p = (int)(e / Kp); k = (int)(e % Kp); }
-        out[e] = __float2bfloat16_rn(im2col_value(x, cin, hin, mode, hout, P, K, p, k));
-    }
+    const int outer = blockIdx.x, inner = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ninner = transposed ? Pp : Kp;
+    if (inner >= ninner) return;
+    const int p = transposed ? inner : outer, k = transposed ? outer : inner;
+    out[(size_t)outer * ninner + inner] = __float2bfloat16_rn(im2col_value(x, cin, hin, mode, hout, P, K, p, k));
 }
 
 // col2im (adjoint of im2col) as a gather: dx[b][c][y][x] = sum of dcol[p][k] over the (p, k)
 // whose im2col element reads x[b][c][y][x].
 __global__ void k_col2im(const float *__restrict__ dcol, int Kp, int B, int cin, int hin, int mode, int hout,
                          float *__restrict__ dx) {
-    const size_t n = (size_t)B * cin * hin * hin;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(e % hin), y = (int)((e / hin) % hin);
-        const int c = (int)((e / ((size_t)hin * hin)) % cin), b = (int)(e / ((size_t)hin * hin * cin));
+    const unsigned n = (unsigned)B * cin * hin * hin;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const unsigned hh = (unsigned)hin * hin;
+        const unsigned bc = e / hh, yx = e - bc * hh;
+        const int y = (int)(yx / (unsigned)hin), x = (int)(yx - (unsigned)y * hin);
+        const unsigned b = bc / (unsigned)cin, c = bc - b * cin;
         const size_t pb = (size_t)b * hout * hout;
         float acc = 0.f;
         for (int u = 0; u < 3; ++u)
             for (int v = 0; v < 3; ++v) {
-                const int k = c * 9 + u * 3 + v;
+                const int k = (int)c * 9 + u * 3 + v;
                 if (mode == WS_MODE_S2) {
                     const int ti = y - u + 1, tj = x - v + 1;
                     if (ti < 0 || tj < 0 || (ti & 1) || (tj & 1)) continue;
@@ -387,8 +390,8 @@ int forward(wsnet_ctx *n, const bf16 *x, int B, float *out) {
     for (size_t li = 0; li < n->L.size(); ++li) {
         auto &l = n->L[li];
         const int P = B * l.hout * l.hout, Pp = rup(P, 128);
-        k_im2col<<<nblk((size_t)Pp * l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 0,
-                                                            n->col);
+        k_im2col<<<dim3(Pp, l.Kp / 64), 64, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 0,
+                                                        n->col);
         PM_LAUNCHED("k_im2col");
         if ((rc = pm::gemm_bf16_launch(n->col, l.wb, n->cbuf, Pp, l.Coutp, l.Kp, n->status, n->st))) return rc;
         const bool last = li + 1 == n->L.size();
@@ -419,8 +422,8 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
         k_bias_grad<<<l.cout, kT, 0, n->st>>>(g, l.y, l.relu, B, l.cout, l.hout, l.gb);
         PM_LAUNCHED("k_bias_grad");
         // weight gradient: dW[Coutp128][Kp] = dzt[Coutp128][Pp] . colT[Kp][Pp]^T
-        k_im2col<<<nblk((size_t)Pp * l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 1,
-                                                            n->col);
+        k_im2col<<<dim3(l.Kp, (Pp + kT - 1) / kT), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp,
+                                                                   l.Kp, 1, n->col);
         PM_LAUNCHED("k_im2col");
         if ((rc = pm::gemm_bf16_launch(n->dzt, n->col, n->cbuf, l.Coutp128, l.Kp, Pp, n->status, n->st, n->work,
                                        n->work_floats)))

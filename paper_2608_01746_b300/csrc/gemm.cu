@@ -4,9 +4,9 @@
 // im2col.  M % 128 == 0, N % 64 == 0, K % 64 == 0 (callers pad with zeros).
 //
 // One CTA per 128 x 64 tile of C, 128 threads (thread r owns row r of the tile = TMEM lane r).
-// K is consumed in chunks of 64 through two shared-memory stages in the no-swizzle core-matrix
-// layout: while the tensor core multiplies one chunk, the threads load the next.  Every wait is
-// bounded; a timeout sets *status.
+// K is consumed in chunks of 64 through four shared-memory stages in the no-swizzle core-matrix
+// layout, filled with cp.async three chunks ahead of the tensor core.  Every wait is bounded; a
+// timeout sets *status.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -22,27 +22,54 @@ using namespace pm;
 
 constexpr int kBM = 128, kBN = 64, kBK = 64;
 constexpr int kThreads = 128;
+constexpr int kStages = 4;                      // chunks in flight
 constexpr uint32_t kABytes = kBM * kBK * 2;     // 16 KB
 constexpr uint32_t kBBytes = kBN * kBK * 2;     // 8 KB
 constexpr uint32_t kStage = kABytes + kBBytes;
-constexpr uint32_t kSmem = 2 * kStage + 1024;
+constexpr uint32_t kSmem = kStages * kStage + 1024;
 constexpr uint32_t kLBO = 128, kSBO = (kBK / 8) * 128;
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// This thread's share of chunk kc (A: row m0 + tid, 8 x 16 bytes; B: 4 x 16 bytes) into a stage,
+// in the core-matrix layout.
+__device__ __forceinline__ void load_chunk(const uint4 *__restrict__ A, const uint4 *__restrict__ B, int m0, int n0,
+                                           int k16, int kc, uint8_t *sa, uint8_t *sb) {
+    const int tid = threadIdx.x;
+    const uint4 *arow = A + (size_t)(m0 + tid) * k16 + kc * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cp_async16(sa + ((tid >> 3) * 8 + q) * 128 + (tid & 7) * 16, arow + q);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int idx = tid + q * kThreads;     // 0 .. 511: 64 rows x 8 pieces
+        const int r = idx >> 3, c = idx & 7;
+        cp_async16(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16, B + (size_t)(n0 + r) * k16 + kc * 8 + c);
+    }
+}
+
 // blockIdx.z selects a slice of K (split-K): chunks [z cps, min((z + 1) cps, K / 64)), written to
-// C + z M N (a partial product; the caller sums the slices).
-__global__ void __launch_bounds__(kThreads, 1)
+// C + z M N (a partial product; the caller sums the slices).  Chunks stream through kStages
+// shared-memory stages with cp.async; a stage is refilled once the MMAs that read it have
+// committed (their mbarrier), so loads run kStages - 1 chunks ahead of the tensor core.
+__global__ void __launch_bounds__(kThreads)
     k_gemm_bf16(const uint4 *__restrict__ A, const uint4 *__restrict__ B, float *__restrict__ C, int M, int N, int K,
                 int cps, int *status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t bar[kStages];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
     if (warp == 0) tc::alloc(&tmem_slot, 64);
     if (tid == 0) {
-        tma::mbar_init(&bar[0], 1);
-        tma::mbar_init(&bar[1], 1);
+        for (int q = 0; q < kStages; ++q) tma::mbar_init(&bar[q], 1);
         tma::fence_barrier_init();
     }
     tc::fence_before();
@@ -53,37 +80,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kchunks = min(K / kBK, kc0 + cps) - kc0;
     const int k16 = K / 8;                       // uint4 per row
     C += (size_t)blockIdx.z * M * N;
-    uint32_t phase[2] = {0, 0};
+    uint32_t phase[kStages] = {};
     bool ok = true;
-    for (int kc = 0; kc < kchunks && ok; ++kc) {
-        const int s = kc & 1;
+    // prologue: chunks 0 .. kStages - 2 in flight (one commit group each, possibly empty)
+#pragma unroll
+    for (int q = 0; q < kStages - 1; ++q) {
+        if (q < kchunks) load_chunk(A, B, m0, n0, k16, kc0 + q, sm + q * kStage, sm + q * kStage + kABytes);
+        cp_async_commit();
+    }
+    for (int kc = 0; kc < kchunks; ++kc) {
+        const int s = kc % kStages;
         uint8_t *sa = sm + s * kStage, *sb = sa + kABytes;
-        if (kc >= 2) {                           // the MMAs that read this stage are done?
-            bool w = true;
-            if (warp == 0) w = tma::mbar_wait(&bar[s], phase[s]);
-            ok = __syncthreads_and(w) != 0;
-            if (!ok) break;
-            phase[s] ^= 1;
-            tc::fence_after();
-        }
-        // A rows: thread tid loads row m0 + tid, chunk columns [kc * 64, kc * 64 + 64)
-        const uint4 *arow = A + (size_t)(m0 + tid) * k16 + (kc0 + kc) * 8;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint4 v = __ldg(arow + q);
-            *reinterpret_cast<uint4 *>(sa + ((tid >> 3) * 8 + q) * 128 + (tid & 7) * 16) = v;
-        }
-        // B rows: 64 rows x 8 uint4, two rows per thread pair
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + q * kThreads;  // 0 .. 511
-            const int r = idx >> 3, c = idx & 7;
-            const uint4 v = __ldg(B + (size_t)(n0 + r) * k16 + (kc0 + kc) * 8 + c);
-            *reinterpret_cast<uint4 *>(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16) = v;
-        }
+        cp_async_wait<kStages - 2>();            // this thread's copies of chunk kc have landed
         tma::fence_async_smem();
         tc::fence_before();
-        __syncthreads();
+        __syncthreads();                         // ... and every thread's
         if (tid == 0) {
             tc::fence_after();
             constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
@@ -94,13 +105,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                              idesc, (uint32_t)((kc | ks) != 0));
             tc::commit(&bar[s]);
         }
+        // refill the stage of chunk kc - 1 with chunk kc + kStages - 1 once its MMAs are done
+        const int nxt = kc + kStages - 1;
+        if (nxt < kchunks) {
+            const int sp = nxt % kStages;
+            if (kc >= 1) {
+                bool w = true;
+                if (warp == 0) w = tma::mbar_wait(&bar[sp], phase[sp]);
+                ok = __syncthreads_and(w) != 0;
+                if (!ok) break;
+                phase[sp] ^= 1;
+            }
+            load_chunk(A, B, m0, n0, k16, kc0 + nxt, sm + sp * kStage, sm + sp * kStage + kABytes);
+        }
+        cp_async_commit();
     }
+    cp_async_wait<0>();
     if (kchunks <= 0) {                          // empty slice: a zero partial
         float *crow = C + (size_t)(m0 + tid) * N + n0;
         for (int q = 0; q < kBN; ++q) crow[q] = 0.f;
     } else if (ok) {
         // the last commit covers every MMA issued before it
-        const int s = (kchunks - 1) & 1;
+        const int s = (kchunks - 1) % kStages;
         bool w = true;
         if (warp == 0) w = tma::mbar_wait(&bar[s], phase[s]);
         ok = __syncthreads_and(w) != 0;
@@ -123,10 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (!ok) {
         if (tid == 0) atomicExch(status, 1);
         // let MMAs still in flight finish before the columns are released (bounded)
-        if (warp == 0) {
-            tma::mbar_wait(&bar[0], phase[0]);
-            tma::mbar_wait(&bar[1], phase[1]);
-        }
+        if (warp == 0)
+            for (int q = 0; q < kStages; ++q) tma::mbar_wait(&bar[q], phase[q]);
     }
     tc::fence_before();
     __syncthreads();
