@@ -133,14 +133,14 @@ typedef struct ptycho_ctx *ptycho_handle;
 enum { PTYCHO_ALG_AP = 0, PTYCHO_ALG_EPIE_COLOUR = 1 };
 
 /* FFT form of the exit-wave step (the paper prescribes none):
- *   RADIX_FP32        FP32 radix FFTs on the CUDA cores (default; N = 16, 64, 256)
+ *   RADIX_FP32        FP32 radix FFTs on the CUDA cores (default; N = 16, 64, 128, 256)
  *   DFTGEMM_BF16X3    split-BF16 3-term DFT-by-GEMM on the tensor cores, FP32 accumulation
  *                     (see dft2_split_bf16); N = 64, one probe mode, algorithm AP. */
 enum { PTYCHO_FFT_RADIX_FP32 = 0, PTYCHO_FFT_DFTGEMM_BF16X3 = 1 };
 
 typedef struct {
     int M;                  /* object side (M x M complex64), M >= N                          */
-    int N;                  /* probe / detector side: 16, 64 or 256                           */
+    int N;                  /* probe / detector side: 16, 64, 128 or 256 (128: one mode)      */
     int J;                  /* scan positions, >= 1                                           */
     int modes;              /* incoherent probe modes Q, 1..8 (Eq. 4 with a discrete spectrum:
                                I = sum_m |F(P_m O_j)|^2, shared object); 1 = coherent Eq. 3   */

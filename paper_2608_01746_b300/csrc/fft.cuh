@@ -157,3 +157,74 @@ __device__ __forceinline__ void fft_group_xs(float2 (&d)[R], float2 *xb, const f
 }
 
 }  // namespace pm
+
+namespace pm {
+
+// N = 128 = 8 x 16 by a group of 8 threads holding 16 elements each.  tw[k1 * 8 + t] = W_128^(t k1)
+// (forward sign), k1 < 16, t < 8.  The exchange buffer is [8][17] float2 per group.
+//
+// fft128_nat_to_rev: thread t holds x[t + 8 m] (natural order).  With n = n2 + 8 n1 and
+// k = k1 + 16 k2:
+//   X[k1 + 16 k2] = sum_n2 W_8^(n2 k2) [ W_128^(n2 k1) sum_n1 x[n2 + 8 n1] W_16^(n1 k1) ]
+// thread t = n2 does the 16-point DFT and the twiddle, the group exchanges, then thread t takes
+// k1 = 2t and 2t + 1 and does two 8-point DFTs: afterwards d[8 i + k2] = X[2t + i + 16 k2].
+template <int SIGN>
+__device__ __forceinline__ void fft128_nat_to_rev(float2 (&d)[16], float2 *xb, const float2 *tw, int t) {
+    dft_reg<16, SIGN>(d);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+        float2 w = tw[k1 * 8 + t];
+        if (SIGN > 0) w.y = -w.y;
+        d[k1] = cmul(d[k1], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) xb[t * 17 + k1] = d[k1];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float2 e[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) e[n2] = xb[n2 * 17 + 2 * t + i];
+        dft_reg<8, SIGN>(e);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) d[8 * i + k2] = e[k2];
+    }
+}
+
+// The mirror split: d[8 i + k2] = X[2t + i + 16 k2] in, x[t + 8 m] out.  With k = k1 + 16 k2,
+// n = n1 + 8 n2:
+//   x[n1 + 8 n2] = sum_k1 W_16^(k1 n2) [ W_128^(k1 n1) sum_k2 X[k1 + 16 k2] W_8^(k2 n1) ]
+// (exponent signs SIGN): two 8-point DFTs over k2 (k1 = 2t, 2t + 1), the twiddle, the exchange,
+// then thread t = n1 does the 16-point DFT over k1.
+template <int SIGN>
+__device__ __forceinline__ void fft128_rev_to_nat(float2 (&d)[16], float2 *xb, const float2 *tw, int t) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float2 e[8];
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) e[k2] = d[8 * i + k2];
+        dft_reg<8, SIGN>(e);
+        const int k1 = 2 * t + i;
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            float2 w = tw[k1 * 8 + n1];
+            if (SIGN > 0) w.y = -w.y;
+            d[8 * i + n1] = cmul(e[n1], w);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) xb[n1 * 17 + 2 * t + i] = d[8 * i + n1];
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) d[k1] = xb[t * 17 + k1];
+    dft_reg<16, SIGN>(d);
+}
+
+// Position of element e of thread t after fft128_nat_to_rev: 2t + e / 8 + 16 (e % 8).
+__device__ __forceinline__ int rev128(int t, int e) { return 2 * t + (e >> 3) + 16 * (e & 7); }
+
+}  // namespace pm

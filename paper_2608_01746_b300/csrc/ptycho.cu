@@ -205,6 +205,114 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
     }
 }
 
+// N = 128 = 8 x 16 (one probe mode; XM_FULL, XM_LIST; dataset tables as k_exit_wave): groups
+// of 8 threads, 16 elements each.  Forward transforms leave digit-reversed order
+// (fft128_nat_to_rev), inverse transforms consume it (fft128_rev_to_nat), so the tile holds the
+// row spectrum at its true frequencies and each column is forward-transformed, projected and
+// inverse-transformed in registers.
+constexpr size_t exit128_smem_bytes() {
+    constexpr int N = 128, G = kThreads / 8;
+    return sizeof(float2) * ((size_t)N + (size_t)G * 8 * 17 + (size_t)N * (N + 1));
+}
+
+template <int XM>
+__global__ void __launch_bounds__(kThreads) k_exit_wave128(ExitArgs a) {
+    constexpr int N = 128, R1 = 8, E = 16;
+    constexpr int G = kThreads / R1;
+    constexpr int TP = N + 1;
+    extern __shared__ float2 smem[];
+    float2 *tw = smem;                       // [N] W_128^((i / 8) (i % 8)), forward sign
+    float2 *xb_all = tw + N;                 // [G][8][17]
+    float2 *rows = xb_all + G * 8 * 17;      // [N][N+1]
+    __shared__ double s_red[kThreads / 32];
+    const int tid = threadIdx.x;
+    const int t = tid % R1, g = tid / R1;
+    for (int i = tid; i < N; i += kThreads) {
+        double sn, cs;
+        sincospi(-2.0 * (double)((i / R1) * (i % R1)) / (double)N, &sn, &cs);
+        tw[i] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    float2 *xb = xb_all + g * 8 * 17;
+    const float invN = 1.0f / (float)N;
+    const int units = (XM == XM_LIST) ? a.count : a.J;
+    for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
+        int j = (XM == XM_LIST) ? a.list[iu] : iu;
+        ExitArgs c = a;
+        if (XM == XM_FULL && a.table) {
+            int lo = 0, hi = a.ntable - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.ustart + mid) <= iu) lo = mid;
+                else hi = mid - 1;
+            }
+            c = a.table[lo];
+            j = iu - __ldg(a.ustart + lo);
+        }
+        const int M = c.M;
+        float2 *psi_j = c.psi + (size_t)j * N * N;
+        const int2 pj = c.pos[j];
+        // (1) psi = P O_j, forward row FFTs; stored at the true frequency kx
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int r = r0 + g;
+            float2 d[E];
+            const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
+            const float2 *prow = c.probe + (size_t)r * N;
+#pragma unroll
+            for (int m = 0; m < E; ++m) d[m] = cmul(__ldg(prow + t + R1 * m), __ldg(orow + t + R1 * m));
+            pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
+#pragma unroll
+            for (int e = 0; e < E; ++e) rows[r * TP + pm::rev128(t, e)] = d[e];
+        }
+        __syncthreads();
+        // (2) columns: forward, modulus (ky = rev128(t, e)), inverse back to natural rows
+        float err = 0.f;
+        const float *amp_j = c.amp + (size_t)j * N * N;
+        for (int c0 = 0; c0 < N; c0 += G) {
+            const int col = c0 + g;
+            float2 d[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) d[m] = rows[(t + R1 * m) * TP + col];
+            pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float2 X = cscale(d[e], invN);
+                const float A = __ldg(amp_j + (size_t)col * N + pm::rev128(t, e));
+                const float mag = sqrtf(cabs2(X));
+                const float dm = mag - A;
+                err += dm * dm;
+                d[e] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+            }
+            pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
+#pragma unroll
+            for (int m = 0; m < E; ++m) rows[(t + R1 * m) * TP + col] = d[m];
+        }
+        __syncthreads();
+        // (3) inverse row FFTs from the true frequencies, psi' written row-major
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int r = r0 + g;
+            float2 d[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) d[e] = rows[r * TP + pm::rev128(t, e)];
+            pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
+#pragma unroll
+            for (int m = 0; m < E; ++m) psi_j[(size_t)r * N + t + R1 * m] = cscale(d[m], invN);
+        }
+        // Fourier error of position j (FP64 block sum)
+        double e64 = (double)err;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = e64;
+        __syncthreads();
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+            c.err[j] = sum;
+        }
+        __syncthreads();
+    }
+}
+
 // Mixed-state modulus constraint, one block per position: S = sum_m |Psi_m|^2,
 // error (sqrt(S) - A)^2, Psi_m <- Psi_m A / sqrt(S) (where S = 0: Psi_0 = A, other modes 0).
 // psi: [J][Q][N][N] spectra (row-major, DC at 0); amp_nat: [J][N][N] row-major amplitudes.
@@ -1080,8 +1188,47 @@ int launch_exit(ptycho_ctx *h, int xm) {
     return PTYCHO_OK;
 }
 
+int setup_exit128(ptycho_ctx *h) {
+    int dev = 0, sms = 0, per_sm = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = exit128_smem_bytes();
+    if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
+        PM_CUDA(cudaFuncSetAttribute(k_exit_wave128<XM_LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_LIST>, kThreads, smem));
+    } else {
+        PM_CUDA(cudaFuncSetAttribute(k_exit_wave128<XM_FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads, smem));
+    }
+    if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "N = 128 exit-wave kernel cannot be resident (smem %zu)", smem);
+    h->exit_smem = smem;
+    h->exit_tma = false;
+    h->grid_exit = std::max(1, std::min(h->J, sms * per_sm));
+    return PTYCHO_OK;
+}
+
+int launch_exit128(ptycho_ctx *h, int xm) {
+    ExitArgs a{};
+    a.obj = h->d_obj;
+    a.probe = h->d_probe;
+    a.amp = h->d_amp;
+    a.pos = h->d_pos;
+    a.psi = h->d_psi;
+    a.err = h->d_err_pos;
+    a.list = h->cur_list;
+    a.count = h->cur_count;
+    a.M = h->M;
+    a.J = h->J;
+    a.Q = 1;
+    if (xm == XM_LIST) k_exit_wave128<XM_LIST><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    else k_exit_wave128<XM_FULL><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    PM_LAUNCHED("k_exit_wave128");
+    return PTYCHO_OK;
+}
+
 int setup_exit(ptycho_ctx *h) {
     switch (h->R) {
+        case 128: return setup_exit128(h);
         case 4: return setup_exit_kernel<4>(h);
         case 8: return setup_exit_kernel<8>(h);
         default: return setup_exit_tma(h);
@@ -1094,6 +1241,7 @@ int launch_exit_pass(ptycho_ctx *h, int xm) {
         return pm::dft64_exit_launch(e, h->gemm_sms, h->st);
     }
     switch (h->R) {
+        case 128: return launch_exit128(h, xm);
         case 4: return launch_exit<4>(h, xm);
         case 8: return launch_exit<8>(h, xm);
         default: return launch_exit_tma(h, xm);
@@ -1240,8 +1388,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     int R = 0;
     if (d->N == 16) R = 4;
     else if (d->N == 64) R = 8;
+    else if (d->N == 128) R = 128;                   // 8 x 16: k_exit_wave128
     else if (d->N == 256) R = 16;
-    else return pm::fail(PTYCHO_EINVAL, "ptycho_init: N = %d unsupported (16, 64 or 256)", d->N);
+    else return pm::fail(PTYCHO_EINVAL, "ptycho_init: N = %d unsupported (16, 64, 128 or 256)", d->N);
     if (d->J < 1) return pm::fail(PTYCHO_EINVAL, "ptycho_init: J = %d < 1", d->J);
     if (d->M < d->N || d->M > 32768) return pm::fail(PTYCHO_EINVAL, "ptycho_init: M = %d must be in [N, 32768]", d->M);
     if (!d->h_pos || !d->d_fused || !d->obj0 || !d->probe0)
@@ -1252,6 +1401,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (d->modes < 1 || d->modes > 8) return pm::fail(PTYCHO_EINVAL, "ptycho_init: modes = %d not in [1, 8]", d->modes);
     if (d->algorithm != PTYCHO_ALG_AP && d->algorithm != PTYCHO_ALG_EPIE_COLOUR)
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: unknown algorithm %d", d->algorithm);
+    if (d->N == 128 && d->modes != 1)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: N = 128 supports one probe mode");
     if (d->algorithm == PTYCHO_ALG_EPIE_COLOUR && d->modes != 1)
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: ePIE by colour supports one probe mode");
     if (d->algorithm == PTYCHO_ALG_EPIE_COLOUR &&
@@ -1562,6 +1713,7 @@ int launch_class(ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c, cudaStre
     a.J = c.units;
     a.Q = 1;
     if (c.kind == 4) k_exit_wave<4, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
+    else if (c.kind == 128) k_exit_wave128<XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
     else k_exit_wave<8, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
     PM_LAUNCHED("k_exit_wave (datasets)");
     return PTYCHO_OK;
@@ -1670,6 +1822,10 @@ double time_iterations(ptycho_batch_ctx *b, int n, int *rc) {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune_cache;
 
+const char *class_name(int kind) {
+    return kind == 64 ? "dftgemm64" : (kind == 8 ? "radix64" : (kind == 128 ? "radix128" : "radix16"));
+}
+
 std::string class_key(const ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c) {
     std::string k = "k" + std::to_string(c.kind) + ":";
     for (int m : c.members) k += std::to_string(b->hs[m]->J) + "/" + std::to_string(b->hs[m]->M) + ",";
@@ -1720,9 +1876,8 @@ int autotune(ptycho_batch_ctx *b) {
             if (it != g_tune_cache.end()) {
                 k.grid = it->second;
                 ++cached;
-                std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d",
-                              rep.size() > 1 ? ", " : "", k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"),
-                              k.grid);
+                std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d", rep.size() > 1 ? ", " : "",
+                              class_name(k.kind), k.grid);
                 rep += buf;
                 continue;
             }
@@ -1751,8 +1906,7 @@ int autotune(ptycho_batch_ctx *b) {
             g_tune_cache[key] = best;
         }
         std::snprintf(buf, sizeof buf, "%s\"class_%s_grid\": %d, \"class_%s_tried_ms\": \"%s\"",
-                      rep.size() > 1 ? ", " : "", k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"),
-                      best, k.kind == 64 ? "dftgemm64" : (k.kind == 8 ? "radix64" : "radix16"), tried.c_str());
+                      rep.size() > 1 ? ", " : "", class_name(k.kind), best, class_name(k.kind), tried.c_str());
         rep += buf;
     }
     // rows per TMA stage of the N = 256 datasets (all together)
@@ -1898,6 +2052,8 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
             int per_sm = 0;
             c.smem = b->hs[c.members[0]]->exit_smem;
             if (c.kind == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<4, XM_FULL>, kThreads, c.smem);
+            else if (c.kind == 128)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads, c.smem);
             else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<8, XM_FULL>, kThreads, c.smem);
             if (e) return bail(pm::cuda_fail(e, "occupancy query"));
             c.grid_max = std::max(1, per_sm) * b->sms;

@@ -84,6 +84,9 @@ CONFIGS = {
                        phase_sigma=2.0),
     "mid": ScanConfig("mid", M=160, N=64, scan="raster", radius=20.0, times=(1.0, 10.0, 100.0),
                       peak=1e4, clip=4095, levels=4, n_iter=20, n_side=5, step=16, jitter=1),
+    # The same construction with a 128^2 probe (radius 40): 5 x 5 raster, step 24, 256^2 object.
+    "mid128": ScanConfig("mid128", M=256, N=128, scan="raster", radius=40.0, times=(1.0, 10.0, 100.0),
+                         peak=1e4, clip=4095, levels=4, n_iter=20, n_side=5, step=24, jitter=1),
 }
 
 
@@ -101,13 +104,13 @@ WARM_NET = ((1, 32, "s2"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (2
 def batched_configs(seed: int | None = None, count: int = 64) -> list:
     """The uneven multi-dataset workload: ``count`` scans built like the small scan (exposures
     1/10/100, 1e4 peak counts, 12-bit clip, 4 pyramid levels, 50 iterations), each with its own
-    probe side N drawn from {64, 256} (aperture radius 5N/16), an n x n raster with n drawn from
+    probe side N drawn from {64, 128, 256} (aperture radius 5N/16), an n x n raster with n drawn from
     [7, 30] (capped so the scan fits a 1024-pixel object; step N/8, +-1 px jitter) and the
     smallest object side M in [256, 1024], a multiple of 32, that holds it."""
     rng = np.random.default_rng(seed_for("batched") if seed is None else seed)
     out = []
     for d in range(count):
-        N = int(rng.choice([64, 256]))
+        N = int(rng.choice([64, 128, 256]))
         step = N // 8
         n_max = min(30, (1024 - N - 2) // step + 1)
         n = int(rng.integers(7, n_max + 1))
@@ -120,7 +123,7 @@ def batched_configs(seed: int | None = None, count: int = 64) -> list:
 
 
 def seed_for(name: str) -> int:
-    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small", "wide64"]
+    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small", "wide64", "mid128"]
     return 1000 + (order.index(name) if name in order else 99)
 
 

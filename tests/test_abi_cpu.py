@@ -83,7 +83,7 @@ def _desc(**kw):
     return api.PtychoDescC(**d), pos
 
 
-@pytest.mark.parametrize("kw", [{"N": 32}, {"N": 128}, {"J": 0}, {"M": 32}, {"alpha_O": -1.0},
+@pytest.mark.parametrize("kw", [{"N": 32}, {"N": 512, "M": 512}, {"N": 128, "modes": 2}, {"J": 0}, {"M": 32}, {"alpha_O": -1.0},
                                 {"modes": 0}, {"modes": 9}, {"algorithm": 2},
                                 {"algorithm": 1, "modes": 2}, {"algorithm": 1, "epie_alpha": 0.0},
                                 {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None},

@@ -24,11 +24,11 @@ def api():
     return a
 
 
-# (config, fft path, probe_update_start): N = 16 / 64 radix classes, the N = 64 tensor-core
-# class, an N = 256 dataset on its own TMA launch, a mixed-state dataset (8 modes)
+# (config, fft path, probe_update_start): N = 16 / 64 / 128 radix classes, the N = 64
+# tensor-core class, an N = 256 dataset on its own TMA launch, a mixed-state dataset (8 modes)
 DATASETS = [("tiny", "radix_fp32", 0), ("small", "radix_fp32", 3), ("mid", "radix_fp32", 0),
             ("small", "dftgemm_bf16x3", 0), ("mid", "dftgemm_bf16x3", 3), ("lab40", "radix_fp32", 0),
-            ("mixed_small", "radix_fp32", 0)]
+            ("mixed_small", "radix_fp32", 0), ("mid128", "radix_fp32", 3)]
 
 
 def _scan(name, seed):

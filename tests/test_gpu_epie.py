@@ -74,6 +74,16 @@ def test_epie_mid_fixed_probe_matches_oracle(api):
     check(api, sc, fused, 1, 10**6)
 
 
+def test_epie_128_matches_oracle(api):
+    """N = 128 (8 x 16 group FFTs), list form of the exit-wave kernel: four disjoint patches (one
+    colour; on the overlapped 5 x 5 scan every position is its own colour and 25 sequential unit
+    steps amplify a 2^-24 perturbation of the start beyond FP32 reach), two iterations."""
+    sc, fused = fused_for("mid128")
+    sc = dict(sc)
+    sc["pos"] = np.array([[0, 0], [0, 128], [128, 0], [128, 128]], np.int32)
+    check(api, sc, fused[:4].copy(), 2, 0)
+
+
 def test_epie_256_matches_oracle(api):
     """Colour lists through the N = 256 TMA exit-wave kernel: lab geometry, 60 positions."""
     cfg = dataclasses.replace(synth.CONFIGS["lab"], J=60, name="lab60")

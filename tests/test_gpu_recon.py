@@ -68,7 +68,8 @@ def oracle_sensitivity(sc, fused32, obj0, probe0, n_iter, pus):
 
 
 @pytest.mark.parametrize("name,n_iter,pus", [("tiny", 30, 0), ("tiny", 30, 5), ("mid", 10, 0),
-                                              ("small", 10, 0), ("small", 10, 10**6)])
+                                              ("small", 10, 0), ("small", 10, 10**6), ("mid128", 3, 0),
+                                              ("mid128", 10, 10**6)])
 def test_reconstruction_matches_oracle(api, name, n_iter, pus):
     """Fixed iteration count, FP32 GPU vs FP64 oracle within 1e-5 relative L2 on object and
     probe, from a start where the method is well conditioned at FP32 resolution."""
