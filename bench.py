@@ -336,8 +336,8 @@ def run_batched(args, world, rank, local):
             "traffic": None, "avg_iteration_ms": round(it_ms, 4),
             "hbm_view": {"achieved_gbs": round(hbm, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                          "frac": round(hbm / hbm_peak, 4)}}
-    n64 = sum(1 for c in cfgs if c.N == 64)
-    launches_per_iter = (1 + sum(1 for c in cfgs if c.N == 256)  # one multi-dataset exit launch + N=256 exits
+    by_n = {n: sum(1 for c in cfgs if c.N == n) for n in sorted({c.N for c in cfgs})}
+    launches_per_iter = (len(by_n) - 1 + sum(1 for c in cfgs if c.N == 256)  # class launches + N=256 exits
                          + 2 * len(cfgs) + 3 * len(cfgs) + len(cfgs))   # object (2), probe (3), error (1)
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -345,7 +345,8 @@ def run_batched(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate for N = 64, f32 for N = 256",
         "data": "synthetic (seeded jittered raster scans, Poisson counts, 12-bit clip)",
-        "config": {"workload": (f"batched: 64 uneven datasets ({n64} with 64^2 probes, {len(cfgs) - n64} with 256^2), "
+        "config": {"workload": (f"batched: 64 uneven datasets ("
+                                + ", ".join(f"{v} with {n}^2 probes" for n, v in by_n.items()) + "), "
                                 f"{updates_per_iter} positions in all, objects {min(c.M for c in cfgs)}-"
                                 f"{max(c.M for c in cfgs)} px, 3 exposures, 4-level pyramid, {n_iter} iterations "
                                 "per step, one batch (CUDA graph, autotuned)"),
