@@ -46,7 +46,7 @@ def parse():
                          "datasets (N in {64, 256}, 49-900 positions) in one batch, 50 iterations; warm: "
                          "train the warm-start network, then time to NRMSE from it vs the flat object")
     ap.add_argument("--fft", choices=["radix_fp32", "dftgemm_bf16x3"], default="radix_fp32",
-                    help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64)")
+                    help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64, 128)")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration count (profiling runs only; not a bench value)")
     ap.add_argument("--positions", type=int, default=None,
@@ -219,7 +219,7 @@ def run_batched(args, world, rank, local):
     updates_per_iter = sum(J_all)
 
     def fft_for(c, fft):
-        return fft if c.N == 64 else "radix_fp32"
+        return fft if c.N in (64, 128) else "radix_fp32"
 
     def make_handles(fft, raws=None):
         for d, c in enumerate(cfgs):
@@ -343,7 +343,7 @@ def run_batched(args, world, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate for N = 64, f32 for N = 256",
+        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate for N = 64, 128; f32 for N = 256",
         "data": "synthetic (seeded jittered raster scans, Poisson counts, 12-bit clip)",
         "config": {"workload": (f"batched: 64 uneven datasets ("
                                 + ", ".join(f"{v} with {n}^2 probes" for n, v in by_n.items()) + "), "

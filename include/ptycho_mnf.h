@@ -110,7 +110,8 @@ int fuse_sli(const uint16_t *d_raw, int J, int K, int N, const float *h_t, float
  * FFT algorithm; this is the precision form offered beside the FP32 radix path.
  *   d_in, d_out  device, complex64 [B][N][N] row-major, DC at index 0; may be the same buffer
  *   B            transforms, >= 0 (0 is a no-op)
- *   N            64 (other sizes: PTYCHO_EINVAL)
+ *   N            64 or 128 (other sizes: PTYCHO_EINVAL); 128 = two 64-point halves and a
+ *                radix-2 butterfly per pass
  *   inverse      0 forward (exp(-2 pi i k n / N), 1/N), 1 inverse (exp(+...), 1/N)
  *   d_status     device int, caller-owned; set to 1 if a bounded device wait gave up (never
  *                cleared by the library)
@@ -135,7 +136,7 @@ enum { PTYCHO_ALG_AP = 0, PTYCHO_ALG_EPIE_COLOUR = 1 };
 /* FFT form of the exit-wave step (the paper prescribes none):
  *   RADIX_FP32        FP32 radix FFTs on the CUDA cores (default; N = 16, 64, 128, 256)
  *   DFTGEMM_BF16X3    split-BF16 3-term DFT-by-GEMM on the tensor cores, FP32 accumulation
- *                     (see dft2_split_bf16); N = 64, one probe mode, algorithm AP. */
+ *                     (see dft2_split_bf16); N = 64 or 128, one probe mode, algorithm AP. */
 enum { PTYCHO_FFT_RADIX_FP32 = 0, PTYCHO_FFT_DFTGEMM_BF16X3 = 1 };
 
 typedef struct {

@@ -205,6 +205,7 @@ __device__ __forceinline__ bool pipe_and(int pipe, bool v) {
 
 // One GEMM pass D = G_hi B_hi + G_hi B_lo + G_lo B_hi of one pipeline.  Every thread of the
 // pipeline calls it; returns false (for all of them) when the completion wait gave up.
+template <int NCOLS = kCols>
 __device__ __forceinline__ bool mma_pass(int pipe, uint32_t tmem, uint32_t gh, uint32_t bh, uint64_t *bar,
                                          uint32_t &phase) {
     tma::fence_async_smem();          // operand writes -> visible to the tensor core
@@ -218,8 +219,8 @@ __device__ __forceinline__ bool mma_pass(int pipe, uint32_t tmem, uint32_t gh, u
     if (waiter) {
       if ((threadIdx.x & (kPipeThreads - 1)) == 0) {
         tc::fence_after();
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, kCols);
-        const uint32_t gl = gh + kGBytes, bl = bh + kBBytes;
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kRows, NCOLS);
+        const uint32_t gl = gh + kGBytes, bl = bh + (uint32_t)NCOLS * kK * 2;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const uint32_t ab = (t == 2) ? gl : gh;
@@ -374,6 +375,228 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// N = 128: each 128-point transform is two 64-point GEMM halves (even / odd samples) and a
+// radix-2 butterfly in the epilogue:  X[h] = E[h] + w O[h],  X[h + 64] = E[h] - w O[h],
+// w = W_128^h.  One patch per group, one 256-thread pipeline per CTA: the operand has 256 rows
+// (parity b, vector index), the accumulator 256 TMEM columns (b 128 + vector index).
+//   pass 1  b_(r%2, c)  = psi[r][c], K index r / 2        -> rows W[u][c], u = h, h + 64
+//   pass 2  b_(c%2, u)  = W[u][c], K index c / 2          -> Psi[u][v], v = h, h + 64
+//   modulus, conj; pass 3 b_(u%2, v) = conj Psi'[u][v]     -> V[k][v]
+//   pass 4  b_(v%2, k)  = V[k][v]                           -> N conj(psi')[k][x]
+constexpr int kN2 = 128;
+constexpr int kCols2 = 2 * kN2;                           // 256 operand rows / accumulator columns
+constexpr uint32_t kB2Bytes = kCols2 * kK * 2;           // 64 KB per split term
+constexpr uint32_t kSmem2 = 2 * kGBytes + 2 * kB2Bytes + 1024;
+constexpr int kThreads2 = 256;
+
+// One word (re, im) of operand row n at K index 2 q.
+__device__ __forceinline__ void put1(uint8_t *bh, uint8_t *bl, int n, int q, float2 z) {
+    uint32_t h, l;
+    split2(z, h, l);
+    const uint32_t off = tc::core_offset(n, 2 * q, kK);
+    *reinterpret_cast<uint32_t *>(bh + off) = h;
+    *reinterpret_cast<uint32_t *>(bl + off) = l;
+}
+
+// Columns [c0, c0 + 32) of both halves of this lane: complex E (column c) and O (column 128 + c)
+// after the lane-pair exchange (the thread owns c = c0 + 4 i + 2 part + {0, 1}), then the
+// butterfly with w: f(c, X_lo(c), X_hi(c), X_lo(c + 1), X_hi(c + 1)).
+template <typename F>
+__device__ __forceinline__ void butterfly_pairs(uint32_t lane_addr, int c0, int part, float2 w, F &&f) {
+    uint32_t ve[32], vo[32];
+    tc::ld_32cols(lane_addr + (uint32_t)c0, ve);
+    tc::ld_32cols(lane_addr + (uint32_t)(kN2 + c0), vo);
+    tc::wait_ld();
+#pragma unroll
+    for (int i = 0; i < 32; i += 4) {
+        const float e0 = __uint_as_float(ve[i]), e1 = __uint_as_float(ve[i + 1]);
+        const float e2 = __uint_as_float(ve[i + 2]), e3 = __uint_as_float(ve[i + 3]);
+        const float o0 = __uint_as_float(vo[i]), o1 = __uint_as_float(vo[i + 1]);
+        const float o2 = __uint_as_float(vo[i + 2]), o3 = __uint_as_float(vo[i + 3]);
+        const float ye0 = __shfl_xor_sync(0xffffffffu, part ? e0 : e2, 1);
+        const float ye1 = __shfl_xor_sync(0xffffffffu, part ? e1 : e3, 1);
+        const float yo0 = __shfl_xor_sync(0xffffffffu, part ? o0 : o2, 1);
+        const float yo1 = __shfl_xor_sync(0xffffffffu, part ? o1 : o3, 1);
+        const float2 Ea = part ? make_float2(ye0, e2) : make_float2(e0, ye0);
+        const float2 Eb = part ? make_float2(ye1, e3) : make_float2(e1, ye1);
+        const float2 wOa = cmul(w, part ? make_float2(yo0, o2) : make_float2(o0, yo0));
+        const float2 wOb = cmul(w, part ? make_float2(yo1, o3) : make_float2(o1, yo1));
+        f(c0 + i + 2 * part, cadd(Ea, wOa), csub(Ea, wOa), cadd(Eb, wOb), csub(Eb, wOb));
+    }
+}
+
+// Operand of pass 1: row (r % 2, c), K index r / 2 = psi[r][c]; thread (b, c) writes 4
+// consecutive rows of its parity per 16-byte store.
+template <int MODE>
+__device__ __forceinline__ void fill_input128(const Args &a, int j, uint8_t *bh, uint8_t *bl) {
+    const int tid = threadIdx.x;
+    const int c = tid & (kN2 - 1), b = tid >> 7;
+    const int n = b * kN2 + c;
+    const float2 *x0, *x1 = nullptr;
+    if constexpr (MODE == MODE_EXIT) {
+        const int2 pj = a.pos[j];
+        x0 = a.obj + (size_t)pj.x * a.M + pj.y + c;
+        x1 = a.probe + c;
+    } else {
+        x0 = a.in + (size_t)j * kN2 * kN2 + c;
+    }
+#pragma unroll 2
+    for (int q4 = 0; q4 < kN2 / 8; ++q4) {           // 4 values (K indices 4 q4 .. 4 q4 + 3) per store
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = 2 * (4 * q4 + q) + b;
+            float2 z;
+            if constexpr (MODE == MODE_EXIT) {
+                z = cmul(__ldg(x1 + (size_t)r * kN2), __ldg(x0 + (size_t)r * a.M));
+            } else {
+                z = __ldg(x0 + (size_t)r * kN2);
+                if (a.inverse) z.y = -z.y;
+            }
+            split2(z, h[q], l[q]);
+        }
+        const uint32_t off = tc::core_offset(n, 8 * q4, kK);
+        *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads2, 1) k_dft128_gemm(Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sG = sm;
+    uint8_t *sBh = sm + 2 * kGBytes;
+    uint8_t *sBl = sBh + kB2Bytes;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double s_err[kThreads2 / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < (int)(2 * kGBytes / 16); i += kThreads2) reinterpret_cast<uint4 *>(sG)[i] = g_dft64[i];
+    if (warp == 0) tc::alloc(&tmem_slot, 256);
+    if (tid == 0) {
+        tma::mbar_init(&bar, 1);
+        tma::fence_barrier_init();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t gh = tc::smem_addr(sG), bh = tc::smem_addr(sBh);
+    uint32_t phase = 0;
+    const int row = 32 * (warp & 3) + lane;              // TMEM lane 2 h + part
+    const int h = row >> 1, part = row & 1;
+    const int cbase = (warp >> 2) * 64;                  // this warp's vector indices: cbase .. + 63
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    float ws, wc;
+    sincospif(-2.0f * (float)h / (float)kN2, &ws, &wc);   // w = W_128^h (forward sign)
+    const float2 w = make_float2(wc, ws);
+    const float invN = 1.0f / (float)kN2;
+    bool failed = false;
+    for (int j = blockIdx.x; j < a.J; j += gridDim.x) {
+        fill_input128<MODE>(a, j, sBh, sBl);
+        if (!mma_pass<kCols2>(0, tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        // pass-2 operand: row (c % 2, u), K index c / 2 = W[u][c], u = h and h + 64
+#pragma unroll 1
+        for (int c0 = cbase; c0 < cbase + 64; c0 += 32)
+            butterfly_pairs(lane_addr, c0, part, w, [&](int c, float2 la, float2 ha, float2 lb, float2 hb) {
+                put1(sBh, sBl, h, c >> 1, la);
+                put1(sBh, sBl, h + 64, c >> 1, ha);
+                put1(sBh, sBl, kN2 + h, c >> 1, lb);
+                put1(sBh, sBl, kN2 + h + 64, c >> 1, hb);
+            });
+        if (!mma_pass<kCols2>(0, tmem, gh, bh, &bar, phase)) { failed = true; break; }
+        // lane (h, part): Psi[u][h] and Psi[u][h + 64] for u = c (even) and c + 1
+        if constexpr (MODE == MODE_DFT) {
+            float2 *o = a.out + (size_t)j * kN2 * kN2;
+            const float sy = a.inverse ? -invN : invN;
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + 64; c0 += 32)
+                butterfly_pairs(lane_addr, c0, part, w, [&](int u, float2 la, float2 ha, float2 lb, float2 hb) {
+                    o[(size_t)u * kN2 + h] = make_float2(la.x * invN, la.y * sy);
+                    o[(size_t)u * kN2 + h + 64] = make_float2(ha.x * invN, ha.y * sy);
+                    o[(size_t)(u + 1) * kN2 + h] = make_float2(lb.x * invN, lb.y * sy);
+                    o[(size_t)(u + 1) * kN2 + h + 64] = make_float2(hb.x * invN, hb.y * sy);
+                });
+        } else {
+            float ep = 0.f;
+            const float *amp = a.amp + (size_t)j * kN2 * kN2;    // amp[kx][ky]
+            auto proj = [&](float2 z, float A) {
+                z = cscale(z, invN);
+                const float mag = sqrtf(cabs2(z));
+                const float dm = mag - A;
+                ep += dm * dm;
+                z = mag > 0.f ? cscale(z, A / mag) : make_float2(A, 0.f);
+                z.y = -z.y;
+                return z;
+            };
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + 64; c0 += 32)
+                butterfly_pairs(lane_addr, c0, part, w, [&](int u, float2 la, float2 ha, float2 lb, float2 hb) {
+                    const float2 A_lo = __ldg(reinterpret_cast<const float2 *>(amp + (size_t)h * kN2 + u));
+                    const float2 A_hi = __ldg(reinterpret_cast<const float2 *>(amp + (size_t)(h + 64) * kN2 + u));
+                    // pass-3 operand: row (u % 2, v), K index u / 2 = conj Psi'[u][v]
+                    put1(sBh, sBl, h, u >> 1, proj(la, A_lo.x));
+                    put1(sBh, sBl, h + 64, u >> 1, proj(ha, A_hi.x));
+                    put1(sBh, sBl, kN2 + h, u >> 1, proj(lb, A_lo.y));
+                    put1(sBh, sBl, kN2 + h + 64, u >> 1, proj(hb, A_hi.y));
+                });
+            if (!mma_pass<kCols2>(0, tmem, gh, bh, &bar, phase)) { failed = true; break; }
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + 64; c0 += 32)
+                butterfly_pairs(lane_addr, c0, part, w, [&](int v, float2 la, float2 ha, float2 lb, float2 hb) {
+                    put1(sBh, sBl, h, v >> 1, la);
+                    put1(sBh, sBl, h + 64, v >> 1, ha);
+                    put1(sBh, sBl, kN2 + h, v >> 1, lb);
+                    put1(sBh, sBl, kN2 + h + 64, v >> 1, hb);
+                });
+            if (!mma_pass<kCols2>(0, tmem, gh, bh, &bar, phase)) { failed = true; break; }
+            // lane (x = h, part): N conj(psi')[k][h], [k][h + 64] for k = c (even), c + 1
+            float2 *o = a.psi + (size_t)j * kN2 * kN2;
+#pragma unroll 1
+            for (int c0 = cbase; c0 < cbase + 64; c0 += 32)
+                butterfly_pairs(lane_addr, c0, part, w, [&](int k, float2 la, float2 ha, float2 lb, float2 hb) {
+                    o[(size_t)k * kN2 + h] = make_float2(la.x * invN, -la.y * invN);
+                    o[(size_t)k * kN2 + h + 64] = make_float2(ha.x * invN, -ha.y * invN);
+                    o[(size_t)(k + 1) * kN2 + h] = make_float2(lb.x * invN, -lb.y * invN);
+                    o[(size_t)(k + 1) * kN2 + h + 64] = make_float2(hb.x * invN, -hb.y * invN);
+                });
+            double d = (double)ep;
+#pragma unroll
+            for (int o2 = 16; o2 > 0; o2 >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o2);
+            if (lane == 0) s_err[warp] = d;
+            __syncthreads();
+            if (tid == 0) {
+                double sum = 0.0;
+                for (int q = 0; q < kThreads2 / 32; ++q) sum += s_err[q];
+                a.err[j] = sum;
+            }
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(a.status, 1);
+        tma::mbar_wait(&bar, phase);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tmem, 256);
+    }
+}
+
+int launch128(const Args &a, int mode, int sm_count, cudaStream_t st) {
+    if (a.J <= 0) return PTYCHO_OK;
+    const int grid = a.J < sm_count ? a.J : sm_count;
+    if (mode == MODE_EXIT)
+        k_dft128_gemm<MODE_EXIT><<<grid, kThreads2, kSmem2, st>>>(a);
+    else
+        k_dft128_gemm<MODE_DFT><<<grid, kThreads2, kSmem2, st>>>(a);
+    PM_LAUNCHED("k_dft128_gemm");
+    return PTYCHO_OK;
+}
+
 std::mutex g_mu;
 bool g_ready[64] = {};
 
@@ -402,6 +625,8 @@ int dft64_prepare(int *sm_count) {
     if (dev >= 0 && dev < 64 && g_ready[dev]) return PTYCHO_OK;
     PM_CUDA(cudaFuncSetAttribute(k_dft64_gemm<MODE_EXIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     PM_CUDA(cudaFuncSetAttribute(k_dft64_gemm<MODE_DFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    PM_CUDA(cudaFuncSetAttribute(k_dft128_gemm<MODE_EXIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2));
+    PM_CUDA(cudaFuncSetAttribute(k_dft128_gemm<MODE_DFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2));
     k_fill_dft64<<<(kRows * kK + 255) / 256, 256>>>();
     PM_LAUNCHED("k_fill_dft64");
     PM_CUDA(cudaDeviceSynchronize());
@@ -425,6 +650,20 @@ int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st) {
 
 int dft64_groups(int J) { return (J + kP - 1) / kP; }
 
+int dft128_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st) {
+    Args a{};
+    a.obj = e.obj;
+    a.probe = e.probe;
+    a.amp = e.amp;
+    a.pos = e.pos;
+    a.psi = e.psi;
+    a.err = e.err;
+    a.status = e.status;
+    a.M = e.M;
+    a.J = e.J;
+    return launch128(a, MODE_EXIT, sm_count, st);
+}
+
 int dft64_exit_multi_launch(const Dft64Exit *d_table, const int *d_gstart, int ntable, int total_groups,
                             int *d_status, int grid_cap, cudaStream_t st) {
     Args a{};
@@ -439,7 +678,7 @@ int dft64_exit_multi_launch(const Dft64Exit *d_table, const int *d_gstart, int n
 
 extern "C" int dft2_split_bf16(const void *d_in, void *d_out, int B, int N, int inverse, int *d_status,
                                void *cuda_stream) {
-    if (N != 64) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: N = %d unsupported (64 only)", N);
+    if (N != 64 && N != 128) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: N = %d unsupported (64 or 128)", N);
     if (B < 0) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: B = %d < 0", B);
     if (inverse != 0 && inverse != 1) return pm::fail(PTYCHO_EINVAL, "dft2_split_bf16: inverse must be 0 or 1");
     if (B == 0) return PTYCHO_OK;
@@ -453,5 +692,6 @@ extern "C" int dft2_split_bf16(const void *d_in, void *d_out, int B, int N, int 
     a.inverse = inverse;
     a.status = d_status;
     a.J = B;
+    if (N == 128) return launch128(a, MODE_DFT, sms, static_cast<cudaStream_t>(cuda_stream));
     return launch(a, MODE_DFT, sms, static_cast<cudaStream_t>(cuda_stream));
 }

@@ -1,5 +1,5 @@
 // Internal interface between the reconstruction engine and the split-BF16 tensor-core DFT
-// (N = 64), see dftgemm.cu.
+// (N = 64 and 128; the Dft64Exit record serves both), see dftgemm.cu.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,6 +23,9 @@ int dft64_prepare(int *sm_count);
 
 // psi_j' = F^-1[A_j F(P O_j) / |F(P O_j)|] for every j, tensor-core DFTs; one launch.
 int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
+
+// The same for N = 128 (two 64-point halves and a radix-2 butterfly per pass; one launch).
+int dft128_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
 
 // Patch groups the kernel makes of J positions (the unit of work of one pipeline).
 int dft64_groups(int J);

@@ -1238,6 +1238,7 @@ int setup_exit(ptycho_ctx *h) {
 int launch_exit_pass(ptycho_ctx *h, int xm) {
     if (h->fft_gemm) {
         pm::Dft64Exit e{h->d_obj, h->d_probe, h->d_amp, h->d_pos, h->d_psi, h->d_err_pos, h->d_status, h->M, h->J};
+        if (h->N == 128) return pm::dft128_exit_launch(e, h->gemm_sms, h->st);
         return pm::dft64_exit_launch(e, h->gemm_sms, h->st);
     }
     switch (h->R) {
@@ -1411,8 +1412,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (d->fft_path != PTYCHO_FFT_RADIX_FP32 && d->fft_path != PTYCHO_FFT_DFTGEMM_BF16X3)
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: unknown fft_path %d", d->fft_path);
     if (d->fft_path == PTYCHO_FFT_DFTGEMM_BF16X3 &&
-        (d->N != 64 || d->modes != 1 || d->algorithm != PTYCHO_ALG_AP))
-        return pm::fail(PTYCHO_EINVAL, "ptycho_init: the DFT-GEMM path needs N = 64, one mode and algorithm AP");
+        ((d->N != 64 && d->N != 128) || d->modes != 1 || d->algorithm != PTYCHO_ALG_AP))
+        return pm::fail(PTYCHO_EINVAL, "ptycho_init: the DFT-GEMM path needs N = 64 or 128, one mode and algorithm AP");
     const int M = d->M, N = d->N, J = d->J, Q = d->modes;
     for (int j = 0; j < J; ++j) {
         const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
@@ -2006,7 +2007,7 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
     // classes of datasets served by one multi-dataset exit-wave launch
     for (int i = 0; i < n; ++i) {
         ptycho_ctx *h = b->hs[i];
-        if (h->Q != 1 || h->exit_tma) continue;
+        if (h->Q != 1 || h->exit_tma || (h->fft_gemm && h->N != 64)) continue;   // own launch on its branch
         const int kind = h->fft_gemm ? 64 : h->R;
         int c = -1;
         for (size_t k = 0; k < b->cls.size(); ++k)

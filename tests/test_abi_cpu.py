@@ -87,7 +87,7 @@ def _desc(**kw):
                                 {"modes": 0}, {"modes": 9}, {"algorithm": 2},
                                 {"algorithm": 1, "modes": 2}, {"algorithm": 1, "epie_alpha": 0.0},
                                 {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None},
-                                {"fft_path": 2}, {"fft_path": 1, "N": 16, "M": 64},
+                                {"fft_path": 2}, {"fft_path": 1, "N": 16, "M": 64}, {"fft_path": 1, "N": 256, "M": 256},
                                 {"fft_path": 1, "modes": 2}, {"fft_path": 1, "algorithm": 1}])
 def test_ptycho_init_rejects_bad_arguments(L, kw):
     d, _pos = _desc(**kw)
@@ -113,7 +113,7 @@ def test_null_handles(L):
     L.ptycho_destroy(None)
 
 
-@pytest.mark.parametrize("B,N,inv", [(1, 32, 0), (1, 256, 0), (-1, 64, 0), (1, 64, 2)])
+@pytest.mark.parametrize("B,N,inv", [(1, 32, 0), (1, 256, 0), (-1, 64, 0), (1, 64, 2), (-1, 128, 0)])
 def test_dft2_split_bf16_rejects_bad_arguments(L, B, N, inv):
     rc = L.dft2_split_bf16(ctypes.c_void_p(16), ctypes.c_void_p(16), B, N, inv, ctypes.c_void_p(16), None)
     assert rc == api.PTYCHO_EINVAL

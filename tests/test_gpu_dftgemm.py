@@ -33,9 +33,9 @@ def api():
     return a
 
 
-def _inputs(B, seed):
+def _inputs(B, seed, N=64):
     rng = np.random.default_rng(seed)
-    x = (rng.standard_normal((B, 64, 64)) + 1j * rng.standard_normal((B, 64, 64))).astype(np.complex64)
+    x = (rng.standard_normal((B, N, N)) + 1j * rng.standard_normal((B, N, N))).astype(np.complex64)
     x[0] = 0
     x[0, 3, 5] = 1.0                     # impulse: a pure twiddle pattern
     if B > 1:
@@ -47,9 +47,10 @@ def _per_transform_rel(a, b):
     return np.array([rel_l2(a[i], b[i]) for i in range(a.shape[0])])
 
 
-@pytest.mark.parametrize("B", [1, 3, 4, 13, 600])
-def test_forward_and_inverse_match_fp64(api, B):
-    x = _inputs(B, B)
+@pytest.mark.parametrize("B,N", [(1, 64), (3, 64), (4, 64), (13, 64), (600, 64), (1, 128), (5, 128),
+                                 (150, 128)])
+def test_forward_and_inverse_match_fp64(api, B, N):
+    x = _inputs(B, B, N)
     xt = torch.from_numpy(x).cuda()
     y, st = api.dft2_split_bf16(xt)
     z, st2 = api.dft2_split_bf16(xt, inverse=True)
@@ -59,7 +60,7 @@ def test_forward_and_inverse_match_fp64(api, B):
     ref_i = np.stack([oracle.ifft2u(x[i].astype(np.complex128)) for i in range(B)])
     ef = _per_transform_rel(y.cpu().numpy(), ref_f)
     ei = _per_transform_rel(z.cpu().numpy(), ref_i)
-    print(f"B={B}: forward rel L2 max {ef.max():.3e} mean {ef.mean():.3e}; "
+    print(f"B={B} N={N}: forward rel L2 max {ef.max():.3e} mean {ef.mean():.3e}; "
           f"inverse max {ei.max():.3e} (bound {DFT_BOUND:.3e})")
     assert ef.max() <= DFT_BOUND
     assert ei.max() <= DFT_BOUND
@@ -149,3 +150,23 @@ def test_gemm_path_is_deterministic_and_timed(api):
         api.ptycho_destroy(h)
         assert list(launches)[0] == 3               # one exit-wave launch per iteration
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("subset", [None, [0, 6, 12]])
+def test_n128_iteration_matches_oracle(api, subset):
+    """N = 128 (two 64-point GEMM halves + radix-2 butterfly per pass): one iteration on the
+    5 x 5 / 128^2-probe scan and on a 3-position subset, within the exit-wave bound."""
+    sc, fused = _fused("mid128")
+    pos = sc["pos"] if subset is None else sc["pos"][subset]
+    fused = fused if subset is None else fused[subset]
+    M = sc["cfg"].M
+    rng = np.random.default_rng(1)
+    obj0 = (1.0 + 0.1 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))).astype(np.complex64)
+    probe0 = sc["probe"].astype(np.complex64)
+    o, p, e = _run(api, sc, fused, pos, obj0, probe0, 1, "dftgemm_bf16x3")
+    ro, rp, re = oracle.reconstruct(fused.astype(np.float64), pos, obj0.astype(np.complex128),
+                                    probe0.astype(np.complex128), 1, 1e-3, 1e-3, 0)
+    print(f"N=128 J={len(pos)}: object {rel_l2(o, ro):.3e} probe {rel_l2(p, rp):.3e}")
+    assert rel_l2(o, ro) <= EXIT_BOUND
+    assert rel_l2(p, rp) <= EXIT_BOUND
+    assert abs(e[0] - re[0]) <= EXIT_BOUND * re[0]
