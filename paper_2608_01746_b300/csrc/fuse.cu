@@ -61,26 +61,6 @@ __device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, s
     for (int k = 0; k < K; ++k) W[k] = (s > 0.f) ? W[k] / s : 1.0f / K;
 }
 
-// U2(X) at fine pixel (m1, m2) of a 2n x 2n grid, X an n x n plane.
-__device__ __forceinline__ float upsample_at(const float *X, int n, int m1, int m2) {
-    int iy[3], ix[3];
-    float wy[3], wx[3];
-    int ny, nx;
-    if (m1 & 1) { const int i = m1 >> 1; iy[0] = i; iy[1] = min(i + 1, n - 1); wy[0] = wy[1] = 0.5f; ny = 2; }
-    else { const int i = m1 >> 1; iy[0] = (i == 0) ? 1 : i - 1; iy[1] = i; iy[2] = min(i + 1, n - 1);
-           wy[0] = 0.125f; wy[1] = 0.75f; wy[2] = 0.125f; ny = 3; }
-    if (m2 & 1) { const int i = m2 >> 1; ix[0] = i; ix[1] = min(i + 1, n - 1); wx[0] = wx[1] = 0.5f; nx = 2; }
-    else { const int i = m2 >> 1; ix[0] = (i == 0) ? 1 : i - 1; ix[1] = i; ix[2] = min(i + 1, n - 1);
-           wx[0] = 0.125f; wx[1] = 0.75f; wx[2] = 0.125f; nx = 3; }
-    float acc = 0.f;
-    for (int a = 0; a < ny; ++a) {
-        float r = 0.f;
-        for (int b = 0; b < nx; ++b) r += wx[b] * __ldg(X + (size_t)iy[a] * n + ix[b]);
-        acc += wy[a] * r;
-    }
-    return acc;
-}
-
 __device__ __forceinline__ float quantise(float x, float delta) {
     return delta > 0.f ? delta * rintf(x / delta) : x;
 }
