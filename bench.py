@@ -39,10 +39,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["lab", "mixed", "wide64", "batched", "warm"], default="lab",
+    ap.add_argument("--workload", choices=["lab", "mixed", "wide64", "wide128", "batched", "warm"], default="lab",
                     help="lab: coherent lab-scale scan (the headline); mixed: the same scan with "
                          "8 incoherent probe modes, 100 iterations; wide64: 64^2 probe, 9216 "
-                         "raster positions on a 1024^2 object, 50 iterations; batched: 64 uneven "
+                         "raster positions on a 1024^2 object, 50 iterations; wide128: 128^2 probe, "
+                         "2304 positions, 50 iterations; batched: 64 uneven "
                          "datasets (N in {64, 256}, 49-900 positions) in one batch, 50 iterations; warm: "
                          "train the warm-start network, then time to NRMSE from it vs the flat object")
     ap.add_argument("--fft", choices=["radix_fp32", "dftgemm_bf16x3"], default="radix_fp32",
@@ -164,8 +165,11 @@ def exit_wave_flops_per_position(N: int) -> float:
 
 
 def dftgemm_flops_per_position(N: int) -> float:
-    """Tensor-core flops of the split-BF16 exit wave: 4 real GEMM passes (2N x 2N DFT matrix
-    times 2N x N interleaved operand), 3 split terms each."""
+    """Tensor-core flops of the split-BF16 exit wave: 4 real GEMM passes, 3 split terms each.
+    N = 64: the 128 x 128 real DFT matrix times the 128 x 64 interleaved operand of a patch.
+    N = 128: the same 64-point matrix times two halves (even / odd samples) of 128 vectors."""
+    if N == 128:
+        return 4 * 3 * 2.0 * 128 * 128 * 256
     return 4 * 3 * 2.0 * (2 * N) * (2 * N) * N
 
 
@@ -581,7 +585,7 @@ def run_ours(args, world, rank, local):
     hbm_algo = Q * exit_wave_bytes_per_position(N) * J / (exit_ms / 1e3) / 1e9
     tpp = profiled_traffic_per_position()
     traffic = int(tpp * J) if (tpp is not None and N == 256 and Q == 1) else None
-    kname = ("k_exit_wave_tma" if N == 256 else "k_exit_wave") + (
+    kname = ("k_exit_wave_tma" if N == 256 else ("k_exit_wave128" if N == 128 else "k_exit_wave")) + (
         " (forward + k_modulus_modes + inverse, per iteration)" if Q > 1 else "")
     roof = {"kernel": kname, "bound": "alu",
             "achieved": round(flops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
@@ -595,7 +599,7 @@ def run_ours(args, world, rank, local):
     if args.fft == "dftgemm_bf16x3":
         tflops = dftgemm_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
         bf16_peak, bf16_kind = bf16_peak_tflops()
-        roof = {"kernel": "k_dft64_gemm<exit> (tcgen05 split-BF16 DFT-GEMM)", "bound": "tensor",
+        roof = {"kernel": f"k_dft{N}_gemm<exit> (tcgen05 split-BF16 DFT-GEMM)", "bound": "tensor",
                 "achieved": round(tflops, 2), "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": round(tflops / bf16_peak, 4), "peak_kind": bf16_kind,
                 "flops_per_position": dftgemm_flops_per_position(N),
@@ -608,7 +612,7 @@ def run_ours(args, world, rank, local):
     launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
 
     conv = None
-    if rank == 0 and not args.no_nrmse and Q == 1 and args.workload == "wide64":
+    if rank == 0 and not args.no_nrmse and Q == 1 and args.workload in ("wide64", "wide128"):
         fixed = 10 ** 9
         conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, 200,
                               probe_update_start=fixed, fft_path=f)
@@ -661,6 +665,9 @@ def workload_text(name: str, n_iter: int) -> str:
     if name == "mixed":
         return ("mixed-state: the lab scan with 8 incoherent probe modes (+-10% bandwidth), modulus per "
                 f"mode, {n_iter} iterations per step")
+    if name == "wide128":
+        return ("wide 128^2-probe scan: object 1024x1024 c64, probe 128x128, 48x48 raster (2304 positions), "
+                f"3 exposures (1/10/100), 4-level pyramid, {n_iter} iterations per step")
     return ("wide 64^2-probe scan: object 1024x1024 c64, probe 64x64, 96x96 raster (9216 positions), "
             f"3 exposures (1/10/100), 4-level pyramid, {n_iter} iterations per step")
 

@@ -210,24 +210,26 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
 // (fft128_nat_to_rev), inverse transforms consume it (fft128_rev_to_nat), so the tile holds the
 // row spectrum at its true frequencies and each column is forward-transformed, projected and
 // inverse-transformed in registers.
+constexpr int kThreads128 = 512;         // 64 groups of 8 threads: 64 rows / columns per pass
+
 constexpr size_t exit128_smem_bytes() {
-    constexpr int N = 128, G = kThreads / 8;
+    constexpr int N = 128, G = kThreads128 / 8;
     return sizeof(float2) * ((size_t)N + (size_t)G * 8 * 17 + (size_t)N * (N + 1));
 }
 
 template <int XM>
-__global__ void __launch_bounds__(kThreads) k_exit_wave128(ExitArgs a) {
+__global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
     constexpr int N = 128, R1 = 8, E = 16;
-    constexpr int G = kThreads / R1;
+    constexpr int G = kThreads128 / R1;
     constexpr int TP = N + 1;
     extern __shared__ float2 smem[];
     float2 *tw = smem;                       // [N] W_128^((i / 8) (i % 8)), forward sign
     float2 *xb_all = tw + N;                 // [G][8][17]
     float2 *rows = xb_all + G * 8 * 17;      // [N][N+1]
-    __shared__ double s_red[kThreads / 32];
+    __shared__ double s_red[kThreads128 / 32];
     const int tid = threadIdx.x;
     const int t = tid % R1, g = tid / R1;
-    for (int i = tid; i < N; i += kThreads) {
+    for (int i = tid; i < N; i += kThreads128) {
         double sn, cs;
         sincospi(-2.0 * (double)((i / R1) * (i % R1)) / (double)N, &sn, &cs);
         tw[i] = make_float2((float)cs, (float)sn);
@@ -268,8 +270,11 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave128(ExitArgs a) {
         // (2) columns: forward, modulus (ky = rev128(t, e)), inverse back to natural rows
         float err = 0.f;
         const float *amp_j = c.amp + (size_t)j * N * N;
+        // the 4 groups of a warp take columns 8 apart: with the row pitch of 129 float2 their
+        // column reads and writes fall in distinct banks (2 t + 16 q words)
+        const int col_off = 8 * (g & 3) + ((g >> 2) & 7) + 32 * (g >> 5);
         for (int c0 = 0; c0 < N; c0 += G) {
-            const int col = c0 + g;
+            const int col = c0 + col_off;
             float2 d[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) d[m] = rows[(t + R1 * m) * TP + col];
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave128(ExitArgs a) {
         __syncthreads();
         if (tid == 0) {
             double sum = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+            for (int w = 0; w < kThreads128 / 32; ++w) sum += s_red[w];
             c.err[j] = sum;
         }
         __syncthreads();
@@ -1195,10 +1200,10 @@ int setup_exit128(ptycho_ctx *h) {
     const size_t smem = exit128_smem_bytes();
     if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
         PM_CUDA(cudaFuncSetAttribute(k_exit_wave128<XM_LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_LIST>, kThreads, smem));
+        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_LIST>, kThreads128, smem));
     } else {
         PM_CUDA(cudaFuncSetAttribute(k_exit_wave128<XM_FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads, smem));
+        PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads128, smem));
     }
     if (per_sm < 1) return pm::fail(PTYCHO_ECUDA, "N = 128 exit-wave kernel cannot be resident (smem %zu)", smem);
     h->exit_smem = smem;
@@ -1220,8 +1225,8 @@ int launch_exit128(ptycho_ctx *h, int xm) {
     a.M = h->M;
     a.J = h->J;
     a.Q = 1;
-    if (xm == XM_LIST) k_exit_wave128<XM_LIST><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
-    else k_exit_wave128<XM_FULL><<<h->grid_exit, kThreads, h->exit_smem, h->st>>>(a);
+    if (xm == XM_LIST) k_exit_wave128<XM_LIST><<<h->grid_exit, kThreads128, h->exit_smem, h->st>>>(a);
+    else k_exit_wave128<XM_FULL><<<h->grid_exit, kThreads128, h->exit_smem, h->st>>>(a);
     PM_LAUNCHED("k_exit_wave128");
     return PTYCHO_OK;
 }
@@ -1714,7 +1719,7 @@ int launch_class(ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c, cudaStre
     a.J = c.units;
     a.Q = 1;
     if (c.kind == 4) k_exit_wave<4, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
-    else if (c.kind == 128) k_exit_wave128<XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
+    else if (c.kind == 128) k_exit_wave128<XM_FULL><<<c.grid, kThreads128, c.smem, s>>>(a);
     else k_exit_wave<8, XM_FULL><<<c.grid, kThreads, c.smem, s>>>(a);
     PM_LAUNCHED("k_exit_wave (datasets)");
     return PTYCHO_OK;
@@ -2054,7 +2059,7 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
             c.smem = b->hs[c.members[0]]->exit_smem;
             if (c.kind == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<4, XM_FULL>, kThreads, c.smem);
             else if (c.kind == 128)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads, c.smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave128<XM_FULL>, kThreads128, c.smem);
             else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_exit_wave<8, XM_FULL>, kThreads, c.smem);
             if (e) return bail(pm::cuda_fail(e, "occupancy query"));
             c.grid_max = std::max(1, per_sm) * b->sms;

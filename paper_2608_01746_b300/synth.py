@@ -78,6 +78,9 @@ CONFIGS = {
     # 1024^2 object with a 96 x 96 raster, step 10: 9216 positions, enough to fill the GPU.
     "wide64": ScanConfig("wide64", M=1024, N=64, scan="raster", radius=20.0, times=(1.0, 10.0, 100.0),
                          peak=1e4, clip=4095, levels=4, n_iter=50, n_side=96, step=10, jitter=1),
+    # The same with a 128^2 probe (radius 40): 48 x 48 raster, step 18 (2304 positions).
+    "wide128": ScanConfig("wide128", M=1024, N=128, scan="raster", radius=40.0, times=(1.0, 10.0, 100.0),
+                          peak=1e4, clip=4095, levels=4, n_iter=50, n_side=48, step=18, jitter=1),
     # Reduced cases for the CPU tests (same construction, smaller sizes).
     "tiny": ScanConfig("tiny", M=64, N=16, scan="raster", radius=5.0, times=(1.0, 10.0, 100.0),
                        peak=1e4, clip=4095, levels=3, n_iter=30, n_side=5, step=4, jitter=1,
@@ -123,7 +126,7 @@ def batched_configs(seed: int | None = None, count: int = 64) -> list:
 
 
 def seed_for(name: str) -> int:
-    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small", "wide64", "mid128"]
+    order = ["small", "lab", "mixed", "batched", "warm", "tiny", "mid", "mixed_small", "wide64", "mid128", "wide128"]
     return 1000 + (order.index(name) if name in order else 99)
 
 
