@@ -161,7 +161,9 @@ __device__ __forceinline__ void fft_group_xs(float2 (&d)[R], float2 *xb, const f
 namespace pm {
 
 // N = 128 = 8 x 16 by a group of 8 threads holding 16 elements each.  tw[k1 * 8 + t] = W_128^(t k1)
-// (forward sign), k1 < 16, t < 8.  The exchange buffer is [8][17] float2 per group.
+// (forward sign), k1 < 16, t < 8.  The exchange buffer is [8][18] float2 per group (rows 18 apart;
+// with groups 145 float2 apart, both exchange patterns of two groups sharing a half-warp hit
+// distinct banks).
 //
 // fft128_nat_to_rev: thread t holds x[t + 8 m] (natural order).  With n = n2 + 8 n1 and
 // k = k1 + 16 k2:
@@ -179,13 +181,13 @@ __device__ __forceinline__ void fft128_nat_to_rev(float2 (&d)[16], float2 *xb, c
     }
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) xb[t * 17 + k1] = d[k1];
+    for (int k1 = 0; k1 < 16; ++k1) xb[t * 18 + k1] = d[k1];
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         float2 e[8];
 #pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2) e[n2] = xb[n2 * 17 + 2 * t + i];
+        for (int n2 = 0; n2 < 8; ++n2) e[n2] = xb[n2 * 18 + 2 * t + i];
         dft_reg<8, SIGN>(e);
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) d[8 * i + k2] = e[k2];
@@ -217,10 +219,10 @@ __device__ __forceinline__ void fft128_rev_to_nat(float2 (&d)[16], float2 *xb, c
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) xb[n1 * 17 + 2 * t + i] = d[8 * i + n1];
+        for (int n1 = 0; n1 < 8; ++n1) xb[n1 * 18 + 2 * t + i] = d[8 * i + n1];
     __syncwarp();
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) d[k1] = xb[t * 17 + k1];
+    for (int k1 = 0; k1 < 16; ++k1) d[k1] = xb[t * 18 + k1];
     dft_reg<16, SIGN>(d);
 }
 

@@ -212,9 +212,11 @@ __global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
 // inverse-transformed in registers.
 constexpr int kThreads128 = 512;         // 64 groups of 8 threads: 64 rows / columns per pass
 
+constexpr int kXB128 = 145;              // exchange buffer per group: [8][18] float2 + 1 (bank offset)
+
 constexpr size_t exit128_smem_bytes() {
     constexpr int N = 128, G = kThreads128 / 8;
-    return sizeof(float2) * ((size_t)N + (size_t)G * 8 * 17 + (size_t)N * (N + 1));
+    return sizeof(float2) * ((size_t)N + (size_t)G * kXB128 + (size_t)N * (N + 1));
 }
 
 template <int XM>
@@ -224,8 +226,8 @@ __global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
     constexpr int TP = N + 1;
     extern __shared__ float2 smem[];
     float2 *tw = smem;                       // [N] W_128^((i / 8) (i % 8)), forward sign
-    float2 *xb_all = tw + N;                 // [G][8][17]
-    float2 *rows = xb_all + G * 8 * 17;      // [N][N+1]
+    float2 *xb_all = tw + N;                 // [G][kXB128]
+    float2 *rows = xb_all + G * kXB128;      // [N][N+1]
     __shared__ double s_red[kThreads128 / 32];
     const int tid = threadIdx.x;
     const int t = tid % R1, g = tid / R1;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
         tw[i] = make_float2((float)cs, (float)sn);
     }
     __syncthreads();
-    float2 *xb = xb_all + g * 8 * 17;
+    float2 *xb = xb_all + g * kXB128;
     const float invN = 1.0f / (float)N;
     const int units = (XM == XM_LIST) ? a.count : a.J;
     for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
