@@ -31,3 +31,21 @@ def test_spiral_fits_object():
     assert pos.min() >= 0 and pos.max() <= 768
     d = np.hypot(*(pos[1:] - pos[:1]).T)
     assert d.max() <= 384 * np.sqrt(2) + 1
+
+
+def test_batched_configs_follow_the_workload_recipe():
+    """64 datasets, probe sides from {64, 128, 256}, n x n rasters with 7 <= n <= 30 (49-900
+    positions), object sides 256-1024 that hold every patch, same draw for the same seed."""
+    from paper_2608_01746_b300 import synth
+    cfgs = synth.batched_configs()
+    assert len(cfgs) == 64
+    assert {c.N for c in cfgs} == {64, 128, 256}
+    for c in cfgs:
+        assert 7 <= c.n_side <= 30 and 49 <= c.n_pos <= 900
+        assert 256 <= c.M <= 1024 and c.M % 32 == 0
+        assert c.step == c.N // 8 and c.radius == 5.0 * c.N / 16.0
+        assert c.N + (c.n_side - 1) * c.step + 2 * c.jitter <= c.M
+    again = synth.batched_configs()
+    assert [(c.N, c.n_side, c.M) for c in cfgs] == [(c.N, c.n_side, c.M) for c in again]
+    other = synth.batched_configs(seed=7)
+    assert [(c.N, c.n_side) for c in cfgs] != [(c.N, c.n_side) for c in other]
