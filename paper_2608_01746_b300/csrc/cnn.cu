@@ -144,16 +144,22 @@ __global__ void k_bwd_dz(const float *__restrict__ g, const bf16 *__restrict__ y
     }
 }
 
-// db[o] = sum over the batch and pixels of dL/dy * relu'(y): one block per output channel,
-// fixed-order FP32 sums (per thread) then a tree.
+// db[o] = sum over the batch and pixels of dL/dy * relu'(y), in two fixed-order passes: block
+// (o, slice) sums its slice of the B * hout^2 pixels (per-thread FP32 sums, then a tree) into
+// part[o * slices + slice]; k_bias_sum adds the slices in order.  32-bit indices (every
+// activation holds fewer than 2^31 elements).
+constexpr int kBiasSlices = 32;
+
 __global__ void k_bias_grad(const float *__restrict__ g, const bf16 *__restrict__ y, int relu, int B, int cout,
-                            int hout, float *__restrict__ db) {
+                            int hout, int slices, float *__restrict__ part) {
     __shared__ float s[kT];
-    const int o = blockIdx.x;
-    const size_t hw = (size_t)hout * hout;
+    const int o = blockIdx.x, sl = blockIdx.y;
+    const unsigned hw = (unsigned)hout * hout, n = (unsigned)B * hw;
+    const unsigned chunk = (n + slices - 1) / slices, e0 = sl * chunk, e1 = min(n, e0 + chunk);
     float acc = 0.f;
-    for (size_t e = threadIdx.x; e < (size_t)B * hw; e += blockDim.x) {
-        const size_t idx = ((e / hw) * cout + o) * hw + e % hw;
+    for (unsigned e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const unsigned b = e / hw, q = e - b * hw;
+        const unsigned idx = (b * cout + o) * hw + q;
         float d = g[idx];
         if (relu && !(__bfloat162float(y[idx]) > 0.f)) d = 0.f;
         acc += d;
@@ -164,7 +170,15 @@ __global__ void k_bias_grad(const float *__restrict__ g, const bf16 *__restrict_
         if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[o] = s[0];
+    if (threadIdx.x == 0) part[o * slices + sl] = s[0];
+}
+
+__global__ void k_bias_sum(const float *__restrict__ part, int cout, int slices, float *__restrict__ db) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= cout) return;
+    float a = 0.f;
+    for (int sl = 0; sl < slices; ++sl) a += part[o * slices + sl];
+    db[o] = a;
 }
 
 // BF16 copies of the FP32 master weights w[o][k]: wb[o][k] (Coutp x Kp) and wt[k][o] (Kp x Coutp).
@@ -346,6 +360,7 @@ struct wsnet_ctx {
     bf16 *col = nullptr;
     float *cbuf = nullptr, *pred = nullptr, *g0 = nullptr, *g1 = nullptr, *dpred = nullptr;
     float *work = nullptr;                     // split-K partial products of the weight gradients
+    float *bpart = nullptr;                    // bias-gradient slice sums [cout][slices]
     size_t work_floats = 0;
     bf16 *dz = nullptr, *dzt = nullptr;
     double *part = nullptr;
@@ -419,8 +434,13 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
         k_bwd_dz<<<nblk((size_t)Pp * l.Coutp128), kT, 0, n->st>>>(g, l.y, l.relu, B, l.cout, l.hout, Pp, l.Coutp,
                                                                   l.Coutp128, n->dz, n->dzt);
         PM_LAUNCHED("k_bwd_dz");
-        k_bias_grad<<<l.cout, kT, 0, n->st>>>(g, l.y, l.relu, B, l.cout, l.hout, l.gb);
-        PM_LAUNCHED("k_bias_grad");
+        {
+            const int slices = std::max(1, std::min(kBiasSlices, B * l.hout * l.hout / (4 * kT)));
+            k_bias_grad<<<dim3(l.cout, slices), kT, 0, n->st>>>(g, l.y, l.relu, B, l.cout, l.hout, slices, n->bpart);
+            PM_LAUNCHED("k_bias_grad");
+            k_bias_sum<<<(l.cout + kT - 1) / kT, kT, 0, n->st>>>(n->bpart, l.cout, slices, l.gb);
+            PM_LAUNCHED("k_bias_sum");
+        }
         // weight gradient: dW[Coutp128][Kp] = dzt[Coutp128][Pp] . colT[Kp][Pp]^T
         k_im2col<<<dim3(l.Kp, (Pp + kT - 1) / kT), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp,
                                                                    l.Kp, 1, n->col);
@@ -558,6 +578,9 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
         return bail(rc);
     n->work_floats = 64 * max_w;
     if ((rc = nalloc(n, &n->work, n->work_floats))) return bail(rc);
+    int max_cout = 0;
+    for (int i = 0; i < nlayers; ++i) max_cout = std::max(max_cout, cout[i]);
+    if ((rc = nalloc(n, &n->bpart, (size_t)max_cout * kBiasSlices))) return bail(rc);
     cudaError_t e;
     if ((e = cudaMemset(n->status, 0, sizeof(int)))) return bail(pm::cuda_fail(e, "wsnet_create: status"));
     *out = n;
