@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "gemm.h"
@@ -169,6 +170,9 @@ __global__ void k_sum_slices(const float *__restrict__ part, int slices, size_t 
     }
 }
 
+// Devices whose kernel attribute (dynamic shared memory above 48 KB) is set; guarded by g_attr_mu
+// so that host threads making their first call at the same time do not race.
+std::mutex g_attr_mu;
 bool g_attr_set[64] = {};
 
 }  // namespace
@@ -182,9 +186,12 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
     if (M == 0 || N == 0) return PTYCHO_OK;
     int dev = 0;
     PM_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !g_attr_set[dev]) {
-        PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
-        g_attr_set[dev] = true;
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        if (dev >= 64 || !g_attr_set[dev]) {
+            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+            if (dev < 64) g_attr_set[dev] = true;
+        }
     }
     if (K == 0) {
         PM_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
