@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -94,7 +95,7 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def start(self):
@@ -735,55 +736,207 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(n_fuse: int = 8):
-    """Time the FP64 oracle on a bounded sample of the lab workload: fuse ``n_fuse`` positions
-    (the share of one iteration when fusion of all J positions is amortised over 200 iterations)
-    and one full-batch iteration over all 1600 positions.  Returns (seconds, position-updates)."""
+# The FP64 oracle timed on the host cores: as it stands on one core, and with its per-position
+# steps (exit_wave_update, mnf_position) spread over every core by a spawn process pool (the
+# object and probe updates stay in the parent, as the oracle writes them).  Amplitudes and the
+# exit waves go through shared memory; only the object and probe travel with each task.
+_W = {}
+
+
+def _pool_init(a_name, a_shape, psi_name, psi_shape):
+    from multiprocessing import shared_memory
+    _W["a_shm"] = shared_memory.SharedMemory(name=a_name)
+    _W["A"] = np.ndarray(a_shape, dtype=np.float64, buffer=_W["a_shm"].buf)
+    _W["p_shm"] = shared_memory.SharedMemory(name=psi_name)
+    _W["psi"] = np.ndarray(psi_shape, dtype=np.complex128, buffer=_W["p_shm"].buf)
+
+
+def _pool_exit_waves(task):
+    import oracle
+    obj, probe, pos, js = task
+    err = 0.0
+    for j in js:
+        _W["psi"][j], e = oracle.exit_wave_update(obj, probe, pos[j], _W["A"][j])
+        err += e
+    return err
+
+
+def _pool_fuse(task):
+    import oracle
+    raw, times, kw = task
+    p = oracle.FuseParams(**kw)
+    return [oracle.mnf_position(r, times, p) for r in raw]
+
+
+class OraclePool:
+    """A spawn pool of `workers` processes over one scan's amplitudes (None: run in-process)."""
+
+    def __init__(self, A, workers: int):
+        self.workers = workers
+        self.A = A
+        self.pool = None
+        if workers > 1:
+            import multiprocessing as mp
+            from multiprocessing import shared_memory
+            J, N, _ = A.shape
+            self.a_shm = shared_memory.SharedMemory(create=True, size=A.nbytes)
+            np.ndarray(A.shape, dtype=np.float64, buffer=self.a_shm.buf)[:] = A
+            self.p_shm = shared_memory.SharedMemory(create=True, size=J * N * N * 16)
+            self.psi = np.ndarray((J, N, N), dtype=np.complex128, buffer=self.p_shm.buf)
+            self.pool = mp.get_context("spawn").Pool(
+                workers, initializer=_pool_init, initargs=(self.a_shm.name, A.shape, self.p_shm.name, (J, N, N)))
+
+    def iteration(self, obj, probe, pos):
+        """One full-batch iteration, the steps of oracle.iterate_once (object, then probe)."""
+        import oracle
+        if self.pool is None:
+            return oracle.iterate_once(obj, probe, pos, self.A, 1e-3, 1e-3, True)
+        chunks = np.array_split(np.arange(len(pos)), self.workers)
+        err = sum(self.pool.map(_pool_exit_waves, [(obj, probe, pos, c) for c in chunks]))
+        obj = oracle.object_update(obj, probe, pos, self.psi, 1e-3)
+        probe = oracle.probe_update(obj, probe, pos, self.psi, 1e-3)
+        return obj, probe, err
+
+    def fuse(self, raw, times, p):
+        import dataclasses
+        import oracle
+        if self.pool is None:
+            return [oracle.mnf_position(r, times, p) for r in raw]
+        chunks = np.array_split(np.arange(len(raw)), self.workers)
+        kw = dataclasses.asdict(p)
+        out = self.pool.map(_pool_fuse, [(raw[c], times, kw) for c in chunks if len(c)])
+        return [x for part in out for x in part]
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.a_shm.close()
+            self.a_shm.unlink()
+            self.p_shm.close()
+            self.p_shm.unlink()
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def lab_oracle_inputs(n_fuse: int):
     import oracle
     from paper_2608_01746_b300 import synth
-
     cfg = synth.CONFIGS[WORKLOAD]
-    sel = list(range(n_fuse))
-    sc = synth.make_scan(cfg, frames_for=sel)
+    sc = synth.make_scan(cfg, frames_for=list(range(n_fuse)))
+    A = oracle.amplitudes(sc["intensity"])     # fusing all 1600 positions in FP64 takes ~2 min per core
+    return cfg, sc, A
+
+
+def time_lab_sample(cfg, sc, A, workers: int, n_fuse: int):
+    """Per step: fusion of n_fuse positions (the share of one iteration when fusing all J
+    positions is amortised over the 200 iterations: J / 200 = 8) and one full-batch iteration
+    over all positions.  Returns (seconds, position-updates, fusion seconds)."""
+    import oracle
     p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
-    A = oracle.amplitudes(sc["intensity"])     # fusing all 1600 positions in FP64 takes ~15 min
     obj = np.ones((cfg.M, cfg.M), complex)
-    t0 = time.perf_counter()
-    for j in range(n_fuse):
-        oracle.mnf_position(sc["raw"][j], sc["times"], p)
-    oracle.iterate_once(obj, sc["probe"], sc["pos"], A, 1e-3, 1e-3, True)
-    dt = time.perf_counter() - t0
-    return dt, len(sc["pos"])
+    pool = OraclePool(A, workers)
+    try:
+        pool.fuse(sc["raw"][:1], sc["times"], p)              # workers up and warm
+        t0 = time.perf_counter()
+        pool.fuse(sc["raw"][:n_fuse], sc["times"], p)
+        t1 = time.perf_counter()
+        pool.iteration(obj, sc["probe"], sc["pos"])
+        t2 = time.perf_counter()
+    finally:
+        pool.close()
+    return t2 - t0, len(sc["pos"]), t1 - t0
+
+
+def time_small_full(workers: int):
+    """The small workload in full: fusion of all 100 positions and 50 iterations."""
+    import oracle
+    from paper_2608_01746_b300 import synth
+    cfg = synth.CONFIGS["small"]
+    sc = synth.make_scan(cfg)
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    pool = OraclePool(np.zeros((len(sc["pos"]), cfg.N, cfg.N)), workers)
+    try:
+        pool.fuse(sc["raw"][:1], sc["times"], p)
+        t0 = time.perf_counter()
+        fused = np.stack(pool.fuse(sc["raw"], sc["times"], p))
+        A = oracle.amplitudes(fused)
+        if pool.pool is not None:
+            np.ndarray(A.shape, dtype=np.float64, buffer=pool.a_shm.buf)[:] = A
+        pool.A = A
+        t1 = time.perf_counter()
+        obj, probe = np.ones((cfg.M, cfg.M), complex), sc["probe"].astype(complex)
+        for _ in range(cfg.n_iter):
+            obj, probe, _e = pool.iteration(obj, probe, sc["pos"])
+        t2 = time.perf_counter()
+    finally:
+        pool.close()
+    return {"seconds": round(t2 - t0, 2), "fusion_seconds": round(t1 - t0, 3),
+            "position_updates_per_s": round(len(sc["pos"]) * cfg.n_iter / (t2 - t0), 1)}
 
 
 def cpu_baseline():
-    dt, upd = oracle_sample()
-    return {"value": round(upd / dt, 2), "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "FP64 numpy oracle: fusion of 8 positions + one full-batch iteration over all "
-                      "1600 positions of the lab scan (numpy FFT, single thread)",
-            "seconds": round(dt, 2)}
+    """The oracle on one core and on every host core (bounded samples; ~30 s in all)."""
+    cores = os.cpu_count() or 1
+    n_fuse = 8
+    cfg, sc, A = lab_oracle_inputs(max(n_fuse, 8 * cores))
+    s1, upd, f1 = time_lab_sample(cfg, sc, A, 1, n_fuse)
+    sn, _, _ = time_lab_sample(cfg, sc, A, cores, n_fuse)
+    # fusion alone, positions per second (lab frames: 5 x 256^2, 6 levels)
+    import oracle
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    pool = OraclePool(A[:1], cores)
+    try:
+        pool.fuse(sc["raw"][:1], sc["times"], p)
+        t0 = time.perf_counter()
+        pool.fuse(sc["raw"][:8 * cores], sc["times"], p)
+        fn = time.perf_counter() - t0
+    finally:
+        pool.close()
+    return {"value": round(upd / sn, 2), "unit": METRIC, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"FP64 numpy oracle on all {cores} host cores (spawn pool over positions): fusion of "
+                       f"{n_fuse} positions + one full-batch iteration over all {upd} positions of the lab scan"),
+            "seconds": round(sn, 2),
+            "single_core": {"value": round(upd / s1, 2), "seconds": round(s1, 2)},
+            "fusion_positions_per_s": {"1_core": round(n_fuse / f1, 2), f"{cores}_cores": round(8 * cores / fn, 2)},
+            "small_workload_in_full": {"workload": "small scan: fusion of 100 positions + 50 iterations",
+                                       "1_core": time_small_full(1), f"{cores}_cores": time_small_full(cores)}}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    cores = os.cpu_count() or 1
+    n_fuse = 8
+    cfg, sc, A = lab_oracle_inputs(n_fuse)
     for _ in range(args.warmup):
-        oracle_sample(n_fuse=1)
+        time_lab_sample(cfg, sc, A, cores, 1)
     total = 0.0
     upd = 0
     for _ in range(args.steps):
-        dt, u = oracle_sample()
+        dt, u, _f = time_lab_sample(cfg, sc, A, cores, n_fuse)
         total += dt
         upd += u
     value = upd / total
+    sample = (f"per step: fusion of {n_fuse} positions + one full-batch iteration over all 1600 positions, "
+              f"FP64 numpy oracle on all {cores} host cores")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": METRIC,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "lab-scale sample: fuse 8 positions + 1 iteration over 1600 positions "
                                    "(object 1024x1024, probe 256x256, 5 exposures, 6 levels)"},
-            "cpu_baseline": {"value": round(value, 2), "kind": "oracle", "cores": 1,
-                             "sample": "per step: fusion of 8 positions + one full-batch iteration"},
+            "cpu_baseline": {"value": round(value, 2), "kind": "oracle", "cores": cores, "cpu_model": cpu_model(),
+                             "sample": sample},
             "e2e": {"value": round(value, 2), "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

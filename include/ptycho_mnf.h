@@ -84,8 +84,10 @@ int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
  *   - Positions are processed in chunks that fit the array; a configuration whose single
  *     position needs more than 16 MiB of scratch (about 4 (2K + 1) N^2 / 3 bytes) is rejected
  *     with PTYCHO_EINVAL and a message naming the sizes.
- *   - The first call on a device (with that device current) looks up the array's device
- *     address; make that first call before any stream capture.
+ *   - A call on a stream that is not being captured looks up the array's device address for
+ *     the current device (and context); a captured call reuses the address found by the
+ *     device's last uncaptured call.  So make one uncaptured call on a device before any
+ *     stream capture, and again after a cudaDeviceReset (which invalidates the address).
  *   - All calls share the array: calls whose work may overlap on the GPU (different streams,
  *     other host threads) race on it and must be serialised by the caller.
  */
@@ -180,8 +182,9 @@ int ptycho_init(ptycho_handle *out, const ptycho_desc *d);
  * over modes and each mode gets its own least-squares probe update.
  *   h_err  host [n_iter] or NULL: per-iteration Fourier error
  *          sum_j sum_q (|Psi_j| - A_j)^2 / sum_j sum_q A_j^2 measured before each projection.
- * With h_err the call synchronises and returns PTYCHO_ENONFINITE if any error is NaN/Inf;
- * without it the call is asynchronous.
+ * With h_err the call synchronises and returns PTYCHO_ENONFINITE if any error is NaN/Inf, or
+ * PTYCHO_ETIMEDOUT if a bounded device wait of an exit-wave kernel gave up (that status stays
+ * set for the life of the handle); without it the call is asynchronous.
  */
 int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err);
 
@@ -218,15 +221,17 @@ int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches 
  *                        candidate launch shapes (persistent grid sizes; rows per TMA stage at
  *                        N = 256) on the datasets themselves, keeps the fastest and restores
  *                        every object and probe (results are unaffected).  The handles stay
- *                        owned by the caller, must outlive the batch, and must not be iterated
- *                        while a batch call is in flight.  The batch runs on a stream of its
+ *                        owned by the caller, must outlive the batch, belong to one batch at a
+ *                        time, and must not be iterated while a batch call is in flight
+ *                        (ptycho_iterate between batch calls is fine).  The batch runs on a stream of its
  *                        own, ordered after `cuda_stream` and the handles' streams at each
  *                        call and before their later work.  Synchronises `cuda_stream`.
  *   ptycho_batch_iterate n_iter iterations of every dataset, the same arithmetic as
  *                        ptycho_iterate on each handle.  h_err: host [n] or NULL, each dataset's
  *                        Fourier error of the last iteration (then the call synchronises and
- *                        reports PTYCHO_ENONFINITE / PTYCHO_ETIMEDOUT).  Later calls on a handle
- *                        are ordered after the batch's work.
+ *                        reports PTYCHO_ENONFINITE, or PTYCHO_ETIMEDOUT if a bounded wait of any
+ *                        dataset's kernels gave up).  Later calls on a handle are ordered after
+ *                        the batch's work.
  *   ptycho_batch_describe  the autotuner's choices and timings as a JSON object text.
  */
 typedef struct ptycho_batch_ctx *ptycho_batch;
@@ -238,6 +243,22 @@ void ptycho_batch_destroy(ptycho_batch b);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *ptycho_last_error(void);
+
+/*
+ * Test hooks for the failure paths (no counterpart in the paper; for the library's own tests).
+ *   ptycho_debug_wait_timeout  enable != 0: every later exit-wave launch of the handle first
+ *       waits, with a limit of about 2^20 SM cycles, on a barrier that nothing arrives on, before
+ *       it issues any copy; the wait gives up, the kernel sets the handle's status word and
+ *       returns, and ptycho_iterate with h_err reports PTYCHO_ETIMEDOUT.  The device context stays
+ *       usable.  The status word is sticky: the handle keeps reporting the timeout, so destroy
+ *       it.  Handles whose exit-wave kernel has no bounded waits (N != 256) get PTYCHO_EINVAL.
+ *   ptycho_debug_fail_alloc  nth > 0: the nth device allocation the library makes from now on
+ *       (any entry point, any thread) fails as if the device were out of memory, and the call
+ *       that made it returns PTYCHO_ENOMEM after releasing what it had allocated; nth = 0
+ *       switches the hook off.  Process-wide.
+ */
+int ptycho_debug_wait_timeout(ptycho_handle h, int enable);
+int ptycho_debug_fail_alloc(int nth);
 
 #ifdef __cplusplus
 }

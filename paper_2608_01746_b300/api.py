@@ -129,6 +129,14 @@ def lib() -> ctypes.CDLL:
     L.ptycho_stage_times.restype = ci
     L.ptycho_last_error.argtypes = []
     L.ptycho_last_error.restype = ctypes.c_char_p
+    L.ptycho_debug_wait_timeout.argtypes = [vp, ci]
+    L.ptycho_debug_wait_timeout.restype = ci
+    L.ptycho_debug_fail_alloc.argtypes = [ci]
+    L.ptycho_debug_fail_alloc.restype = ci
+    L.measure_fp32_fma.argtypes = [ci, ci, vp, ctypes.POINTER(cd), vp]
+    L.measure_fp32_fma.restype = ci
+    L.measure_fma_threads_per_block.argtypes = []
+    L.measure_fma_threads_per_block.restype = ci
     _LIB = L
     return L
 
@@ -322,6 +330,40 @@ def ptycho_get_colouring(h: PtychoHandle):
 
 def ptycho_destroy(h: PtychoHandle) -> None:
     h.close()
+
+
+def ptycho_debug_wait_timeout(h: PtychoHandle, enable: bool) -> None:
+    """Test hook: the handle's exit-wave launches first wait on a barrier nothing arrives on."""
+    _check(lib().ptycho_debug_wait_timeout(h.ptr, int(bool(enable))))
+
+
+def ptycho_debug_fail_alloc(nth: int) -> None:
+    """Test hook: the nth device allocation of the library from now on fails (0 = off)."""
+    _check(lib().ptycho_debug_fail_alloc(int(nth)))
+
+
+def measure_fp32_fma_tflops(blocks_per_sm: int = 8, iters: int = 4096, reps: int = 5, device=None) -> dict:
+    """The device's FP32 FMA rate: the best of ``reps`` timed launches of the library's FMA
+    kernel (CUDA events on the current stream, after one warm-up launch)."""
+    import torch
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = blocks_per_sm * sms
+    sink = torch.empty(blocks * lib().measure_fma_threads_per_block(), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    flops = ctypes.c_double()
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib().measure_fp32_fma(blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flops),
+                                      ctypes.c_void_p(st.cuda_stream)))
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if r > 0 and (best is None or ms < best):
+            best = ms
+    return {"tflops": flops.value / (best / 1e3) / 1e12, "ms": best, "blocks": blocks, "iters": iters}
 
 
 def ptycho_set_timing(h: PtychoHandle, enable: bool) -> None:

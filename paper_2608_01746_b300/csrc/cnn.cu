@@ -375,7 +375,7 @@ namespace {
 template <typename T>
 int nalloc(wsnet_ctx *n, T **p, size_t count) {
     *p = nullptr;
-    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = pm::dev_malloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) return pm::cuda_fail(e, "wsnet: cudaMalloc");
     n->allocs.push_back(*p);
     return PTYCHO_OK;
@@ -669,22 +669,21 @@ extern "C" int ws_stitch(const float *d_pred, const int32_t *d_pos, int J, const
     if (!d_pred || !d_pos || !d_probe || !d_obj) return pm::fail(PTYCHO_EINVAL, "ws_stitch: NULL pointer");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int n = N / 4, Mc = M / 4;
-    float *wgt = nullptr, *den = nullptr, *dmax = nullptr;
-    float2 *num = nullptr;
-    PM_CUDA(cudaMallocAsync((void **)&wgt, (size_t)n * n * sizeof(float), st));
-    PM_CUDA(cudaMallocAsync((void **)&den, (size_t)Mc * Mc * sizeof(float), st));
-    PM_CUDA(cudaMallocAsync((void **)&num, (size_t)Mc * Mc * sizeof(float2), st));
-    PM_CUDA(cudaMallocAsync((void **)&dmax, sizeof(float), st));
+    // one scratch block: num (float2, Mc^2) | den (Mc^2) | wgt (n^2) | dmax (1)
+    void *blk = nullptr;
+    const size_t MMc = (size_t)Mc * Mc;
+    PM_CUDA(pm::dev_malloc_async(&blk, MMc * sizeof(float2) + (MMc + (size_t)n * n + 1) * sizeof(float), st));
+    float2 *num = static_cast<float2 *>(blk);
+    float *den = reinterpret_cast<float *>(num + MMc);
+    float *wgt = den + MMc;
+    float *dmax = wgt + (size_t)n * n;
     k_coarse_weights<<<nblk((size_t)n * n), kT, 0, st>>>(static_cast<const float2 *>(d_probe), N, wgt);
     k_stitch_coarse<<<nblk((size_t)Mc * Mc), kT, 0, st>>>(d_pred, reinterpret_cast<const int2 *>(d_pos), J, n, wgt,
                                                          Mc, num, den);
     k_max_reduce<<<1, kT, 0, st>>>(den, Mc * Mc, dmax);
     k_stitch_upsample<<<nblk((size_t)M * M), kT, 0, st>>>(num, den, dmax, Mc, M, static_cast<float2 *>(d_obj));
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(wgt, st);
-    cudaFreeAsync(den, st);
-    cudaFreeAsync(num, st);
-    cudaFreeAsync(dmax, st);
+    cudaFreeAsync(blk, st);
     if (e != cudaSuccess) return pm::cuda_fail(e, "ws_stitch");
     return PTYCHO_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "ptycho_mnf.h"
@@ -13,6 +14,19 @@ int fail(int code, const char *fmt, ...);
 // Records a CUDA failure ("<what>: <cuda error string>") and returns PTYCHO_ECUDA, or
 // PTYCHO_ENOMEM for cudaErrorMemoryAllocation.
 int cuda_fail(cudaError_t e, const char *what);
+// Every device allocation of the library goes through these two (cudaMalloc / cudaMallocAsync),
+// so that ptycho_debug_fail_alloc can make the n-th one report cudaErrorMemoryAllocation.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+
+// NVTX range for the host-side extent of one stage (visible in Nsight timelines; a no-op
+// unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace pm
 

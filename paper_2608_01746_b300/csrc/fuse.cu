@@ -405,6 +405,7 @@ int fuse_dispatch(const uint16_t *d_raw, int J, int K, int N, const FuseDev &f, 
 
 extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
                           const fuse_params *p, float *d_fused, void *cuda_stream) {
+    pm::NvtxRange range("fuse_stack");
     FuseDev f;
     int rc = pm::validate_fuse(d_raw, J, K, N, h_t, p, d_fused, &f);
     if (rc != PTYCHO_OK || J == 0) return rc;
@@ -416,7 +417,7 @@ extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const floa
     if (per_pos > 0) chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)J, cap_floats / per_pos));
     chunk = std::min(chunk, 65535 / K);           // grid.z of the reduce kernels is J * K
     float *scratch = nullptr;
-    if (per_pos > 0) PM_CUDA(cudaMallocAsync((void **)&scratch, per_pos * chunk * sizeof(float), st));
+    if (per_pos > 0) PM_CUDA(pm::dev_malloc_async((void **)&scratch, per_pos * chunk * sizeof(float), st));
     const size_t NN = (size_t)N * N;
     for (int j0 = 0; j0 < J && rc == PTYCHO_OK; j0 += chunk) {
         const int jn = std::min(chunk, J - j0);
@@ -440,11 +441,14 @@ extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const floa
 //
 // The array below is part of the library image: every GPU that loads the library holds it
 // until the process exits.  Its host-side name is only a stand-in for the symbol, so the
-// device address is looked up with cudaGetSymbolAddress, once per device, on the first call
-// made with that device current; that first call should therefore happen before any stream
-// capture.  All calls share the array and it keeps the previous call's contents (every element
-// a call reads is written by that call first, so nothing needs clearing); calls whose work
-// overlaps on the GPU race on it.
+// device address is looked up with cudaGetSymbolAddress with the device current.  A call on a
+// stream that is not being captured looks it up again (the address belongs to the device's
+// current context, which cudaDeviceReset replaces); a call on a capturing stream uses the
+// address the device's last uncaptured call found, so the first call on a device should
+// happen before any stream capture, and none should be captured across a cudaDeviceReset.
+// All calls share the array and it keeps the previous call's contents (every element a call
+// reads is written by that call first, so nothing needs clearing); calls whose work overlaps
+// on the GPU race on it.
 namespace {
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
 constexpr int kMaxDevices = 64;
@@ -452,18 +456,23 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float g_fuse_scratch[kNoAllocScratchBytes / sizeof(float)];
 
-static int noalloc_scratch(float **out) {
+static int noalloc_scratch(float **out, cudaStream_t st) {
     static std::mutex mu;
     static float *by_device[kMaxDevices] = {};
     int dev = 0;
     PM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return pm::fail(PTYCHO_EINVAL, "fuse_stack_noalloc: device %d unsupported", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PM_CUDA(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(mu);
-    if (!by_device[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_fuse_scratch);
         if (e != cudaSuccess) return pm::cuda_fail(e, "cudaGetSymbolAddress(fusion scratch)");
         by_device[dev] = (float *)p;
+    } else if (!by_device[dev]) {
+        return pm::fail(PTYCHO_EINVAL, "fuse_stack_noalloc: the first call on device %d is being captured; "
+                                       "make one uncaptured call on the device first", dev);
     }
     *out = by_device[dev];
     return PTYCHO_OK;
@@ -483,11 +492,11 @@ extern "C" int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, co
                         per_pos * sizeof(float), N, K, f.L, kNoAllocScratchBytes);
     if (J == 0) return PTYCHO_OK;
     float *scratch = nullptr;
-    if (per_pos > 0 && (rc = noalloc_scratch(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (per_pos > 0 && (rc = noalloc_scratch(&scratch, st))) return rc;
     int chunk = per_pos > 0 ? (int)std::min<size_t>((size_t)J, cap / per_pos) : J;
     chunk = std::max(1, std::min(chunk, 65535 / K));
     const size_t NN = (size_t)N * N;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     for (int j0 = 0; j0 < J && rc == PTYCHO_OK; j0 += chunk) {
         const int jn = std::min(chunk, J - j0);
         rc = pm::fuse_dispatch(d_raw + (size_t)j0 * K * NN, jn, K, N, f, d_fused + (size_t)j0 * NN, scratch, st);

@@ -1,13 +1,17 @@
 // Iterative ptychographic reconstruction on one GPU (§3.3 forward model, Eqs. 2-3).
 //
 // One iteration (full-batch alternating projections):
-//   k_exit_wave    per position j (one thread-block cluster at a time, persistent grid):
+//   exit waves     per position j (persistent grids):
 //                  psi = P * O_j  ->  row FFTs  ->  column FFTs, modulus replacement against
 //                  A_j and Fourier error, inverse column FFTs  ->  inverse row FFTs  ->  psi_j'
-//                  The N x N intermediate stays in the cluster's distributed shared memory
-//                  (a 256 x 256 complex64 tile is 512 KB: 8 CTAs x 64 KB); FFTs are
-//                  register/shared-memory radix passes (fft.cuh).
-//   k_object_gather  owner-computes object update: each 32 x 32 object tile sums
+//                  k_exit_wave<R> (N = 16, 64): one CTA per position, the whole N x N tile
+//                  in shared memory.  k_exit_wave128 (N = 128): one CTA per position, groups of
+//                  8 threads with 16 elements each, the tile in shared memory.
+//                  k_exit_wave_tma (N = 256): the 512 KB tile does not fit one SM, so each
+//                  CTA streams it through a private slot in global memory (L2) with TMA bulk
+//                  tensor copies, rows and columns in batches of 16 or 32 (fft.cuh radix-16
+//                  group transforms in registers and shared memory).
+//   k_object_gather  owner-computes object update: each 8 x 32 object tile sums
 //                  conj(P) psi_j' and |P|^2 over the positions whose patch covers it, in
 //                  ascending j (deterministic, no atomics).
 //   k_apply        O = num / (den + alpha_O max den) on pixels inside some scan patch.
@@ -383,6 +387,7 @@ struct TmaArgs {
     const int *list;         // XM_FULL: if not NULL, process positions list[0 .. count)
     int count;
     int M, J, Q;
+    int inject_wait;         // test hook: wait on a barrier nothing arrives on (short limit) first
 };
 
 struct TmaMaps {
@@ -431,14 +436,22 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     }
     __syncthreads();
     uint32_t parity = 0u;                                        // bit s: phase parity of bar[s]
+    __shared__ uint32_t s_pending;                               // thread 0: bit s = a load into stage s is in flight
+    if (tid == 0) s_pending = 0u;
     const int slot_col = blockIdx.x * N;                         // this CTA's slot columns
     const float invN = 1.0f / (float)N;
     const int M = a.M;
     bool failed = false;                                         // uniform after each barrier
     bool timed_out = false;                                      // this thread's waits
+    // After a wait gives up the kernel leaves its loop before waiting again, so the parity of
+    // a stage whose wait failed stays that of the load still in flight (drained at the end).
     auto wait_stage = [&](int s) {
-        if (!T::mbar_wait(&bar[s], (parity >> s) & 1u)) timed_out = true;
-        parity ^= 1u << s;
+        if (T::mbar_wait(&bar[s], (parity >> s) & 1u)) {
+            if (tid == 0) s_pending &= ~(1u << s);
+            parity ^= 1u << s;
+        } else {
+            timed_out = true;
+        }
     };
     // Barrier A of every batch: the batch's input buffer is consumed, the staging buffer's
     // previous store has finished reading it (thread 0 waited just before), and a timed-out
@@ -459,6 +472,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     };
     auto prefetch = [&](int s, const CUtensorMap *map, int x, int y) {
         if (tid == 0) {
+            s_pending |= 1u << s;
             T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
             T::load_2d(bin(s), map, x, y, &bar[s]);
         }
@@ -466,6 +480,16 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
 
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
+    if (a.inject_wait) {
+        // Test hook (ptycho_debug_wait_timeout): a wait on a barrier that nothing arrives on,
+        // limited to ~2^20 cycles, before any copy is issued; the CTA then takes the timeout path.
+        if (tid == 0) {
+            T::mbar_init(&bar[2], 1);
+            T::fence_barrier_init();
+            if (!T::mbar_wait_for(&bar[2], 0u, 1ll << 20)) timed_out = true;
+        }
+        if (__syncthreads_or(timed_out)) failed = true;
+    }
     for (int iu = blockIdx.x; iu < units && !failed; iu += gridDim.x) {
         const int u = (XM == XM_LIST) ? a.list[iu] : iu;
         const int j = kFull ? u : u / a.Q;
@@ -558,6 +582,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         // ---- phase C (XM_INV): inverse column FFTs of psi[j][m] in place
         auto load_psi_cols = [&](int s, int c0) {
             if (tid == 0) {
+                s_pending |= 1u << s;
                 T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
                 T::load_2d(bin(s), &tm.psi_c, c0, u * N, &bar[s]);
                 if constexpr (B == 32) T::load_2d(bin(s) + 4096, &tm.psi_c, c0 + 16, u * N, &bar[s]);
@@ -624,6 +649,11 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
         __syncthreads();
     }
     if (tid == 0) {
+        // After a timeout: let every load still in flight land (bounded) before the CTA's
+        // shared memory is released, then drain the bulk stores.
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (failed && ((s_pending >> s) & 1u)) T::mbar_wait(&bar[s], (parity >> s) & 1u);
         T::wait_all<0>();
         if (failed) atomicExch(a.status, 1);
     }
@@ -984,10 +1014,14 @@ struct ptycho_ctx {
     float *d_tile_max = nullptr, *d_pmax = nullptr;
     double *d_err_pos = nullptr, *d_a2 = nullptr, *d_inv_norm = nullptr, *d_err = nullptr;
     int err_cap = 0;
+    // Error slot of batch iterations: allocated once at init and never replaced, so a captured
+    // batch graph may keep its address while ptycho_iterate grows d_err.
+    double *d_err_batch = nullptr;
     int *d_tstart = nullptr, *d_torder = nullptr;
     int4 *d_tlist = nullptr;                              // tile lists: (j, y, x, 0)
     int ntx = 0, ntiles = 0;
     int *d_status = nullptr;
+    int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout
     TmaMaps tm;
     bool exit_tma = false;
     bool fft_gemm = false;                                // split-BF16 tensor-core DFTs (N = 64)
@@ -1008,7 +1042,7 @@ template <typename T>
 int dalloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    cudaError_t e = pm::dev_malloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) return pm::cuda_fail(e, "cudaMalloc");
     return PTYCHO_OK;
 }
@@ -1018,7 +1052,7 @@ void free_ctx(ptycho_ctx *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
-                    h->d_a2, h->d_inv_norm, h->d_err, h->d_tstart, h->d_tlist, h->d_status, h->d_torder,
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder,
                     h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1130,6 +1164,7 @@ TmaArgs tma_args(ptycho_ctx *h) {
     a.M = h->M;
     a.J = h->J;
     a.Q = h->Q;
+    a.inject_wait = h->inject_wait;
     return a;
 }
 
@@ -1272,14 +1307,19 @@ int launch_exit_any(ptycho_ctx *h, int *launches) {
     return launch_exit_pass(h, XM_INV);
 }
 
+// Stage s of an iteration: an NVTX range around its launches, and CUDA events when timing.
+const char *const kStageNames[ST_COUNT] = {"ptycho: exit waves", "ptycho: object update", "ptycho: probe update",
+                                           "ptycho: error"};
+
 int stage_begin(ptycho_ctx *h, int s, size_t idx) {
+    nvtxRangePushA(kStageNames[s]);
     if (!h->timing) return PTYCHO_OK;
-    (void)s;
     PM_CUDA(cudaEventRecord(h->ev[2 * idx], h->st));
     return PTYCHO_OK;
 }
 
 int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
+    nvtxRangePop();
     if (!h->timing) return PTYCHO_OK;
     PM_CUDA(cudaEventRecord(h->ev[2 * idx + 1], h->st));
     h->stage_launches[s] += launches;
@@ -1289,7 +1329,7 @@ int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
 // ePIE by colour: colours in ascending order; per colour the fused exit-wave kernel on the
 // colour's positions, the object step (disjoint patches, no atomics) and the averaged probe
 // step.  The whole colour loop is timed as stage 0.
-int iterate_one_epie(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe) {
+int iterate_one_epie(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_probe) {
     int rc;
     if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
     const size_t NN = (size_t)h->N * h->N;
@@ -1320,14 +1360,15 @@ int iterate_one_epie(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool u
         if ((rc = stage_end(h, st, ev_base + st, 0))) return rc;
     }
     if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
-    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, h->d_err + it_in_call);
+    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, err_dst);
     PM_LAUNCHED("k_error_reduce");
     return stage_end(h, ST_ERROR, ev_base + 3, 1);
 }
 
-// exit_done: the exit waves of this iteration were already computed by a multi-dataset launch.
-int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update_probe, bool exit_done = false) {
-    if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) return iterate_one_epie(h, it_in_call, ev_base, update_probe);
+// err_dst: device slot of this iteration's Fourier error.  exit_done: the exit waves of this
+// iteration were already computed by a multi-dataset launch.
+int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_probe, bool exit_done = false) {
+    if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) return iterate_one_epie(h, err_dst, ev_base, update_probe);
     int rc;
     // exit waves
     if (!exit_done) {
@@ -1375,7 +1416,7 @@ int iterate_one(ptycho_ctx *h, long long it_in_call, size_t ev_base, bool update
     if ((rc = stage_end(h, ST_PROBE, ev_base + 2, update_probe ? 3 : 0))) return rc;
     // error
     if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
-    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, h->d_err + it_in_call);
+    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, err_dst);
     PM_LAUNCHED("k_error_reduce");
     if ((rc = stage_end(h, ST_ERROR, ev_base + 3, 1))) return rc;
     return PTYCHO_OK;
@@ -1392,6 +1433,7 @@ int copy_in_complex(float2 *dst, const void *src, size_t count, bool on_device, 
 extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!out) return pm::fail(PTYCHO_EINVAL, "ptycho_init: out is NULL");
     *out = nullptr;
+    pm::NvtxRange range("ptycho_init");
     if (!d) return pm::fail(PTYCHO_EINVAL, "ptycho_init: desc is NULL");
     int R = 0;
     if (d->N == 16) R = 4;
@@ -1517,6 +1559,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_err_pos, (size_t)J);
     if (!rc) rc = dalloc(&h->d_a2, J);
     if (!rc) rc = dalloc(&h->d_inv_norm, 1);
+    if (!rc) rc = dalloc(&h->d_err_batch, 1);
     if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
     if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
     if (!rc) rc = dalloc(&h->d_torder, (size_t)h->ntiles);
@@ -1557,6 +1600,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
 }
 
 extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
+    pm::NvtxRange range("ptycho_iterate");
     if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_iterate: NULL handle");
     if (n_iter < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_iterate: n_iter = %d < 0", n_iter);
     if (n_iter == 0) return PTYCHO_OK;
@@ -1580,7 +1624,7 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
     }
     for (int i = 0; i < n_iter; ++i) {
         const bool upd = h->iter >= h->probe_update_start;
-        int rc = iterate_one(h, i, (size_t)i * ST_COUNT, upd);
+        int rc = iterate_one(h, h->d_err + i, (size_t)i * ST_COUNT, upd);
         if (rc) return rc;
         ++h->iter;
     }
@@ -1637,6 +1681,15 @@ extern "C" int ptycho_set_timing(ptycho_handle h, int enable) {
 extern "C" int ptycho_stage_times(ptycho_handle h, double *ms, long long *launches) {
     if (!h || !ms || !launches) return pm::fail(PTYCHO_EINVAL, "ptycho_stage_times: NULL argument");
     for (int s = 0; s < ST_COUNT; ++s) { ms[s] = h->stage_ms[s]; launches[s] = h->stage_launches[s]; }
+    return PTYCHO_OK;
+}
+
+extern "C" int ptycho_debug_wait_timeout(ptycho_handle h, int enable) {
+    if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: NULL handle");
+    if (!h->exit_tma || h->fft_gemm)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: the handle's exit-wave kernel (N = %d) has no "
+                                       "bounded waits to exercise; the hook needs N = 256", h->N);
+    h->inject_wait = enable != 0;
     return PTYCHO_OK;
 }
 
@@ -1743,9 +1796,12 @@ int enqueue_iteration(ptycho_batch_ctx *b, const std::vector<char> &upd) {
         const int c = b->cls_of[i];
         if (c >= 0) PM_CUDA(cudaStreamWaitEvent(s, b->ev_cls[c], 0));
         cudaStream_t saved = h->st;
+        const bool timing = h->timing;                 // no per-stage events inside a batch
         h->st = s;
-        const int rc = iterate_one(h, 0, 0, upd[i] != 0, c >= 0);
+        h->timing = false;
+        const int rc = iterate_one(h, h->d_err_batch, 0, upd[i] != 0, c >= 0);
         h->st = saved;
+        h->timing = timing;
         if (rc) return rc;
         PM_CUDA(cudaEventRecord(b->ev_join[i], s));
         PM_CUDA(cudaStreamWaitEvent(b->st, b->ev_join[i], 0));
@@ -2072,12 +2128,6 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
         if ((e = cudaMemcpy(c.d_start, start.data(), (nm + 1) * sizeof(int), cudaMemcpyHostToDevice)))
             return bail(pm::cuda_fail(e, "copy dataset prefix"));
     }
-    // every dataset's error slot for the batch's iterations
-    for (ptycho_ctx *h : b->hs)
-        if (h->err_cap < 1) {
-            if ((rc = dalloc(&h->d_err, 1))) return bail(rc);
-            h->err_cap = 1;
-        }
     b->side.assign(n, nullptr);
     b->ev_join.assign(n, nullptr);
     b->ev_in.assign(n, nullptr);
@@ -2113,6 +2163,7 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
 }
 
 extern "C" int ptycho_batch_iterate(ptycho_batch b, int n_iter, double *h_err) {
+    pm::NvtxRange range("ptycho_batch_iterate");
     if (!b) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_iterate: NULL batch");
     if (n_iter < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_iterate: n_iter = %d < 0", n_iter);
     if (n_iter == 0) return PTYCHO_OK;
@@ -2128,12 +2179,19 @@ extern "C" int ptycho_batch_iterate(ptycho_batch b, int n_iter, double *h_err) {
     PM_CUDA(cudaStreamWaitEvent(b->user_st, b->ev_done, 0));
     for (ptycho_ctx *h : b->hs) PM_CUDA(cudaStreamWaitEvent(h->st, b->ev_done, 0));
     if (h_err) {
-        int status = 0;
-        for (size_t i = 0; i < b->hs.size(); ++i)
-            PM_CUDA(cudaMemcpyAsync(h_err + i, b->hs[i]->d_err, sizeof(double), cudaMemcpyDeviceToHost, b->st));
-        PM_CUDA(cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+        // status words: the batch's own (shared launches) and every member's (kernels on the
+        // member's branch write the handle's word)
+        std::vector<int> status(b->hs.size() + 1, 0);
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            PM_CUDA(cudaMemcpyAsync(h_err + i, b->hs[i]->d_err_batch, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+            PM_CUDA(cudaMemcpyAsync(&status[i], b->hs[i]->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+        }
+        PM_CUDA(cudaMemcpyAsync(&status[b->hs.size()], b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st));
         PM_CUDA(cudaStreamSynchronize(b->st));
-        if (status) return pm::fail(PTYCHO_ETIMEDOUT, "ptycho_batch_iterate: a bounded device wait gave up");
+        for (size_t i = 0; i <= b->hs.size(); ++i)
+            if (status[i])
+                return pm::fail(PTYCHO_ETIMEDOUT, "ptycho_batch_iterate: a bounded device wait gave up (%s)",
+                                i < b->hs.size() ? "a dataset's own kernels" : "a shared multi-dataset launch");
         for (size_t i = 0; i < b->hs.size(); ++i)
             if (!std::isfinite(h_err[i]))
                 return pm::fail(PTYCHO_ENONFINITE, "ptycho_batch_iterate: error of dataset %zu is not finite", i);

@@ -42,14 +42,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete, giving up after `max_cycles` SM
+// cycles (or 2^26 polls); returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, long long max_cycles) {
     const long long start = clock64();
     for (uint32_t i = 0; i < (1u << 26); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - start > (1ll << 31)) break;
+        if (clock64() - start > max_cycles) break;
     }
     return false;
+}
+
+// Bounded wait for the phase with the given parity to complete (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, 1ll << 31);
 }
 
 // 2-D tiled load of the box at coordinates (x inner, y outer) into shared memory; completes

@@ -112,3 +112,78 @@ def test_batch_rejects_epie_and_duplicates(api, inputs):
         api.ptycho_batch_create([h2, h2])
     api.ptycho_destroy(h)
     api.ptycho_destroy(h2)
+
+
+def test_batch_graph_survives_handle_iterations(api, inputs):
+    """A captured batch iteration keeps working after the handles are iterated on their own in
+    between (ptycho_iterate with more iterations than before grows its own error buffer; the
+    graph must not depend on it): batch 2, alone 4, batch 3 == alone 2 + 4 + 3."""
+    ref_h = _handles(api, inputs)
+    for h in ref_h:
+        api.ptycho_iterate(h, 2)
+        api.ptycho_iterate(h, 4)
+    ref_err = np.array([api.ptycho_iterate(h, 3)[-1] for h in ref_h])
+    ref = [(api.ptycho_get_object(h), api.ptycho_get_probe(h)) for h in ref_h]
+    for h in ref_h:
+        api.ptycho_destroy(h)
+    hs = _handles(api, inputs)
+    b = api.ptycho_batch_create(hs, graph=True)
+    api.ptycho_batch_iterate(b, 2)
+    for h in hs:
+        api.ptycho_iterate(h, 4)
+    err = api.ptycho_batch_iterate(b, 3)
+    for i, h in enumerate(hs):
+        assert np.array_equal(api.ptycho_get_object(h), ref[i][0]), DATASETS[i]
+        assert np.array_equal(api.ptycho_get_probe(h), ref[i][1]), DATASETS[i]
+    np.testing.assert_array_equal(err, ref_err)
+    api.ptycho_batch_destroy(b)
+    for h in hs:
+        api.ptycho_destroy(h)
+
+
+# One dataset of every exit-wave class, fused by the oracle: (config, fft path, probe_update_start,
+# tolerance on object and probe after 2 + 3 iterations).  The split-BF16 form is held to its own
+# bound, 12 x 2^-16 per iteration (see test_gpu_dftgemm.py).
+ORACLE_DATASETS = [("tiny", "radix_fp32", 0, 1e-5), ("small", "radix_fp32", 3, 1e-5),
+                   ("small", "dftgemm_bf16x3", 0, 5 * 12 * 2.0 ** -16), ("mid128", "radix_fp32", 3, 1e-5),
+                   ("mid128", "dftgemm_bf16x3", 0, 5 * 12 * 2.0 ** -16), ("lab12", "radix_fp32", 0, 1e-5)]
+
+
+def test_batch_classes_match_the_oracle(api):
+    """Every class of a graph-captured, autotuned batch (N = 16, 64 and 128 radix launches, the
+    N = 64 and 128 tensor-core forms, an N = 256 dataset on its own TMA launch) against the FP64
+    oracle directly, on fusion computed by the oracle."""
+    import oracle
+    from tests.parity_helpers import rel_l2
+    data = []
+    for i, (name, fft, pus, tol) in enumerate(ORACLE_DATASETS):
+        if name == "lab12":
+            cfg = dataclasses.replace(synth.CONFIGS["lab"], J=12)
+            sc = synth.make_scan_torch(cfg, seed=900 + i, device="cpu")
+            raw = sc["raw"].numpy()
+        else:
+            cfg = synth.CONFIGS[name]
+            sc = synth.make_scan(cfg, seed=900 + i)
+            raw = sc["raw"]
+        p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+        fused = oracle.mnf_stack(raw, cfg.times, p).astype(np.float32)
+        rng = np.random.default_rng(100 + i)
+        M = cfg.M
+        obj0 = (1 + 0.1 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))).astype(np.complex64)
+        data.append(dict(fused=fused, pos=sc["pos"], obj0=obj0, probe0=sc["probe"].astype(np.complex64),
+                         fft=fft, pus=pus, tol=tol))
+    hs = [api.ptycho_init(torch.from_numpy(d["fused"]).cuda(), d["pos"], d["obj0"], d["probe0"],
+                          probe_update_start=d["pus"], fft_path=d["fft"]) for d in data]
+    b = api.ptycho_batch_create(hs, graph=True, autotune=True)
+    api.ptycho_batch_iterate(b, 2)
+    api.ptycho_batch_iterate(b, 3)
+    for d, h, spec in zip(data, hs, ORACLE_DATASETS):
+        ro, rp, _ = oracle.reconstruct(d["fused"].astype(np.float64), d["pos"], d["obj0"].astype(np.complex128),
+                                       d["probe0"].astype(np.complex128), 5, 1e-3, 1e-3, d["pus"])
+        eo = rel_l2(api.ptycho_get_object(h), ro)
+        ep = rel_l2(api.ptycho_get_probe(h), rp)
+        print(spec, f"object {eo:.2e} probe {ep:.2e}")
+        assert eo <= d["tol"] and ep <= d["tol"], (spec, eo, ep)
+    api.ptycho_batch_destroy(b)
+    for h in hs:
+        api.ptycho_destroy(h)

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2608_01746_b300 import synth
-from tests.parity_helpers import rel_l2, tie_mask
+from tests.parity_helpers import rel_l2, tie_allowance
 
 pytestmark = pytest.mark.gpu
 
@@ -40,31 +40,67 @@ def test_unquantised_matches_oracle(api, name, mode):
     assert rel_l2(got, ref) <= 1e-6
 
 
+def check_quantised(got, raw, times, p, js):
+    """Every sampled position: |GPU - oracle| <= 1e-5 of the position's peak plus the tie
+    allowance (tie_allowance: quantiser decisions within FP32 reach of a rounding tie).  Returns
+    (ties, coefficients, pixels with an allowance, pixels that needed it, pixels)."""
+    n_ties = n_coeffs = allowed = used = pixels = 0
+    for j, g in zip(js, got):
+        ref = oracle.mnf_position(raw[j], times, p)
+        allow, nt, nc = tie_allowance(raw[j], times, p)
+        diff = np.abs(g - ref)
+        tol = 1e-5 * np.max(np.abs(ref))
+        bad = diff > tol + allow
+        assert not bad.any(), (j, np.argwhere(bad)[:5], diff[bad][:5], allow[bad][:5])
+        n_ties += nt
+        n_coeffs += nc
+        allowed += int((allow > 0).sum())
+        used += int((diff > tol).sum())
+        pixels += diff.size
+    return n_ties, n_coeffs, allowed, used, pixels
+
+
 @pytest.mark.parametrize("name,delta0", [("tiny", 0.5), ("small", 0.5), ("small", 4.0)])
 def test_quantised_matches_oracle_outside_ties(api, name, delta0):
     sc = synth.make_scan(name)
     cfg = sc["cfg"]
     p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip), delta0=delta0)
     got = run_gpu(api, sc["raw"], sc["times"], p)
-    n_ties = n_coeffs = 0
-    masked = pixels = 0
-    for j in range(sc["raw"].shape[0]):
-        ref = oracle.mnf_position(sc["raw"][j], sc["times"], p)
-        mask, nt, nc = tie_mask(sc["raw"][j], sc["times"], p)
-        n_ties += nt
-        n_coeffs += nc
-        diff = np.abs(got[j] - ref)
-        scale = np.max(np.abs(ref))
-        bad = (diff > 1e-5 * scale) & ~mask
-        assert not bad.any(), (j, np.argwhere(bad)[:5], diff[bad][:5])
-        # a flip moves the output by at most sum_l K Delta_l / 2 (U2 is a max-norm contraction)
-        bound = sum(sc["raw"].shape[1] * p.delta(l) / 2 for l in range(p.levels - 1)) * 2
-        assert np.all(diff[mask] <= bound + 1e-5 * scale)
-        masked += int(mask.sum())
-        pixels += mask.size
-    # the tie window must stay a small exception, or the test would check nothing
-    assert n_ties <= 1e-2 * n_coeffs
-    assert masked <= 0.25 * pixels
+    J = sc["raw"].shape[0]
+    n_ties, n_coeffs, allowed, used, pixels = check_quantised(got, sc["raw"], sc["times"], p, range(J))
+    print(f"{name} delta0={delta0}: ties {n_ties / max(n_coeffs, 1):.2e} of coefficients, allowance on "
+          f"{allowed / pixels:.3%} of pixels, needed on {used / pixels:.3%}")
+    # the tie window must stay a small exception, or the test would check nothing (measured:
+    # ties 1.5e-3 / 2.4e-4 / 1.8e-5 of the coefficients, the allowance needed on <= 0.005% of pixels)
+    assert n_ties <= 3e-3 * n_coeffs
+    assert used <= 1e-3 * pixels
+
+
+def test_lab_quantised_sampled_positions(api):
+    """The benchmarked fusion exactly as bench.py calls it: the 1600-position lab scan (N = 256,
+    K = 5, L = 6, clip 65535) with the default quantiser (delta0 = 0.5, ratio 2), in one call;
+    eight or nine positions (first, second, two inner ones, last and the four scan extremes)
+    against the oracle."""
+    sc = synth.make_scan_torch("lab", device="cuda")
+    cfg = sc["cfg"]
+    raw = sc["raw"]
+    params = api.fuse_params(levels=cfg.levels, clip=float(cfg.clip))
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    assert params.delta0 == p.delta0 == 0.5 and params.delta_ratio == p.delta_ratio == 2.0
+    out = api.fuse_stack(raw, cfg.times, params)
+    torch.cuda.synchronize()
+    pos = sc["pos"]
+    js = sorted({0, 1, 777, 1200, cfg.J - 1, int(np.argmin(pos[:, 0])), int(np.argmax(pos[:, 0])),
+                 int(np.argmin(pos[:, 1])), int(np.argmax(pos[:, 1]))})
+    assert len(js) >= 8
+    raw_h = {j: raw[j].cpu().numpy() for j in js}
+    got = [out[j].cpu().numpy().astype(np.float64) for j in js]
+    n_ties, n_coeffs, allowed, used, pixels = check_quantised(got, raw_h, cfg.times, p, js)
+    print(f"lab: ties {n_ties / n_coeffs:.2e} of coefficients, allowance on {allowed / pixels:.3%} of "
+          f"pixels, needed on {used / pixels:.3%}")
+    # measured on the CPU with the same generator: ties 1.1e-3 of the coefficients
+    assert n_ties <= 2e-3 * n_coeffs
+    assert used <= 5e-2 * pixels
 
 
 def test_single_exposure_linear_case(api):

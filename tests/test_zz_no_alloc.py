@@ -22,10 +22,6 @@ def api():
     return a
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
 @pytest.mark.parametrize("case", ["small", "lab200"])
 def test_matches_fuse_stack_two_calls_in_a_row(api, case):
     if case == "small":
@@ -45,7 +41,8 @@ def test_matches_fuse_stack_two_calls_in_a_row(api, case):
         out = torch.full(ref.shape, float("nan"), dtype=torch.float32, device="cuda")
         api.fuse_stack_noalloc(raw, cfg.times, params, out)
         torch.cuda.synchronize()
-        assert rel_l2(out.cpu().numpy(), ref) <= 1e-6
+        # the same kernels on the same positions (only the chunking differs): bit-identical
+        assert np.array_equal(out.cpu().numpy(), ref)
 
 
 def test_rejects_scratch_beyond_the_static_buffer(api):
