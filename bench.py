@@ -182,19 +182,39 @@ def bf16_peak_tflops():
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
-    """148 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    """Derived FP32 rate for context: 148 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def profiled_traffic_per_position():
-    """DRAM bytes per position of k_exit_wave_tma from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "exit_wave_tma_lab400.md")
-    if not os.path.exists(path):
-        return None
-    for line in open(path):
-        if line.startswith("traffic_bytes_per_position:"):
-            return int(line.split(":")[1])
-    return None
+def iteration_bytes_per_update(N: int) -> int:
+    """Algorithmic bytes of one position-update through the whole iteration: A_j (4 N^2), the
+    object patch (8 N^2), the object numerator read-modify-write (16 N^2) and the probe
+    numerator (8 N^2) = 36 N^2."""
+    return 36 * N * N
+
+
+def iteration_flops_per_update(N: int) -> float:
+    """Flops of one position-update through the whole iteration: two 2-D FFTs (5 n log2 n
+    each, n = N^2) plus ~60 flops per pixel of pointwise work (exit wave, modulus, object and
+    probe numerators and denominators, updates)."""
+    n = N * N
+    return 2 * 5.0 * n * np.log2(n) + 60.0 * n
+
+
+# DRAM bytes per position of the N = 256 exit-wave kernel from one ncu capture (400 lab
+# positions, one launch: dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel sources it was taken on (their SHA-256, first 16 hex digits).  A changed kernel
+# reports traffic null until it is captured again.
+EXIT_TRAFFIC = {"sources_sha16": None, "bytes_per_position": None, "capture": None}
+
+
+def exit_kernel_sources_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ptycho.cu", "fft.cuh", "tma.cuh"):
+        with open(os.path.join(ROOT, "paper_2608_01746_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # ----------------------------------------------------------------------------- batched arm
@@ -328,19 +348,21 @@ def run_batched(args, world, rank, local):
                                          + sum(o.nbytes for o in outs) + sum(p.numel() * 8 for p in probe0)),
                "d2h_bytes_per_step": int(sum(o.nbytes for o in outs))}
 
-    # whole-iteration ALU roofline (every kernel of the batched iteration together): the exit-wave
-    # FFT flops of every position against the FP32 lanes at the maximum clock
+    # whole-iteration roofline (every kernel of the batched iteration together; per-kernel events
+    # are not available inside the graph): 36 N^2 bytes per position-update against the measured
+    # copy bandwidth, and the iteration's flops against the measured FP32 FMA rate
     it_ms = variants["batch_graph_autotuned"]["ms_per_iteration"] if variants else ms_total / args.steps / n_iter
-    flops = sum(exit_wave_flops_per_position(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e12
-    alu_peak = fp32_peak_tflops(2032.0)
+    fma = api.measure_fp32_fma_tflops(device=dev)
+    flops = sum(iteration_flops_per_update(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e12
     hbm_peak, peak_kind = peaks()
-    hbm = sum(exit_wave_bytes_per_position(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e9
+    hbm = sum(iteration_bytes_per_update(c.N) * c.n_pos for c in cfgs) / (it_ms / 1e3) / 1e9
     roof = {"kernel": "whole batched iteration (all kernels; per-kernel events are not available inside the graph)",
-            "bound": "alu", "achieved": round(flops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-            "frac": round(flops / alu_peak, 4), "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
-            "traffic": None, "avg_iteration_ms": round(it_ms, 4),
-            "hbm_view": {"achieved_gbs": round(hbm, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
-                         "frac": round(hbm / hbm_peak, 4)}}
+            "bound": "hbm", "achieved": round(hbm, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(hbm / hbm_peak, 4), "peak_kind": peak_kind,
+            "bytes_per_position_update": "36 N^2", "traffic": None, "avg_iteration_ms": round(it_ms, 4),
+            "alu_view": {"achieved_tflops": round(flops, 2), "peak_tflops": round(fma["tflops"], 2),
+                         "peak_kind": "measured: the library's FP32 FMA kernel, best of 5 launches",
+                         "frac": round(flops / fma["tflops"], 4)}}
     by_n = {n: sum(1 for c in cfgs if c.N == n) for n in sorted({c.N for c in cfgs})}
     launches_per_iter = (len(by_n) - 1 + sum(1 for c in cfgs if c.N == 256)  # class launches + N=256 exits
                          + 2 * len(cfgs) + 3 * len(cfgs) + len(cfgs))   # object (2), probe (3), error (1)
@@ -571,32 +593,50 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(raw_h.numel() * 2 + obj_h.nbytes + probe_h.nbytes + pos.nbytes),
                "d2h_bytes_per_step": int(out_o.nbytes + out_p.nbytes)}
 
-    # roofline of the dominant kernel (exit-wave), from the per-stage CUDA events of the timed
-    # steps (recorded on the library's stream).  The kernel is bound by its FP32 FFT instruction
-    # stream, so the roofline is ALU: FFT + pointwise flops against 148 x 128 FP32 lanes at the
-    # maximum SM clock; the algorithmic-HBM view is reported beside it.
+    # Roofline of the dominant kernel (the exit wave), from the per-stage CUDA events of the timed
+    # steps (recorded on the library's stream).  HBM: the kernel's algorithmic bytes per position
+    # (A_j, object patch, probe, psi_j': 28 N^2) against the measured copy bandwidth; ALU: its
+    # FFT and pointwise flops against the FP32 FMA rate measured by the library's own kernel;
+    # iteration: the whole iteration's 36 N^2 bytes per position-update over its time.
     hbm_peak, peak_kind = peaks()
     dom = int(np.argmax(stage_ms))
     names = ["k_exit_wave", "object update (k_object_gather + k_apply)",
              "probe update (k_probe_partial + k_probe_reduce + k_apply)", "k_error_reduce"]
     Q = cfg.modes
     exit_ms = stage_ms[0] / max(stage_n[0], 1) * (3 if Q > 1 else 1)   # per iteration
+    iter_ms = float(stage_ms.sum()) / (args.steps * n_iter)
+    fma = api.measure_fp32_fma_tflops(device=dev)
     flops = Q * exit_wave_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
-    alu_peak = fp32_peak_tflops(2032.0)
     hbm_algo = Q * exit_wave_bytes_per_position(N) * J / (exit_ms / 1e3) / 1e9
-    tpp = profiled_traffic_per_position()
-    traffic = int(tpp * J) if (tpp is not None and N == 256 and Q == 1) else None
+    traffic = None
+    if N == 256 and Q == 1 and EXIT_TRAFFIC["bytes_per_position"] and \
+            EXIT_TRAFFIC["sources_sha16"] == exit_kernel_sources_sha16():
+        traffic = int(EXIT_TRAFFIC["bytes_per_position"] * J)
     kname = ("k_exit_wave_tma" if N == 256 else ("k_exit_wave128" if N == 128 else "k_exit_wave")) + (
         " (forward + k_modulus_modes + inverse, per iteration)" if Q > 1 else "")
-    roof = {"kernel": kname, "bound": "alu",
-            "achieved": round(flops, 2), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-            "frac": round(flops / alu_peak, 4),
-            "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
-            "traffic": traffic, "traffic_note": "DRAM bytes per launch scaled from a 400-position ncu capture",
+    it_gbs = Q * iteration_bytes_per_update(N) * J / (iter_ms / 1e3) / 1e9
+    it_tflops = Q * iteration_flops_per_update(N) * J / (iter_ms / 1e3) / 1e12
+    roof = {"kernel": kname, "bound": "hbm",
+            "achieved": round(hbm_algo, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(hbm_algo / hbm_peak, 4), "peak_kind": peak_kind,
+            "bytes_per_position": exit_wave_bytes_per_position(N), "positions_per_launch": J,
+            "traffic": traffic,
+            "traffic_note": (f"ncu DRAM bytes per position {EXIT_TRAFFIC['bytes_per_position']} x {J} positions "
+                             f"({EXIT_TRAFFIC['capture']})" if traffic else
+                             "null: no ncu capture of the current kernel sources"),
             "avg_launch_ms": round(exit_ms, 4),
-            "hbm_view": {"achieved_gbs": round(hbm_algo, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
-                         "frac": round(hbm_algo / hbm_peak, 4),
-                         "bytes_per_position": exit_wave_bytes_per_position(N)}}
+            "alu_view": {"achieved_tflops": round(flops, 2), "peak_tflops": round(fma["tflops"], 2),
+                         "peak_kind": "measured: the library's FP32 FMA kernel, best of 5 launches",
+                         "frac": round(flops / fma["tflops"], 4),
+                         "flops_per_position": exit_wave_flops_per_position(N),
+                         "derived_peak_tflops_2032mhz": round(fp32_peak_tflops(2032.0), 2)},
+            "iteration_view": {"ms_per_iteration": round(iter_ms, 4),
+                               "bytes_per_position_update": iteration_bytes_per_update(N),
+                               "achieved_gbs": round(it_gbs, 1), "peak_gbs": hbm_peak,
+                               "frac": round(it_gbs / hbm_peak, 4),
+                               "flops_per_position_update": iteration_flops_per_update(N),
+                               "achieved_tflops": round(it_tflops, 2),
+                               "alu_frac": round(it_tflops / fma["tflops"], 4)}}
     if args.fft == "dftgemm_bf16x3":
         tflops = dftgemm_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
         bf16_peak, bf16_kind = bf16_peak_tflops()
@@ -608,7 +648,8 @@ def run_ours(args, world, rank, local):
                 "fp32_fft_equivalent_tflops": round(flops, 2),
                 "hbm_view": {"achieved_gbs": round(hbm_algo, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                              "frac": round(hbm_algo / hbm_peak, 4),
-                             "bytes_per_position": exit_wave_bytes_per_position(N)}}
+                             "bytes_per_position": exit_wave_bytes_per_position(N)},
+                "iteration_view": roof["iteration_view"]}
     fuse_n = fuse_launches(cfg.levels)
     launches = int(args.steps * (fuse_n + 2) + stage_n.sum())
 
