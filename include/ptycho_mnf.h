@@ -220,7 +220,12 @@ int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches 
  *                        datasets updating their probe changes); PTYCHO_BATCH_AUTOTUNE times
  *                        candidate launch shapes (persistent grid sizes; rows per TMA stage at
  *                        N = 256) on the datasets themselves, keeps the fastest and restores
- *                        every object and probe (results are unaffected).  The handles stay
+ *                        every object and probe (results are unaffected).  PTYCHO_BATCH_ONE_LAUNCH
+ *                        computes the exit waves of every single-mode radix-FFT dataset, of any
+ *                        N, in ONE persistent launch per iteration (units ordered by cost and
+ *                        dealt to one 512-thread CTA per SM; N <= 64 positions four at a time per
+ *                        CTA); results are bit-identical to the per-size launches, and the
+ *                        per-size launch grids are then not tuned.  The handles stay
  *                        owned by the caller, must outlive the batch, belong to one batch at a
  *                        time, and must not be iterated while a batch call is in flight
  *                        (ptycho_iterate between batch calls is fine).  The batch runs on a stream of its
@@ -235,7 +240,7 @@ int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches 
  *   ptycho_batch_describe  the autotuner's choices and timings as a JSON object text.
  */
 typedef struct ptycho_batch_ctx *ptycho_batch;
-enum { PTYCHO_BATCH_GRAPH = 1, PTYCHO_BATCH_AUTOTUNE = 2 };
+enum { PTYCHO_BATCH_GRAPH = 1, PTYCHO_BATCH_AUTOTUNE = 2, PTYCHO_BATCH_ONE_LAUNCH = 4 };
 int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handles, int n, int flags, void *cuda_stream);
 int ptycho_batch_iterate(ptycho_batch b, int n_iter, double *h_err);
 int ptycho_batch_describe(ptycho_batch b, char *buf, int len);

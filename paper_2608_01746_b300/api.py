@@ -380,6 +380,7 @@ def ptycho_stage_times(h: PtychoHandle):
 
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
+BATCH_ONE_LAUNCH = 4
 
 
 class PtychoBatch:
@@ -401,11 +402,12 @@ class PtychoBatch:
             pass
 
 
-def ptycho_batch_create(handles, graph: bool = False, autotune: bool = False, stream=None) -> PtychoBatch:
+def ptycho_batch_create(handles, graph: bool = False, autotune: bool = False, one_launch: bool = False,
+                        stream=None) -> PtychoBatch:
     n = len(handles)
     arr = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
     b = ctypes.c_void_p()
-    flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+    flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0) | (BATCH_ONE_LAUNCH if one_launch else 0)
     _check(lib().ptycho_batch_create(ctypes.byref(b), arr, n, flags, ctypes.c_void_p(_stream_ptr(stream))))
     return PtychoBatch(b.value, handles)
 

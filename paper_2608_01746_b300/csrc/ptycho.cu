@@ -78,134 +78,157 @@ constexpr size_t exit_smem_bytes() {
     return sizeof(float2) * ((size_t)N + (size_t)G * R * (R + 1) + (size_t)N * (N + 1));
 }
 
-// N <= 64: one CTA per unit at a time (persistent grid), the whole N x N tile in shared
-// memory: row FFTs, column FFTs (with the modulus replacement between the forward and inverse
-// column transforms in XM_FULL), inverse row FFTs.
-template <int R, int XM>
-__global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
+// Per-unit body of the N <= 64 exit wave, run by NT threads (rank tid) that synchronise with
+// sync(): the whole N x N tile in shared memory: row FFTs, column FFTs (with the modulus
+// replacement between the forward and inverse column transforms in XM_FULL), inverse row FFTs.
+// c: the unit's dataset arguments; u: the unit (position j, or j Q + m); tw: [N] twiddles;
+// xb_all: [NT / R][R][R + 1] exchange buffers; rows: [N][N + 1]; s_red: [NT / 32].
+template <int R, int XM, int NT, typename Sync>
+__device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const float2 *tw, float2 *xb_all,
+                                                float2 *rows, double *s_red, int tid, int Q, Sync sync) {
     constexpr int N = R * R;
-    constexpr int G = kThreads / R;          // FFT groups per CTA
+    constexpr int G = NT / R;                // FFT groups
     constexpr int TP = N + 1;                // padded row pitch
-    extern __shared__ float2 smem[];
-    float2 *tw = smem;                       // [N] W_N^(a b), forward sign
-    float2 *xb_all = tw + N;                 // [G][R][R+1]
-    float2 *rows = xb_all + G * R * (R + 1); // [N][N+1]
-    __shared__ double s_red[kThreads / 32];
-
-    const int tid = threadIdx.x;
+    constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int t = tid % R, g = tid / R;
-    for (int i = tid; i < N; i += kThreads) {
+    float2 *xb = xb_all + g * R * (R + 1);
+    const float invN = 1.0f / (float)N;
+    const int M = c.M;
+    const int j = kFull ? u : u / Q;
+    const int mode = kFull ? 0 : u % Q;
+    float2 *psi_u = c.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
+    if constexpr (XM != XM_INV) {
+        // (1) psi = P_m * O_j, forward row FFTs in place
+        const int2 pj = c.pos[j];
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int r = r0 + g;
+            if (r < N) {                                 // warp-uniform (see fft.cuh)
+                float2 d[R];
+                const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
+                const float2 *prow = c.probe + (size_t)mode * N * N + (size_t)r * N;
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
+                pm::fft_group<R, -1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) rows[r * TP + t + R * m] = d[m];
+            }
+        }
+    } else {
+        for (int i = tid; i < N * N; i += NT) rows[(i / N) * TP + i % N] = psi_u[i];
+    }
+    sync();
+    // (2) column FFTs: forward (+ modulus + inverse in XM_FULL) or inverse (XM_INV)
+    float err = 0.f;
+    const float *amp_j = c.amp + (size_t)j * N * N;
+    for (int c0 = 0; c0 < N; c0 += G) {
+        const int col = c0 + g;
+        if (col < N) {
+            float2 d[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) d[m] = rows[(t + R * m) * TP + col];
+            if constexpr (XM == XM_INV) {
+                pm::fft_group<R, +1>(d, xb, tw, t);
+            } else {
+                pm::fft_group<R, -1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
+            }
+            if constexpr (kFull) {
+#pragma unroll
+                for (int m = 0; m < R; ++m) {
+                    const float2 X = d[m];
+                    const float A = __ldg(amp_j + (size_t)col * N + t + R * m);
+                    const float mag = sqrtf(cabs2(X));
+                    const float dm = mag - A;
+                    err += dm * dm;
+                    d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+                }
+                pm::fft_group<R, +1>(d, xb, tw, t);
+            }
+#pragma unroll
+            for (int m = 0; m < R; ++m) rows[(t + R * m) * TP + col] = d[m];
+        }
+    }
+    sync();
+    if constexpr (XM == XM_FWD) {
+        for (int i = tid; i < N * N; i += NT) psi_u[i] = rows[(i / N) * TP + i % N];
+    } else {
+        // (3) inverse row FFTs, psi' written row-major
+        for (int r0 = 0; r0 < N; r0 += G) {
+            const int r = r0 + g;
+            if (r < N) {
+                float2 d[R];
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = rows[r * TP + t + R * m];
+                pm::fft_group<R, +1>(d, xb, tw, t);
+#pragma unroll
+                for (int m = 0; m < R; ++m) psi_u[(size_t)r * N + t + R * m] = cscale(d[m], invN);
+            }
+        }
+    }
+    if constexpr (kFull) {
+        // Fourier error of position j (FP64 sum over the NT threads)
+        double e = (double)err;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = e;
+        sync();
+        if (tid == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < NT / 32; ++w) sum += s_red[w];
+            c.err[j] = sum;
+        }
+    }
+    sync();          // the next unit's first pass overwrites the tile
+}
+
+// The N x N twiddle table W_N^(a b) (forward sign) indexed [a * R + b], N = R * R.
+template <int R>
+__device__ __forceinline__ void fill_twiddles(float2 *tw, int tid, int nt) {
+    constexpr int N = R * R;
+    for (int i = tid; i < N; i += nt) {
         const int ab = (i / R) * (i % R);
         double sn, cs;
         sincospi(-2.0 * (double)ab / (double)N, &sn, &cs);
         tw[i] = make_float2((float)cs, (float)sn);
     }
+}
+
+// Dataset of unit iu of a multi-dataset launch: the d with ustart[d] <= iu < ustart[d + 1].
+__device__ __forceinline__ int table_lookup(const int *ustart, int ntable, int iu) {
+    int lo = 0, hi = ntable - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(ustart + mid) <= iu) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// N <= 64: one CTA per unit at a time (persistent grid).
+template <int R, int XM>
+__global__ void __launch_bounds__(kThreads) k_exit_wave(ExitArgs a) {
+    constexpr int N = R * R;
+    constexpr int G = kThreads / R;          // FFT groups per CTA
+    extern __shared__ float2 smem[];
+    float2 *tw = smem;                       // [N] W_N^(a b), forward sign
+    float2 *xb_all = tw + N;                 // [G][R][R+1]
+    float2 *rows = xb_all + G * R * (R + 1); // [N][N+1]
+    __shared__ double s_red[kThreads / 32];
+    const int tid = threadIdx.x;
+    fill_twiddles<R>(tw, tid, kThreads);
     __syncthreads();
-    float2 *xb = xb_all + g * R * (R + 1);
-    const float invN = 1.0f / (float)N;
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
-
     for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
         int u = (XM == XM_LIST) ? a.list[iu] : iu;
         ExitArgs c = a;
         if (XM == XM_FULL && a.table) {
-            int lo = 0, hi = a.ntable - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(a.ustart + mid) <= iu) lo = mid;
-                else hi = mid - 1;
-            }
-            c = a.table[lo];
-            u = iu - __ldg(a.ustart + lo);
+            const int d = table_lookup(a.ustart, a.ntable, iu);
+            c = a.table[d];
+            u = iu - __ldg(a.ustart + d);
         }
-        const int M = c.M;
-        const int j = kFull ? u : u / a.Q;
-        const int mode = kFull ? 0 : u % a.Q;
-        float2 *psi_u = c.psi + (size_t)u * N * N;          // u = j (one mode) or j Q + m
-        if constexpr (XM != XM_INV) {
-            // (1) psi = P_m * O_j, forward row FFTs in place
-            const int2 pj = c.pos[j];
-            for (int r0 = 0; r0 < N; r0 += G) {
-                const int r = r0 + g;
-                if (r < N) {                                 // warp-uniform (see fft.cuh)
-                    float2 d[R];
-                    const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
-                    const float2 *prow = c.probe + (size_t)mode * N * N + (size_t)r * N;
-#pragma unroll
-                    for (int m = 0; m < R; ++m) d[m] = cmul(__ldg(prow + t + R * m), __ldg(orow + t + R * m));
-                    pm::fft_group<R, -1>(d, xb, tw, t);
-#pragma unroll
-                    for (int m = 0; m < R; ++m) rows[r * TP + t + R * m] = d[m];
-                }
-            }
-        } else {
-            for (int i = tid; i < N * N; i += kThreads) rows[(i / N) * TP + i % N] = psi_u[i];
-        }
-        __syncthreads();
-        // (2) column FFTs: forward (+ modulus + inverse in XM_FULL) or inverse (XM_INV)
-        float err = 0.f;
-        const float *amp_j = c.amp + (size_t)j * N * N;
-        for (int c0 = 0; c0 < N; c0 += G) {
-            const int c = c0 + g;
-            if (c < N) {
-                float2 d[R];
-#pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = rows[(t + R * m) * TP + c];
-                if constexpr (XM == XM_INV) {
-                    pm::fft_group<R, +1>(d, xb, tw, t);
-                } else {
-                    pm::fft_group<R, -1>(d, xb, tw, t);
-#pragma unroll
-                    for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
-                }
-                if constexpr (kFull) {
-#pragma unroll
-                    for (int m = 0; m < R; ++m) {
-                        const float2 X = d[m];
-                        const float A = __ldg(amp_j + (size_t)c * N + t + R * m);
-                        const float mag = sqrtf(cabs2(X));
-                        const float dm = mag - A;
-                        err += dm * dm;
-                        d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
-                    }
-                    pm::fft_group<R, +1>(d, xb, tw, t);
-                }
-#pragma unroll
-                for (int m = 0; m < R; ++m) rows[(t + R * m) * TP + c] = d[m];
-            }
-        }
-        __syncthreads();
-        if constexpr (XM == XM_FWD) {
-            for (int i = tid; i < N * N; i += kThreads) psi_u[i] = rows[(i / N) * TP + i % N];
-        } else {
-            // (3) inverse row FFTs, psi' written row-major
-            for (int r0 = 0; r0 < N; r0 += G) {
-                const int r = r0 + g;
-                if (r < N) {
-                    float2 d[R];
-#pragma unroll
-                    for (int m = 0; m < R; ++m) d[m] = rows[r * TP + t + R * m];
-                    pm::fft_group<R, +1>(d, xb, tw, t);
-#pragma unroll
-                    for (int m = 0; m < R; ++m) psi_u[(size_t)r * N + t + R * m] = cscale(d[m], invN);
-                }
-            }
-        }
-        if constexpr (kFull) {
-            // Fourier error of position j (FP64 block sum)
-            double e = (double)err;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if ((tid & 31) == 0) s_red[tid >> 5] = e;
-            __syncthreads();
-            if (tid == 0) {
-                double sum = 0.0;
-                for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
-                c.err[j] = sum;
-            }
-        }
-        __syncthreads();          // the next unit's first pass overwrites the tile
+        exit_small_unit<R, XM, kThreads>(c, u, tw, xb_all, rows, s_red, tid, a.Q, [] { __syncthreads(); });
     }
 }
 
@@ -223,104 +246,112 @@ constexpr size_t exit128_smem_bytes() {
     return sizeof(float2) * ((size_t)N + (size_t)G * kXB128 + (size_t)N * (N + 1));
 }
 
-template <int XM>
-__global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
+// Per-unit body of the N = 128 exit wave (position j of dataset c), kThreads128 threads.
+// tw: [N] W_128^((i / 8) (i % 8)); xb_all: [G][kXB128]; rows: [N][N + 1]; s_red: [16].
+__device__ __forceinline__ void exit128_unit(const ExitArgs &c, int j, const float2 *tw, float2 *xb_all,
+                                             float2 *rows, double *s_red) {
     constexpr int N = 128, R1 = 8, E = 16;
     constexpr int G = kThreads128 / R1;
     constexpr int TP = N + 1;
+    const int tid = threadIdx.x;
+    const int t = tid % R1, g = tid / R1;
+    float2 *xb = xb_all + g * kXB128;
+    const float invN = 1.0f / (float)N;
+    const int M = c.M;
+    float2 *psi_j = c.psi + (size_t)j * N * N;
+    const int2 pj = c.pos[j];
+    // (1) psi = P O_j, forward row FFTs; stored at the true frequency kx
+    for (int r0 = 0; r0 < N; r0 += G) {
+        const int r = r0 + g;
+        float2 d[E];
+        const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
+        const float2 *prow = c.probe + (size_t)r * N;
+#pragma unroll
+        for (int m = 0; m < E; ++m) d[m] = cmul(__ldg(prow + t + R1 * m), __ldg(orow + t + R1 * m));
+        pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
+#pragma unroll
+        for (int e = 0; e < E; ++e) rows[r * TP + pm::rev128(t, e)] = d[e];
+    }
+    __syncthreads();
+    // (2) columns: forward, modulus (ky = rev128(t, e)), inverse back to natural rows
+    float err = 0.f;
+    const float *amp_j = c.amp + (size_t)j * N * N;
+    // the 4 groups of a warp take columns 8 apart: with the row pitch of 129 float2 their
+    // column reads and writes fall in distinct banks (2 t + 16 q words)
+    const int col_off = 8 * (g & 3) + ((g >> 2) & 7) + 32 * (g >> 5);
+    for (int c0 = 0; c0 < N; c0 += G) {
+        const int col = c0 + col_off;
+        float2 d[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) d[m] = rows[(t + R1 * m) * TP + col];
+        pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float2 X = cscale(d[e], invN);
+            const float A = __ldg(amp_j + (size_t)col * N + pm::rev128(t, e));
+            const float mag = sqrtf(cabs2(X));
+            const float dm = mag - A;
+            err += dm * dm;
+            d[e] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+        }
+        pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
+#pragma unroll
+        for (int m = 0; m < E; ++m) rows[(t + R1 * m) * TP + col] = d[m];
+    }
+    __syncthreads();
+    // (3) inverse row FFTs from the true frequencies, psi' written row-major
+    for (int r0 = 0; r0 < N; r0 += G) {
+        const int r = r0 + g;
+        float2 d[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) d[e] = rows[r * TP + pm::rev128(t, e)];
+        pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
+#pragma unroll
+        for (int m = 0; m < E; ++m) psi_j[(size_t)r * N + t + R1 * m] = cscale(d[m], invN);
+    }
+    // Fourier error of position j (FP64 block sum)
+    double e64 = (double)err;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, o);
+    if ((tid & 31) == 0) s_red[tid >> 5] = e64;
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads128 / 32; ++w) sum += s_red[w];
+        c.err[j] = sum;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fill_twiddles128(float2 *tw, int tid, int nt) {
+    for (int i = tid; i < 128; i += nt) {
+        double sn, cs;
+        sincospi(-2.0 * (double)((i / 8) * (i % 8)) / 128.0, &sn, &cs);
+        tw[i] = make_float2((float)cs, (float)sn);
+    }
+}
+
+template <int XM>
+__global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
+    constexpr int N = 128;
+    constexpr int G = kThreads128 / 8;
     extern __shared__ float2 smem[];
     float2 *tw = smem;                       // [N] W_128^((i / 8) (i % 8)), forward sign
     float2 *xb_all = tw + N;                 // [G][kXB128]
     float2 *rows = xb_all + G * kXB128;      // [N][N+1]
     __shared__ double s_red[kThreads128 / 32];
-    const int tid = threadIdx.x;
-    const int t = tid % R1, g = tid / R1;
-    for (int i = tid; i < N; i += kThreads128) {
-        double sn, cs;
-        sincospi(-2.0 * (double)((i / R1) * (i % R1)) / (double)N, &sn, &cs);
-        tw[i] = make_float2((float)cs, (float)sn);
-    }
+    fill_twiddles128(tw, threadIdx.x, kThreads128);
     __syncthreads();
-    float2 *xb = xb_all + g * kXB128;
-    const float invN = 1.0f / (float)N;
     const int units = (XM == XM_LIST) ? a.count : a.J;
     for (int iu = blockIdx.x; iu < units; iu += gridDim.x) {
         int j = (XM == XM_LIST) ? a.list[iu] : iu;
         ExitArgs c = a;
         if (XM == XM_FULL && a.table) {
-            int lo = 0, hi = a.ntable - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(a.ustart + mid) <= iu) lo = mid;
-                else hi = mid - 1;
-            }
-            c = a.table[lo];
-            j = iu - __ldg(a.ustart + lo);
+            const int d = table_lookup(a.ustart, a.ntable, iu);
+            c = a.table[d];
+            j = iu - __ldg(a.ustart + d);
         }
-        const int M = c.M;
-        float2 *psi_j = c.psi + (size_t)j * N * N;
-        const int2 pj = c.pos[j];
-        // (1) psi = P O_j, forward row FFTs; stored at the true frequency kx
-        for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
-            float2 d[E];
-            const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
-            const float2 *prow = c.probe + (size_t)r * N;
-#pragma unroll
-            for (int m = 0; m < E; ++m) d[m] = cmul(__ldg(prow + t + R1 * m), __ldg(orow + t + R1 * m));
-            pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
-#pragma unroll
-            for (int e = 0; e < E; ++e) rows[r * TP + pm::rev128(t, e)] = d[e];
-        }
-        __syncthreads();
-        // (2) columns: forward, modulus (ky = rev128(t, e)), inverse back to natural rows
-        float err = 0.f;
-        const float *amp_j = c.amp + (size_t)j * N * N;
-        // the 4 groups of a warp take columns 8 apart: with the row pitch of 129 float2 their
-        // column reads and writes fall in distinct banks (2 t + 16 q words)
-        const int col_off = 8 * (g & 3) + ((g >> 2) & 7) + 32 * (g >> 5);
-        for (int c0 = 0; c0 < N; c0 += G) {
-            const int col = c0 + col_off;
-            float2 d[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) d[m] = rows[(t + R1 * m) * TP + col];
-            pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float2 X = cscale(d[e], invN);
-                const float A = __ldg(amp_j + (size_t)col * N + pm::rev128(t, e));
-                const float mag = sqrtf(cabs2(X));
-                const float dm = mag - A;
-                err += dm * dm;
-                d[e] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
-            }
-            pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
-#pragma unroll
-            for (int m = 0; m < E; ++m) rows[(t + R1 * m) * TP + col] = d[m];
-        }
-        __syncthreads();
-        // (3) inverse row FFTs from the true frequencies, psi' written row-major
-        for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
-            float2 d[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) d[e] = rows[r * TP + pm::rev128(t, e)];
-            pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
-#pragma unroll
-            for (int m = 0; m < E; ++m) psi_j[(size_t)r * N + t + R1 * m] = cscale(d[m], invN);
-        }
-        // Fourier error of position j (FP64 block sum)
-        double e64 = (double)err;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = e64;
-        __syncthreads();
-        if (tid == 0) {
-            double sum = 0.0;
-            for (int w = 0; w < kThreads128 / 32; ++w) sum += s_red[w];
-            c.err[j] = sum;
-        }
-        __syncthreads();
+        exit128_unit(c, j, tw, xb_all, rows, s_red);
     }
 }
 
@@ -362,314 +393,76 @@ __global__ void __launch_bounds__(kThreads) k_modulus_modes(float2 *__restrict__
     }
 }
 
+#include "exit_tma.cuh"
+
 // ---------------------------------------------------------------------------------------
-// N = 256 exit-wave kernel: one 512-thread CTA per SM, persistent over positions, with a
-// TMA pipeline through a per-CTA 512 KB tile slot that stays in L2.  Batches are 32 rows or
-// columns (one per 16-thread FFT group); every batch of tile data is a bulk tensor copy that
-// runs while the previous batch is transformed.
-//
-//   phase R   rows r = 32 b + g: probe rows arrive by TMA (double-buffered), object patch rows
-//             by register-prefetched loads (the patch origin x is not 16-byte aligned);
-//             psi = P * O_j, forward row FFT, written (128-byte swizzle) to a staging buffer
-//             that is TMA-stored column-major into the slot.
-//   phase C   32 slot columns per TMA load (double-buffered); forward column FFT, modulus
-//             replacement against A_j (loads issued before the FFT), inverse column FFT;
-//             results TMA-stored (128-byte swizzle) into psi_j, row-major.
-//   phase R'  32 rows of psi_j per TMA load, inverse row FFT, TMA-stored back in place.
-// FFT exchanges happen in place in the group's own staged row or column.  Waits are bounded
-// (tma.cuh); on a timeout the kernel sets *a.status and returns.
-struct TmaArgs {
-    const float2 *obj;
-    const float *amp;        // [J][N][N] column-major per position
-    const int2 *pos;
-    double *err;             // [J] Fourier error per position (XM_FULL)
-    int *status;             // set to 1 if a bounded wait gave up
-    const int *list;         // XM_FULL: if not NULL, process positions list[0 .. count)
-    int count;
-    int M, J, Q;
-    int inject_wait;         // test hook: wait on a barrier nothing arrives on (short limit) first
-};
+// One persistent launch for the exit waves of many datasets of every probe size (batches of
+// uneven scans).  A unit is (kind, dataset, first position, count): kind 256 and 128 take the
+// whole 512-thread CTA for one position (the bodies of k_exit_wave_tma<32> and k_exit_wave128);
+// kinds 64 and 16 run up to four positions at once, one per 128-thread quarter of the CTA
+// (k_exit_wave's body with a named barrier per quarter).  Units are ordered by cost (256, 128,
+// 64, 16) and dealt to the CTAs round-robin, one CTA per SM.  Per-position arithmetic is that of
+// the per-size kernels, so the results are bit-identical to them.
+constexpr int kAllThreads = 512;
+constexpr int kQuarter = kAllThreads / 4;
+template <int R>
+__host__ __device__ constexpr size_t quarter_bytes() {
+    constexpr int N = R * R, G = kQuarter / R;
+    return sizeof(float2) * ((size_t)G * R * (R + 1) + (size_t)N * (N + 1));
+}
+__host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kAllScratch =
+    cmax(3 * tma_buf_bytes<32>(),
+         cmax(sizeof(float2) * ((size_t)(kThreads128 / 8) * kXB128 + 128 * 129), 4 * quarter_bytes<8>()));
+constexpr size_t kAllTw = sizeof(float2) * (256 + 128 + 64 + 16);
+constexpr size_t all_smem_bytes() { return 1024 + kAllScratch + kAllTw; }
 
-struct TmaMaps {
-    CUtensorMap prow;        // probe rows ([Q N] rows) box {256 c, B r}
-    CUtensorMap slot_r;      // slot, column-major    box {16 r, 256 c}, 128-byte swizzle
-    CUtensorMap slot_c;      // slot, column-major    box {256 r, 32 c}
-    CUtensorMap psi_c;       // psi, row-major        box {16 c, 256 r}, 128-byte swizzle
-    CUtensorMap psi_r;       // psi, row-major        box {256 c, 32 r}  (loads)
-    CUtensorMap psi_w;       // psi, row-major        box {256 c, 16 r}  (stores)
-};
+// Out-of-line unit bodies of the one launch (N <= 128), so that the inlined N = 256 body keeps
+// its registers.
+__device__ __noinline__ void all_unit128(const ExitArgs &c, int j, const float2 *tw, unsigned char *base, double *s_red) {
+    exit128_unit(c, j, tw, (float2 *)base, (float2 *)base + (kThreads128 / 8) * kXB128, s_red);
+}
+template <int R>
+__device__ __noinline__ void all_unit_small(const ExitArgs &c, int u, const float2 *tw, unsigned char *base,
+                                            double *s_red, int q, int qt) {
+    constexpr int G = kQuarter / R;
+    float2 *xb = (float2 *)(base + q * quarter_bytes<R>());
+    auto sync = [q] { asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(kQuarter) : "memory"); };
+    exit_small_unit<R, XM_FULL, kQuarter>(c, u, tw, xb, xb + G * R * (R + 1), s_red + 4 * q, qt, 1, sync);
+}
 
-// Batch = rows or columns per pipeline stage = FFT groups per CTA (16 threads each).  32:
-// one 512-thread CTA per SM; 16: two 256-thread CTAs per SM, each with its own position.
-template <int B>
-__host__ __device__ constexpr size_t tma_buf_bytes() { return (size_t)B * 256 * sizeof(float2); }
-template <int B>
-__host__ __device__ constexpr size_t tma_smem_bytes() { return 1024 /*alignment slack*/ + 3 * tma_buf_bytes<B>() + 256 * sizeof(float2) + 64; }
-
-// Every copy carries an L2 cache policy: the probe rows, the slot and the intermediate psi
-// columns (re-read by this CTA within the position) are kept, data read for the last time and
-// the final psi_j' rows are evicted first (measured at lab scale: DRAM traffic 2.47 -> 1.24 MB per
-// position with B = 32).
-template <int B, int XM>
-__global__ void __launch_bounds__(B * 16, 32 / B)
-k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
-    constexpr int R = 16, N = 256, NB = N / B;
-    constexpr int kTmaThreads = B * 16, kTmaBatch = B;
-    constexpr size_t kTmaBuf = tma_buf_bytes<B>();
-    namespace T = pm::tma;
+__global__ void __launch_bounds__(kAllThreads, 1)
+k_exit_wave_all(const int4 *__restrict__ units, int nunits, const ExitArgs *__restrict__ etab,
+                const TmaArgs *__restrict__ ttab, const TmaMaps *__restrict__ mtab, int *status) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    auto bin = [&](int s) { return (float2 *)(base + s * kTmaBuf); };
-    float2 *bout = (float2 *)(base + 2 * kTmaBuf);
-    float2 *tw = (float2 *)(base + 3 * kTmaBuf);                 // tw[k1 * 16 + t] = W_N^(t k1)
-    uint64_t *bar = (uint64_t *)(base + 3 * kTmaBuf + 256 * sizeof(float2));
-    __shared__ double s_red[kTmaThreads / 32];
-
+    float2 *tw256 = (float2 *)(base + kAllScratch);
+    float2 *tw128 = tw256 + 256, *tw64 = tw128 + 128, *tw16 = tw64 + 64;
+    __shared__ uint64_t s_bar[4];
+    __shared__ double s_red[kAllThreads / 32];
+    __shared__ uint32_t s_pending;
     const int tid = threadIdx.x;
-    const int t = tid & 15, g = tid >> 4;                        // g in [0, B)
-    const int h = g >> 4, gl = g & 15;                           // 16-wide box of the batch, row in it
-    if (tid < 256) {
-        double sn, cs;
-        sincospi(-2.0 * (double)((tid >> 4) * (tid & 15)) / (double)N, &sn, &cs);
-        tw[tid] = make_float2((float)cs, (float)sn);
-    }
-    if (tid == 0) {
-        T::mbar_init(&bar[0], 1);
-        T::mbar_init(&bar[1], 1);
-        T::fence_barrier_init();
-    }
-    __syncthreads();
-    uint32_t parity = 0u;                                        // bit s: phase parity of bar[s]
-    __shared__ uint32_t s_pending;                               // thread 0: bit s = a load into stage s is in flight
-    if (tid == 0) s_pending = 0u;
-    const int slot_col = blockIdx.x * N;                         // this CTA's slot columns
-    const float invN = 1.0f / (float)N;
-    const int M = a.M;
-    const uint64_t pol_keep = T::policy_keep(), pol_stream = T::policy_stream();
-    bool failed = false;                                         // uniform after each barrier
-    bool timed_out = false;                                      // this thread's waits
-    // After a wait gives up the kernel leaves its loop before waiting again, so the parity of
-    // a stage whose wait failed stays that of the load still in flight (drained at the end).
-    auto wait_stage = [&](int s) {
-        if (T::mbar_wait(&bar[s], (parity >> s) & 1u)) {
-            if (tid == 0) s_pending &= ~(1u << s);
-            parity ^= 1u << s;
+    TmaPipe p;
+    fill_twiddles128(tw128, tid, kAllThreads);
+    fill_twiddles<8>(tw64, tid, kAllThreads);
+    fill_twiddles<4>(tw16, tid, kAllThreads);
+    tma_pipe_init(p, base, tw256, s_bar, &s_pending, s_red, blockIdx.x * 256);   // ends with a barrier
+    for (int iu = blockIdx.x; iu < nunits && !p.failed; iu += gridDim.x) {
+        const int4 un = units[iu];                       // (kind, dataset, first position, count)
+        if (un.x == 256) {
+            tma_apply(p, tma_unit<32, XM_FULL>(p, ttab[un.y], mtab[un.y], un.z));
+        } else if (un.x == 128) {
+            all_unit128(etab[un.y], un.z, tw128, base, s_red);
         } else {
-            timed_out = true;
-        }
-    };
-    // Barrier A of every batch: the batch's input buffer is consumed, the staging buffer's
-    // previous store has finished reading it (thread 0 waited just before), and a timed-out
-    // wait anywhere in the CTA is agreed on.
-    auto barrier_a = [&]() {
-        if (tid == 0) T::wait_read<0>();
-        if (__syncthreads_or(timed_out)) failed = true;
-    };
-    // Staging buffer written: thread 0 stores it.
-    auto publish = [&](const CUtensorMap *map, int x0, int y0, int dx, int dy, uint64_t pol) {
-        T::fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            T::store_2d_hint(map, x0, y0, bout, pol);
-            if constexpr (B == 32) T::store_2d_hint(map, x0 + dx, y0 + dy, bout + 4096, pol);
-            T::commit();
-        }
-    };
-    auto prefetch = [&](int s, const CUtensorMap *map, int x, int y, uint64_t pol) {
-        if (tid == 0) {
-            s_pending |= 1u << s;
-            T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
-            T::load_2d_hint(bin(s), map, x, y, &bar[s], pol);
-        }
-    };
-
-    constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
-    const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
-    if (a.inject_wait) {
-        // Test hook (ptycho_debug_wait_timeout): a wait on a barrier that nothing arrives on,
-        // limited to ~2^20 cycles, before any copy is issued; the CTA then takes the timeout path.
-        if (tid == 0) {
-            T::mbar_init(&bar[2], 1);
-            T::fence_barrier_init();
-            if (!T::mbar_wait_for(&bar[2], 0u, 1ll << 20)) timed_out = true;
-        }
-        if (__syncthreads_or(timed_out)) failed = true;
-    }
-    for (int iu = blockIdx.x; iu < units && !failed; iu += gridDim.x) {
-        const int u = (XM == XM_LIST) ? a.list[iu] : iu;
-        const int j = kFull ? u : u / a.Q;
-        const int prow0 = kFull ? 0 : (u % a.Q) * N;              // first probe row of the mode
-        float err = 0.f;
-        if constexpr (XM != XM_INV) {
-        const int2 pj = a.pos[j];
-        // ---- phase R: forward row FFTs -> slot (column-major)
-        prefetch(0, &tm.prow, 0, prow0, pol_keep);
-        prefetch(1, &tm.prow, 0, prow0 + kTmaBatch, pol_keep);
-        float2 pO[R];                                      // object row of the next batch
-        {
-            const float2 *orow = a.obj + (size_t)(pj.x + g) * M + pj.y;
-#pragma unroll
-            for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
-        }
-        for (int b = 0; b < NB; ++b) {
-            const int s = b & 1;
-            wait_stage(s);
-            float2 *row = bin(s) + g * 256;
-            float2 d[R];
-#pragma unroll
-            for (int m = 0; m < R; ++m) d[m] = cmul(row[t + R * m], pO[m]);
-            if (b + 1 < NB) {
-                const float2 *orow = a.obj + (size_t)(pj.x + kTmaBatch * (b + 1) + g) * M + pj.y;
-#pragma unroll
-                for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
+            const int q = tid / kQuarter, qt = tid % kQuarter;
+            if (q < un.w) {
+                if (un.x == 64) all_unit_small<8>(etab[un.y], un.z + q, tw64, base, s_red, q, qt);
+                else all_unit_small<4>(etab[un.y], un.z + q, tw16, base, s_red, q, qt);
             }
-            pm::fft_group_xs<R, -1>(d, row, tw, t);
-            barrier_a();
-            if (failed) break;
-            if (b + 2 < NB) prefetch(s, &tm.prow, 0, prow0 + kTmaBatch * (b + 2), pol_keep);
-            float2 *ob = bout + h * 4096;
-#pragma unroll
-            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
-            publish(&tm.slot_r, kTmaBatch * b, slot_col, 16, 0, pol_keep);
-        }
-        if (failed) break;
-        if (tid == 0) T::wait_all<0>();                 // slot complete before phase C reads it
-        prefetch(0, &tm.slot_c, 0, slot_col, pol_stream);
-        prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch, pol_stream);
-        // ---- phase C: column FFTs (modulus replacement and inverse column FFTs in XM_FULL)
-        for (int b = 0; b < NB; ++b) {
-            const int s = b & 1;
-            const int c = kTmaBatch * b + g;
-            float A[R];                                   // A[k2] = |F psi| target at ky = t + 16 k2
-            if constexpr (kFull) {
-                const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c) * N + t * R);
-#pragma unroll
-                for (int v = 0; v < R / 4; ++v) {
-                    const float4 q = T::ldg_hint(amp + v, pol_stream);
-                    A[4 * v] = q.x; A[4 * v + 1] = q.y; A[4 * v + 2] = q.z; A[4 * v + 3] = q.w;
-                }
-            }
-            wait_stage(s);
-            float2 *col = bin(s) + g * 256;
-            float2 d[R];
-#pragma unroll
-            for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
-            pm::fft_group_xs<R, -1>(d, col, tw, t);
-            if constexpr (kFull) {
-                // d = N Psi (unnormalised transforms).  The projection A Psi / |Psi| does not
-                // depend on the scale of Psi, and the inverse transform's 1/N is folded into the
-                // projected amplitude, so neither unitary scaling costs a pass of its own.
-#pragma unroll
-                for (int m = 0; m < R; ++m) {
-                    const float2 X = d[m];
-                    const float mag2 = cabs2(X);
-                    if (mag2 > 0.f) {
-                        const float inv = rsqrtf(mag2);
-                        const float dm = mag2 * inv * invN - A[m];
-                        err += dm * dm;
-                        d[m] = cscale(X, A[m] * invN * inv);
-                    } else {
-                        err += A[m] * A[m];
-                        d[m] = make_float2(A[m] * invN, 0.f);
-                    }
-                }
-                pm::fft_group_xs<R, +1>(d, col, tw, t);
-            } else {
-#pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
-            }
-            barrier_a();
-            if (failed) break;
-            if (b + 2 < NB) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2), pol_stream);
-            float2 *ob = bout + h * 4096;
-#pragma unroll
-            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
-            publish(&tm.psi_c, kTmaBatch * b, u * N, 16, 0, pol_keep);
-        }
-        } else {
-        // ---- phase C (XM_INV): inverse column FFTs of psi[j][m] in place
-        auto load_psi_cols = [&](int s, int c0) {
-            if (tid == 0) {
-                s_pending |= 1u << s;
-                T::mbar_expect_tx(&bar[s], (uint32_t)kTmaBuf);
-                T::load_2d(bin(s), &tm.psi_c, c0, u * N, &bar[s]);
-                if constexpr (B == 32) T::load_2d(bin(s) + 4096, &tm.psi_c, c0 + 16, u * N, &bar[s]);
-            }
-        };
-        if (tid == 0) T::wait_all<0>();
-        load_psi_cols(0, 0);
-        load_psi_cols(1, kTmaBatch);
-        for (int b = 0; b < NB; ++b) {
-            const int s = b & 1;
-            wait_stage(s);
-            float2 d[R];
-            const float2 *colsw = bin(s) + h * 4096;
-#pragma unroll
-            for (int m = 0; m < R; ++m) d[m] = colsw[T::swz128_index(t + R * m, gl)];
-            if (__syncthreads_or(timed_out)) failed = true;      // batch read: regions free
-            if (failed) break;
-            pm::fft_group_xs<R, +1>(d, bin(s) + g * 256, tw, t);
-            barrier_a();
-            if (failed) break;
-            if (b + 2 < NB) load_psi_cols(s, kTmaBatch * (b + 2));
-            float2 *ob = bout + h * 4096;
-#pragma unroll
-            for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
-            publish(&tm.psi_c, kTmaBatch * b, u * N, 16, 0, pol_keep);
-        }
-        }
-        if (failed) break;
-        if constexpr (XM != XM_FWD) {
-        if (tid == 0) T::wait_all<0>();                 // psi columns complete before R'
-        prefetch(0, &tm.psi_r, 0, u * N, pol_stream);
-        prefetch(1, &tm.psi_r, 0, u * N + kTmaBatch, pol_stream);
-        // ---- phase R': inverse row FFTs of psi[u] -> psi'
-        for (int b = 0; b < NB; ++b) {
-            const int s = b & 1;
-            wait_stage(s);
-            float2 *row = bin(s) + g * 256;
-            float2 d[R];
-#pragma unroll
-            for (int m = 0; m < R; ++m) d[m] = row[t + R * m];
-            pm::fft_group_xs<R, +1>(d, row, tw, t);
-            barrier_a();
-            if (failed) break;
-            if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, u * N + kTmaBatch * (b + 2), pol_stream);
-            if constexpr (kFull) {                        // 1/N already applied in phase C
-#pragma unroll
-                for (int m = 0; m < R; ++m) bout[g * 256 + t + R * m] = d[m];
-            } else {
-#pragma unroll
-                for (int m = 0; m < R; ++m) bout[g * 256 + t + R * m] = cscale(d[m], invN);
-            }
-            publish(&tm.psi_w, 0, u * N + kTmaBatch * b, 0, 16, pol_stream);
-        }
-        }
-        if (failed) break;
-        if constexpr (kFull) {
-            double e = (double)err;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if ((tid & 31) == 0) s_red[tid >> 5] = e;
             __syncthreads();
-            if (tid == 0) a.err[j] = [&] {
-                double sum = 0.0;
-                for (int w = 0; w < kTmaThreads / 32; ++w) sum += s_red[w];
-                return sum;
-            }();
         }
-        if (tid == 0) T::wait_all<0>();                 // psi[u] complete; buffers free for u + 1
-        __syncthreads();
     }
-    if (tid == 0) {
-        // After a timeout: let every load still in flight land (bounded) before the CTA's
-        // shared memory is released, then drain the bulk stores.
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-            if (failed && ((s_pending >> s) & 1u)) T::mbar_wait(&bar[s], (parity >> s) & 1u);
-        T::wait_all<0>();
-        if (failed) atomicExch(a.status, 1);
-    }
+    tma_pipe_finish(p, status);
 }
 
 // Each warp parks its kTR x 32 register tile in shared memory; after one barrier, thread
@@ -1150,20 +943,24 @@ int setup_exit_tma(ptycho_ctx *h) {
 }
 
 // Tensor maps of the TMA kernel; called once the buffers exist.
-int encode_exit_tma(ptycho_ctx *h) {
-    const uint64_t N = (uint64_t)h->N, Q = (uint64_t)h->Q;
-    const uint32_t B = (uint32_t)h->tma_batch;
+// Tensor maps of the N = 256 kernel with B rows per stage over the given probe, psi and slot
+// buffers (slots: `slots` column-major 256 x 256 tiles).
+int encode_tma_maps(TmaMaps *tm, float2 *probe, float2 *psi, float2 *slot, int Q, int J, int slots, int B) {
+    const uint64_t N = 256;
     const CUtensorMapDataType c64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;    // one complex64 = 8 bytes
-    const uint64_t psi_rows = N * Q * (uint64_t)h->J;
+    const uint64_t psi_rows = N * (uint64_t)Q * (uint64_t)J;
+    const uint32_t b = (uint32_t)B;
     int rc;
-    if ((rc = encode_2d(&h->tm.prow, h->d_probe, c64, 8, N, N * Q, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
-    if ((rc = encode_2d(&h->tm.slot_r, h->d_slot, c64, 8, N, N * h->grid_exit, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B)))
-        return rc;
-    if ((rc = encode_2d(&h->tm.slot_c, h->d_slot, c64, 8, N, N * h->grid_exit, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE)))
-        return rc;
-    if ((rc = encode_2d(&h->tm.psi_c, h->d_psi, c64, 8, N, psi_rows, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
-    if ((rc = encode_2d(&h->tm.psi_r, h->d_psi, c64, 8, N, psi_rows, 256, B, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
-    return encode_2d(&h->tm.psi_w, h->d_psi, c64, 8, N, psi_rows, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
+    if ((rc = encode_2d(&tm->prow, probe, c64, 8, N, N * Q, 256, b, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = encode_2d(&tm->slot_r, slot, c64, 8, N, N * slots, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = encode_2d(&tm->slot_c, slot, c64, 8, N, N * slots, 256, b, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    if ((rc = encode_2d(&tm->psi_c, psi, c64, 8, N, psi_rows, 16, 256, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = encode_2d(&tm->psi_r, psi, c64, 8, N, psi_rows, 256, b, CU_TENSOR_MAP_SWIZZLE_NONE))) return rc;
+    return encode_2d(&tm->psi_w, psi, c64, 8, N, psi_rows, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+int encode_exit_tma(ptycho_ctx *h) {
+    return encode_tma_maps(&h->tm, h->d_probe, h->d_psi, h->d_slot, h->Q, h->J, h->grid_exit, h->tma_batch);
 }
 
 TmaArgs tma_args(ptycho_ctx *h) {
@@ -1751,6 +1548,15 @@ struct ptycho_batch_ctx {
     std::vector<char> cap_mask;
     int *d_status = nullptr;
     std::string describe;
+    // one persistent exit-wave launch for every single-mode radix dataset (k_exit_wave_all)
+    bool one_launch = false;
+    std::vector<char> in_all;                 // dataset i's exit waves are in the one launch
+    int4 *d_units = nullptr;
+    int nunits = 0, grid_all = 0;
+    ExitArgs *d_etab = nullptr;
+    TmaArgs *d_ttab = nullptr;
+    TmaMaps *d_mtab = nullptr;
+    float2 *d_slot = nullptr;                 // one 256 x 256 slot per CTA of the one launch
 };
 
 namespace {
@@ -1774,6 +1580,9 @@ void free_batch(ptycho_batch_ctx *b) {
     if (b->st) cudaStreamDestroy(b->st);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
     if (b->d_status) cudaFree(b->d_status);
+    void *ptrs[] = {b->d_units, b->d_etab, b->d_ttab, b->d_mtab, b->d_slot};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
     delete b;
 }
 
@@ -1796,8 +1605,13 @@ int launch_class(ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &c, cudaStre
 
 // Enqueue one iteration of every dataset on the batch stream (fork / join over side streams).
 int enqueue_iteration(ptycho_batch_ctx *b, const std::vector<char> &upd) {
+    if (b->one_launch) {
+        k_exit_wave_all<<<b->grid_all, kAllThreads, all_smem_bytes(), b->st>>>(b->d_units, b->nunits, b->d_etab,
+                                                                               b->d_ttab, b->d_mtab, b->d_status);
+        PM_LAUNCHED("k_exit_wave_all");
+    }
     PM_CUDA(cudaEventRecord(b->ev_fork, b->st));
-    for (size_t c = 0; c < b->cls.size(); ++c) {
+    for (size_t c = 0; c < b->cls.size() && !b->one_launch; ++c) {
         PM_CUDA(cudaStreamWaitEvent(b->cls_st[c], b->ev_fork, 0));
         int rc = launch_class(b, b->cls[c], b->cls_st[c]);
         if (rc) return rc;
@@ -1807,13 +1621,14 @@ int enqueue_iteration(ptycho_batch_ctx *b, const std::vector<char> &upd) {
         ptycho_ctx *h = b->hs[i];
         cudaStream_t s = b->side[i];
         PM_CUDA(cudaStreamWaitEvent(s, b->ev_fork, 0));
-        const int c = b->cls_of[i];
+        const int c = b->one_launch ? -1 : b->cls_of[i];
         if (c >= 0) PM_CUDA(cudaStreamWaitEvent(s, b->ev_cls[c], 0));
         cudaStream_t saved = h->st;
         const bool timing = h->timing;                 // no per-stage events inside a batch
         h->st = s;
         h->timing = false;
-        const int rc = iterate_one(h, h->d_err_batch, 0, upd[i] != 0, c >= 0);
+        const bool exit_done = b->one_launch ? b->in_all[i] != 0 : c >= 0;
+        const int rc = iterate_one(h, h->d_err_batch, 0, upd[i] != 0, exit_done);
         h->st = saved;
         h->timing = timing;
         if (rc) return rc;
@@ -1920,11 +1735,11 @@ int autotune(ptycho_batch_ctx *b) {
     bool need = false;                     // anything not in the cache?  (else no snapshot)
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        for (const auto &c : b->cls) need = need || !g_tune_cache.count(class_key(b, c));
+        for (const auto &c : b->cls) need = need || (!b->one_launch && !g_tune_cache.count(class_key(b, c)));
         std::string bkey = "tma:";
         bool any = false;
         for (ptycho_ctx *h : b->hs)
-            if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP) {
+            if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch) {
                 bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
                 any = true;
             }
@@ -1945,7 +1760,7 @@ int autotune(ptycho_batch_ctx *b) {
     char buf[256];
     int cached = 0;
     // grids of the multi-dataset classes
-    for (size_t c = 0; c < b->cls.size() && !rc; ++c) {
+    for (size_t c = 0; c < b->cls.size() && !rc && !b->one_launch; ++c) {
         auto &k = b->cls[c];
         const std::string key = class_key(b, k);
         {
@@ -1990,7 +1805,7 @@ int autotune(ptycho_batch_ctx *b) {
     // rows per TMA stage of the N = 256 datasets (all together)
     std::vector<ptycho_ctx *> big;
     for (ptycho_ctx *h : b->hs)
-        if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP) big.push_back(h);
+        if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch) big.push_back(h);
     std::string bkey = "tma:";
     for (ptycho_ctx *h : big) bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
     int bcached = 0;
@@ -2047,6 +1862,60 @@ int autotune(ptycho_batch_ctx *b) {
     return rc;
 }
 
+// The unit list and dataset tables of the one persistent exit-wave launch (k_exit_wave_all):
+// every single-mode, full-batch, radix-FFT dataset; the others keep their own launches.
+int setup_one_launch(ptycho_batch_ctx *b) {
+    const int n = (int)b->hs.size();
+    b->in_all.assign(n, 0);
+    std::vector<ExitArgs> et(n);
+    std::vector<TmaArgs> tt(n);
+    std::vector<int4> units;
+    const int kinds[4] = {256, 128, 64, 16};
+    for (int k : kinds)
+        for (int i = 0; i < n; ++i) {
+            ptycho_ctx *h = b->hs[i];
+            if (h->Q != 1 || h->fft_gemm || h->N != k) continue;
+            b->in_all[i] = 1;
+            const int per = (k <= 64) ? 4 : 1;             // positions per unit (one per CTA quarter)
+            for (int j0 = 0; j0 < h->J; j0 += per) units.push_back(make_int4(k, i, j0, std::min(per, h->J - j0)));
+        }
+    if (units.empty()) return PTYCHO_OK;
+    b->grid_all = std::min<int>((int)units.size(), b->sms);
+    bool any256 = false;
+    for (int i = 0; i < n; ++i) {
+        ptycho_ctx *h = b->hs[i];
+        ExitArgs a{};
+        a.obj = h->d_obj; a.probe = h->d_probe; a.amp = h->d_amp; a.pos = h->d_pos; a.psi = h->d_psi;
+        a.err = h->d_err_pos; a.M = h->M; a.J = h->J; a.Q = 1;
+        et[i] = a;
+        tt[i] = tma_args(h);
+        tt[i].status = b->d_status;
+        tt[i].list = nullptr;
+        tt[i].count = 0;
+        any256 = any256 || (b->in_all[i] && h->N == 256);
+    }
+    int rc;
+    std::vector<TmaMaps> mt(n);
+    if (any256 && (rc = dalloc(&b->d_slot, (size_t)b->grid_all * 256 * 256))) return rc;
+    for (int i = 0; i < n; ++i) {
+        ptycho_ctx *h = b->hs[i];
+        if (b->in_all[i] && h->N == 256 &&
+            (rc = encode_tma_maps(&mt[i], h->d_probe, h->d_psi, b->d_slot, 1, h->J, b->grid_all, 32)))
+            return rc;
+    }
+    if ((rc = dalloc(&b->d_units, units.size())) || (rc = dalloc(&b->d_etab, (size_t)n)) ||
+        (rc = dalloc(&b->d_ttab, (size_t)n)) || (rc = dalloc(&b->d_mtab, (size_t)n)))
+        return rc;
+    PM_CUDA(cudaMemcpy(b->d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    PM_CUDA(cudaMemcpy(b->d_etab, et.data(), n * sizeof(ExitArgs), cudaMemcpyHostToDevice));
+    PM_CUDA(cudaMemcpy(b->d_ttab, tt.data(), n * sizeof(TmaArgs), cudaMemcpyHostToDevice));
+    PM_CUDA(cudaMemcpy(b->d_mtab, mt.data(), n * sizeof(TmaMaps), cudaMemcpyHostToDevice));
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)all_smem_bytes()));
+    b->nunits = (int)units.size();
+    b->one_launch = true;
+    return PTYCHO_OK;
+}
+
 }  // namespace
 
 extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handles, int n, int flags,
@@ -2054,7 +1923,7 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
     if (!out) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: out is NULL");
     *out = nullptr;
     if (!handles || n < 1) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: need n >= 1 handles");
-    if (flags & ~(PTYCHO_BATCH_GRAPH | PTYCHO_BATCH_AUTOTUNE))
+    if (flags & ~(PTYCHO_BATCH_GRAPH | PTYCHO_BATCH_AUTOTUNE | PTYCHO_BATCH_ONE_LAUNCH))
         return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: unknown flags 0x%x", flags);
     for (int i = 0; i < n; ++i) {
         if (!handles[i]) return pm::fail(PTYCHO_EINVAL, "ptycho_batch_create: handle %d is NULL", i);
@@ -2151,6 +2020,7 @@ extern "C" int ptycho_batch_create(ptycho_batch *out, const ptycho_handle *handl
             (e = cudaEventCreateWithFlags(&b->ev_in[i], cudaEventDisableTiming)))
             return bail(pm::cuda_fail(e, "ptycho_batch_create: streams"));
     }
+    if ((flags & PTYCHO_BATCH_ONE_LAUNCH) && (rc = setup_one_launch(b))) return bail(rc);
     b->cls_st.assign(b->cls.size(), nullptr);
     b->ev_cls.assign(b->cls.size(), nullptr);
     for (size_t c = 0; c < b->cls.size(); ++c)

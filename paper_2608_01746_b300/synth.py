@@ -99,9 +99,10 @@ CONFIGS = {
 # layers bring a 128^2 input to an 8^2 bottleneck, so the bottleneck sees most of the pattern
 # (a far-field pattern mixes every object pixel into every detector pixel).  Input: the fused
 # pattern binned to (N/2)^2, one channel; output: the (N/4)^2 coarse object patch, two channels
-# (real, imaginary).  1.35 M weights.
-WARM_NET = ((1, 32, "s2"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (256, 256, "s1"),
-            (256, 128, "up"), (128, 64, "up"), (64, 2, "up"))
+# (real, imaginary).  2.05 M weights (the widest layers at the 8^2 bottleneck and the first
+# up-sampling step).
+WARM_NET = ((1, 32, "s2"), (32, 64, "s2"), (64, 128, "s2"), (128, 256, "s2"), (256, 384, "s1"),
+            (384, 192, "up"), (192, 64, "up"), (64, 2, "up"))
 
 
 def batched_configs(seed: int | None = None, count: int = 64) -> list:
@@ -257,8 +258,9 @@ def make_scan_torch(cfg: ScanConfig | str, seed: int | None = None, device="cuda
                     chunk: int = 64) -> dict:
     """Same recipe as ``make_scan``; frames simulated with torch on ``device``.
 
-    Returns obj/probe/pos as numpy (complex128 / int32) and ``raw`` as a device tensor of dtype
-    torch.uint16 with shape [J][K][N][N].
+    Returns obj/probe/pos as numpy (complex128 / int32), ``raw`` as a device tensor of dtype
+    torch.uint16 with shape [J][K][N][N] and ``intensity`` (expected counts of the longest
+    exposure, noiseless and unclipped, DC-centred) as a float32 device tensor [J][N][N].
     """
     import torch
 
@@ -304,4 +306,4 @@ def make_scan_torch(cfg: ScanConfig | str, seed: int | None = None, device="cuda
     if cfg.modes == 1:
         probe = probe[0]
     return {"cfg": cfg, "obj": obj, "probe": probe, "pos": pos, "times": np.asarray(cfg.times),
-            "clip_value": float(cfg.clip), "raw": raw, "seed": seed}
+            "clip_value": float(cfg.clip), "raw": raw, "intensity": inten, "seed": seed}

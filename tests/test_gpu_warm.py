@@ -126,10 +126,16 @@ def test_warm_network_matches_oracle(api):
         dw, db = api.wsnet_get_grads(net, i)
         errs.append((rel_l2(dw, grads[i][0]), rel_l2(db, grads[i][1])))
     print("per-layer gradient rel L2 (w, b):", [(f"{a:.1e}", f"{b:.1e}") for a, b in errs])
+    # Both sides store dL/dz in BF16 at the same points; where FP32 and FP64 accumulation put a
+    # value on different sides of a BF16 rounding boundary the stored values differ, and layer i's
+    # gradient passes the L - i backward storage points between the loss and layer i, each
+    # adding at most one relative rounding U (first-order bound (L - i) U; measured with the
+    # 2.05 M-weight layout: 1.1e-4 at the last layer, 3.8e-3 at the first).
+    L = len(layers)
     worst = max(max(e) for e in errs)
     for i, e in enumerate(errs):
-        assert max(e) <= U, (i, e)
-    print(f"worst gradient rel L2 {worst:.2e} (bound {U:.2e})")
+        assert max(e) <= (L - i) * U, (i, e)
+    print(f"worst gradient rel L2 {worst:.2e} (first-layer bound {L * U:.2e})")
     api.wsnet_destroy(net)
 
 
