@@ -910,13 +910,14 @@ int setup_tma_kernel(ptycho_ctx *h, int *per_sm) {
     return PTYCHO_OK;
 }
 
-// Batch size of the N = 256 kernel (rows per stage): 32 (one 512-thread CTA per SM: 148 live
-// slots, 77 MB, which the L2 keeps) unless PTYCHO_TMA_BATCH = 16 (two 256-thread CTAs per SM).
-// The mixed-state forward/inverse kernels use 16.
+// Batch size of the N = 256 kernel (rows per stage): 16, two 256-thread CTAs per SM (measured
+// at lab scale: 1.083 ms per launch; 32, one 512-thread CTA per SM whose 148 live slots the L2
+// keeps, moves 1.23 instead of 1.84 MB of DRAM traffic per position but takes 1.106 ms), unless
+// PTYCHO_TMA_BATCH = 32.  The mixed-state forward/inverse kernels use 16.
 int tma_batch_choice(int Q) {
     const char *env = std::getenv("PTYCHO_TMA_BATCH");
-    if (Q != 1 || (env && std::atoi(env) == 16)) return 16;
-    return 32;
+    if (Q == 1 && env && std::atoi(env) == 32) return 32;
+    return 16;
 }
 
 int setup_exit_tma(ptycho_ctx *h) {
