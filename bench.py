@@ -45,10 +45,10 @@ def parse():
                          "8 incoherent probe modes, 100 iterations; wide64: 64^2 probe, 9216 "
                          "raster positions on a 1024^2 object, 50 iterations; wide128: 128^2 probe, "
                          "2304 positions, 50 iterations; batched: 64 uneven "
-                         "datasets (N in {64, 256}, 49-900 positions) in one batch, 50 iterations; warm: "
+                         "datasets (N in {64, 128, 256}, 49-900 positions) in one batch, 50 iterations; warm: "
                          "train the warm-start network, then time to NRMSE from it vs the flat object")
     ap.add_argument("--fft", choices=["radix_fp32", "dftgemm_bf16x3"], default="radix_fp32",
-                    help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64, 128)")
+                    help="FFT form of the exit-wave step (dftgemm_bf16x3: tensor cores, N = 64, 128, 256)")
     ap.add_argument("--iters", type=int, default=None,
                     help="override the iteration count (profiling runs only; not a bench value)")
     ap.add_argument("--positions", type=int, default=None,
@@ -168,7 +168,10 @@ def exit_wave_flops_per_position(N: int) -> float:
 def dftgemm_flops_per_position(N: int) -> float:
     """Tensor-core flops of the split-BF16 exit wave: 4 real GEMM passes, 3 split terms each.
     N = 64: the 128 x 128 real DFT matrix times the 128 x 64 interleaved operand of a patch.
-    N = 128: the same 64-point matrix times two halves (even / odd samples) of 128 vectors."""
+    N = 128: the same 64-point matrix times two halves (even / odd samples) of 128 vectors.
+    N = 256: the same matrix times the four decimated quarters (x[4 r + q]) of 256 vectors."""
+    if N == 256:
+        return 4 * 3 * 2.0 * 128 * 128 * (4 * 256)
     if N == 128:
         return 4 * 3 * 2.0 * 128 * 128 * 256
     return 4 * 3 * 2.0 * (2 * N) * (2 * N) * N
@@ -205,7 +208,7 @@ def iteration_flops_per_update(N: int) -> float:
 # positions, one launch: dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256, first 16 hex digits).  A changed kernel
 # reports traffic null until it is captured again.
-EXIT_TRAFFIC = {"sources_sha16": "6a4e570a7d13ebad", "bytes_per_position": 1844193,
+EXIT_TRAFFIC = {"sources_sha16": "b710b654f18d5d72", "bytes_per_position": 1846878,
                 "capture": "ncu, k_exit_wave_tma<16, FULL>, one launch over 400 lab positions"}
 
 
@@ -245,7 +248,7 @@ def run_batched(args, world, rank, local):
     updates_per_iter = sum(J_all)
 
     def fft_for(c, fft):
-        return fft if c.N in (64, 128) else "radix_fp32"
+        return fft
 
     def make_handles(fft, raws=None):
         for d, c in enumerate(cfgs):
@@ -373,7 +376,7 @@ def run_batched(args, world, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate for N = 64, 128; f32 for N = 256",
+        "dtype": "f32" if args.fft == "radix_fp32" else "bf16x3 (split) with f32 accumulate",
         "data": "synthetic (seeded jittered raster scans, Poisson counts, 12-bit clip)",
         "config": {"workload": (f"batched: 64 uneven datasets ("
                                 + ", ".join(f"{v} with {n}^2 probes" for n, v in by_n.items()) + "), "
@@ -645,7 +648,8 @@ def run_ours(args, world, rank, local):
     if args.fft == "dftgemm_bf16x3":
         tflops = dftgemm_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
         bf16_peak, bf16_kind = bf16_peak_tflops()
-        roof = {"kernel": f"k_dft{N}_gemm<exit> (tcgen05 split-BF16 DFT-GEMM)", "bound": "tensor",
+        kn = "k_exit_wave_tma<16, FULL, tensor cores>" if N == 256 else f"k_dft{N}_gemm<exit>"
+        roof = {"kernel": f"{kn} (tcgen05 split-BF16 DFT-GEMM)", "bound": "tensor",
                 "achieved": round(tflops, 2), "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": round(tflops / bf16_peak, 4), "peak_kind": bf16_kind,
                 "flops_per_position": dftgemm_flops_per_position(N),

@@ -138,7 +138,9 @@ enum { PTYCHO_ALG_AP = 0, PTYCHO_ALG_EPIE_COLOUR = 1 };
 /* FFT form of the exit-wave step (the paper prescribes none):
  *   RADIX_FP32        FP32 radix FFTs on the CUDA cores (default; N = 16, 64, 128, 256)
  *   DFTGEMM_BF16X3    split-BF16 3-term DFT-by-GEMM on the tensor cores, FP32 accumulation
- *                     (see dft2_split_bf16); N = 64 or 128, one probe mode, algorithm AP. */
+ *                     (see dft2_split_bf16); N = 64, 128 or 256 (256 = four 64-point GEMMs of
+ *                     the decimated quarters x[4 r + q] and a radix-4 epilogue, in the N = 256
+ *                     kernel's TMA slot pipeline); one probe mode, algorithm AP. */
 enum { PTYCHO_FFT_RADIX_FP32 = 0, PTYCHO_FFT_DFTGEMM_BF16X3 = 1 };
 
 typedef struct {

@@ -78,16 +78,7 @@ struct Args {
     int ntable;
 };
 
-__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
-
-// (re, im) -> packed hi word and lo word (re in the low half: the lower K index).
-__device__ __forceinline__ void split2(float2 z, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
-    const float2 r = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(z.x - r.x, z.y - r.y);
-    hi = bf2_bits(h);
-    lo = bf2_bits(l);
-}
+using tc::split2;
 
 __global__ void k_fill_dft64() {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -631,6 +622,15 @@ int dft64_prepare(int *sm_count) {
     PM_LAUNCHED("k_fill_dft64");
     PM_CUDA(cudaDeviceSynchronize());
     if (dev >= 0 && dev < 64) g_ready[dev] = true;
+    return PTYCHO_OK;
+}
+
+int dft64_matrix(const void **d_matrix) {
+    int sms = 0, rc = dft64_prepare(&sms);
+    if (rc) return rc;
+    void *p = nullptr;
+    PM_CUDA(cudaGetSymbolAddress(&p, g_dft64));
+    *d_matrix = p;
     return PTYCHO_OK;
 }
 

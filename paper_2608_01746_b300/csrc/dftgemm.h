@@ -27,6 +27,10 @@ int dft64_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
 // The same for N = 128 (two 64-point halves and a radix-2 butterfly per pass; one launch).
 int dft128_exit_launch(const Dft64Exit &e, int sm_count, cudaStream_t st);
 
+// Device address of the split 64-point DFT matrix (G_hi then G_lo, 128 x 128 BF16 each in the
+// tcgen05 core-matrix layout, 64 KB), built by dft64_prepare (which this call makes first).
+int dft64_matrix(const void **d_matrix);
+
 // Patch groups the kernel makes of J positions (the unit of work of one pipeline).
 int dft64_groups(int J);
 

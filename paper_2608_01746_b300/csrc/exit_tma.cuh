@@ -29,6 +29,7 @@ struct TmaArgs {
     int count;
     int M, J, Q;
     int inject_wait;         // test hook: wait on a barrier nothing arrives on (short limit) first
+    const uint4 *gmat;       // tensor-core form: the split 64-point DFT matrix (64 KB, global)
 };
 
 struct TmaMaps {
@@ -59,7 +60,93 @@ struct TmaPipe {
     bool timed_out;          // this thread's waits
     int slot_col;            // this CTA's slot columns
     uint64_t pol_keep, pol_stream;
+    // tensor-core form only
+    unsigned char *gs;       // the split DFT matrix in shared memory (G_hi, G_lo)
+    unsigned char *op;       // operand of one pass (B_hi, B_lo: 64 rows x 128 K each)
+    uint32_t tmem;           // 64 FP32 accumulator columns
+    uint32_t mphase;         // phase parity of the MMA barrier bar[3]
+    float2 twq[3];           // W_256^(q u), q = 1, 2, 3, for this thread's accumulator lane u
 };
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core 256-point DFT of the 16 vectors of one stage buffer (the fft_path DFTGEMM form
+// at N = 256), in place, by 256 threads.  256 = 4 x 64: the 64-point DFTs of the four decimated
+// sub-sequences x[4 r + q] are one split-BF16 GEMM against the resident 64-point matrix (operand
+// row 4 v + q, K index 2 r + s; accumulator lane 2 u + s', column 4 v + q holds part s' of
+// E_q[u]); the epilogue combines them with a radix-4 step,
+//   X[u + 64 m] = sum_q (-i)^(q m) W_256^(q u) E_q[u],
+// lane pairs (s' = 0, 1) exchanging their halves with one shuffle per value.  The inverse is
+// the forward transform by conjugation (unnormalised, like the radix path).  Returns false
+// (uniformly) when the MMA completion wait gave up.
+__device__ __forceinline__ bool tc_dft256(float2 *buf, bool inverse, const TmaPipe &p, uint32_t &mphase) {
+    namespace T = pm::tma;
+    const int tid = threadIdx.x;
+    {
+        const int v = tid >> 4, t = tid & 15, q = t & 3;
+        unsigned char *oh = p.op, *ol = p.op + 16384;
+#pragma unroll 4
+        for (int sI = 0; sI < 16; ++sI) {
+            const int e = 16 * sI + t;                            // element of vector v
+            float2 z = buf[v * 256 + e];
+            if (inverse) z.y = -z.y;
+            uint32_t hw, lw;
+            pm::tc::split2(z, hw, lw);
+            const uint32_t off = pm::tc::core_offset(4 * v + q, 2 * (e >> 2), 128);
+            *reinterpret_cast<uint32_t *>(oh + off) = hw;
+            *reinterpret_cast<uint32_t *>(ol + off) = lw;
+        }
+    }
+    T::fence_async_smem();                                        // operand writes -> tensor core
+    pm::tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        pm::tc::fence_after();
+        constexpr uint32_t idesc = pm::tc::idesc_bf16_f32(128, 64);
+        const uint32_t gh = pm::tc::smem_addr(p.gs), gl = gh + 32768;
+        const uint32_t bh = pm::tc::smem_addr(p.op), bl = bh + 16384;
+#pragma unroll
+        for (int term = 0; term < 3; ++term) {                    // hi hi, hi lo, lo hi
+            const uint32_t ab = (term == 2) ? gl : gh, bb = (term == 1) ? bl : bh;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+                pm::tc::mma_bf16(p.tmem, pm::tc::smem_desc(ab + ks * 256, 128, 2048),
+                                 pm::tc::smem_desc(bb + ks * 256, 128, 2048), idesc, (uint32_t)((term | ks) != 0));
+        }
+        pm::tc::commit(&p.bar[3]);
+    }
+    const bool ok = T::mbar_wait(&p.bar[3], mphase);
+    if (__syncthreads_or(!ok)) return false;                      // the MMAs are drained at the end
+    mphase ^= 1u;
+    pm::tc::fence_after();
+    const int w = tid >> 5, lane = tid & 31, lq = w & 3, ch = w >> 2;
+    const int u = 16 * lq + (lane >> 1), part = lane & 1;
+    uint32_t r[32];
+    pm::tc::ld_32cols(p.tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(32 * ch), r);
+    pm::tc::wait_ld();
+#pragma unroll
+    for (int vv = 0; vv < 8; ++vv) {
+        float2 E[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float a = __uint_as_float(r[4 * vv + q]);
+            const float y = __shfl_xor_sync(0xffffffffu, a, 1);
+            E[q] = part ? make_float2(y, a) : make_float2(a, y);
+        }
+        const float2 Y1 = cmul(p.twq[0], E[1]), Y2 = cmul(p.twq[1], E[2]), Y3 = cmul(p.twq[2], E[3]);
+        const float2 A0 = cadd(E[0], Y2), A1 = csub(E[0], Y2), B0 = cadd(Y1, Y3), B1 = csub(Y1, Y3);
+        const float2 mB1 = make_float2(B1.y, -B1.x);              // -i B1
+        float2 X0, X1;
+        if (part == 0) { X0 = cadd(A0, B0); X1 = cadd(A1, mB1); }  // m = 0, 1
+        else { X0 = csub(A0, B0); X1 = csub(A1, mB1); }            // m = 2, 3
+        if (inverse) { X0.y = -X0.y; X1.y = -X1.y; }
+        float2 *o = buf + (8 * ch + vv) * 256 + u + 128 * part;
+        o[0] = X0;
+        o[64] = X1;
+    }
+    pm::tc::fence_before();
+    __syncthreads();                                              // buffer complete, TMEM read
+    return true;
+}
 
 // Every copy carries an L2 cache policy: the probe rows, the slot and the intermediate psi
 // columns (re-read by this CTA within the position) are kept, data read for the last time and
@@ -67,13 +154,17 @@ struct TmaPipe {
 // position with B = 32).  One unit: position j (or (j, m) for the mixed-state forms).  After a
 // wait gives up the unit returns with p.failed set (uniformly) before waiting again, so the parity
 // of a stage whose wait failed stays that of the load still in flight (tma_pipe_finish drains it).
-// Returns the updated mutable state: bits 0-1 parity, bit 2 failed, bit 3 timed out.
-__host__ __device__ constexpr uint32_t tma_state(uint32_t parity, bool failed, bool timed_out) {
-    return parity | (failed ? 4u : 0u) | (timed_out ? 8u : 0u);
+// Returns the updated mutable state: bits 0-1 parity, bit 2 failed, bit 3 timed out, bit 4 the
+// MMA barrier's phase parity (tensor-core form).
+__host__ __device__ constexpr uint32_t tma_state(uint32_t parity, bool failed, bool timed_out, uint32_t mphase = 0) {
+    return parity | (failed ? 4u : 0u) | (timed_out ? 8u : 0u) | (mphase << 4);
 }
 
-template <int B, int XM>
+// TC: the 256-point transforms on the tensor cores (tc_dft256) instead of the FP32 radix FFT;
+// 16-row stages, one-mode XM_FULL only.
+template <int B, int XM, bool TC = false>
 __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a, const TmaMaps &tm, int u) {
+    static_assert(!TC || (B == 16 && XM == XM_FULL), "tensor-core form: 16-row stages, XM_FULL");
     constexpr int R = 16, N = 256, NB = N / B;
     constexpr int kTmaThreads = B * 16, kTmaBatch = B;
     constexpr size_t kTmaBuf = tma_buf_bytes<B>();
@@ -88,7 +179,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
     uint64_t *bar = p.bar;
     const float invN = 1.0f / (float)N;
     const int M = a.M;
-    uint32_t parity = p.parity;
+    uint32_t parity = p.parity, mphase = p.mphase;
     bool failed = p.failed, timed_out = p.timed_out;
     auto wait_stage = [&](int s) {
         if (T::mbar_wait(&bar[s], (parity >> s) & 1u)) {
@@ -149,9 +240,20 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
 #pragma unroll
                 for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
             }
-            pm::fft_group_xs<R, -1>(d, row, tw, t);
+            if constexpr (TC) {
+#pragma unroll
+                for (int m = 0; m < R; ++m) row[t + R * m] = d[m];
+                __syncthreads();
+                if (!tc_dft256(bin(s), false, p, mphase)) failed = true;
+                else {
+#pragma unroll
+                    for (int m = 0; m < R; ++m) d[m] = row[t + R * m];
+                }
+            } else {
+                pm::fft_group_xs<R, -1>(d, row, tw, t);
+            }
             barrier_a();
-            if (failed) return tma_state(parity, failed, timed_out);
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
             if (b + 2 < NB) prefetch(s, &tm.prow, 0, prow0 + kTmaBatch * (b + 2), p.pol_keep);
             float2 *ob = bout + h * 4096;
 #pragma unroll
@@ -162,24 +264,41 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
         prefetch(0, &tm.slot_c, 0, slot_col, p.pol_stream);
         prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch, p.pol_stream);
         // ---- phase C: column FFTs (modulus replacement and inverse column FFTs in XM_FULL)
+        float4 An[R / 4];                                         // amplitudes of the next column
+        if constexpr (kFull) {
+            const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + g) * N + t * R);
+#pragma unroll
+            for (int v = 0; v < R / 4; ++v) An[v] = T::ldg_hint(amp + v, p.pol_stream);
+        }
         for (int b = 0; b < NB; ++b) {
             const int s = b & 1;
             const int c = kTmaBatch * b + g;
             float A[R];                                           // A[k2] = |F psi| target at ky = t + 16 k2
             if constexpr (kFull) {
-                const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c) * N + t * R);
 #pragma unroll
                 for (int v = 0; v < R / 4; ++v) {
-                    const float4 q = T::ldg_hint(amp + v, p.pol_stream);
-                    A[4 * v] = q.x; A[4 * v + 1] = q.y; A[4 * v + 2] = q.z; A[4 * v + 3] = q.w;
+                    A[4 * v] = An[v].x; A[4 * v + 1] = An[v].y; A[4 * v + 2] = An[v].z; A[4 * v + 3] = An[v].w;
+                }
+                if (b + 1 < NB) {
+                    const float4 *amp =
+                        reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c + kTmaBatch) * N + t * R);
+#pragma unroll
+                    for (int v = 0; v < R / 4; ++v) An[v] = T::ldg_hint(amp + v, p.pol_stream);
                 }
             }
             wait_stage(s);
             float2 *col = bin(s) + g * 256;
             float2 d[R];
+            if constexpr (TC) {
+                if (__syncthreads_or(timed_out)) failed = true;           // stage arrived everywhere
+                if (failed || !tc_dft256(bin(s), false, p, mphase)) {
+                    failed = true;
+                    return tma_state(parity, failed, timed_out, mphase);
+                }
+            }
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
-            pm::fft_group_xs<R, -1>(d, col, tw, t);
+            if constexpr (!TC) pm::fft_group_xs<R, -1>(d, col, tw, t);
             if constexpr (kFull) {
                 // d = N Psi (unnormalised transforms).  The projection A Psi / |Psi| does not
                 // depend on the scale of Psi, and the inverse transform's 1/N is folded into the
@@ -198,13 +317,24 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
                         d[m] = make_float2(A[m] * invN, 0.f);
                     }
                 }
-                pm::fft_group_xs<R, +1>(d, col, tw, t);
+                if constexpr (TC) {
+#pragma unroll
+                    for (int m = 0; m < R; ++m) col[t + R * m] = d[m];
+                    __syncthreads();
+                    if (!tc_dft256(bin(s), true, p, mphase)) failed = true;
+                    else {
+#pragma unroll
+                        for (int m = 0; m < R; ++m) d[m] = col[t + R * m];
+                    }
+                } else {
+                    pm::fft_group_xs<R, +1>(d, col, tw, t);
+                }
             } else {
 #pragma unroll
                 for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
             }
             barrier_a();
-            if (failed) return tma_state(parity, failed, timed_out);
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
             if (b + 2 < NB) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2), p.pol_stream);
             float2 *ob = bout + h * 4096;
 #pragma unroll
@@ -232,10 +362,10 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = colsw[T::swz128_index(t + R * m, gl)];
             if (__syncthreads_or(timed_out)) failed = true;   // batch read: regions free
-            if (failed) return tma_state(parity, failed, timed_out);
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
             pm::fft_group_xs<R, +1>(d, bin(s) + g * 256, tw, t);
             barrier_a();
-            if (failed) return tma_state(parity, failed, timed_out);
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
             if (b + 2 < NB) load_psi_cols(s, kTmaBatch * (b + 2));
             float2 *ob = bout + h * 4096;
 #pragma unroll
@@ -253,11 +383,18 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             wait_stage(s);
             float2 *row = bin(s) + g * 256;
             float2 d[R];
+            if constexpr (TC) {
+                if (__syncthreads_or(timed_out)) failed = true;
+                if (failed || !tc_dft256(bin(s), true, p, mphase)) {
+                    failed = true;
+                    return tma_state(parity, failed, timed_out, mphase);
+                }
+            }
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = row[t + R * m];
-            pm::fft_group_xs<R, +1>(d, row, tw, t);
+            if constexpr (!TC) pm::fft_group_xs<R, +1>(d, row, tw, t);
             barrier_a();
-            if (failed) return tma_state(parity, failed, timed_out);
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
             if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, u * N + kTmaBatch * (b + 2), p.pol_stream);
             if constexpr (kFull) {                               // 1/N already applied in phase C
 #pragma unroll
@@ -283,13 +420,14 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
     }
     if (tid == 0) T::wait_all<0>();                              // psi[u] complete; buffers free for u + 1
     __syncthreads();
-    return tma_state(parity, failed, timed_out);
+    return tma_state(parity, failed, timed_out, mphase);
 }
 
 __device__ __forceinline__ void tma_apply(TmaPipe &p, uint32_t st) {
     p.parity = st & 3u;
     p.failed = (st & 4u) != 0;
     p.timed_out = (st & 8u) != 0;
+    p.mphase = (st >> 4) & 1u;
 }
 
 // Sets up the pipeline state (mbarriers, twiddles, policies); ends with a block barrier.
@@ -306,6 +444,10 @@ __device__ __forceinline__ void tma_pipe_init(TmaPipe &p, unsigned char *base, f
     p.failed = false;
     p.timed_out = false;
     p.slot_col = slot_col;
+    p.gs = nullptr;
+    p.op = nullptr;
+    p.tmem = 0;
+    p.mphase = 0;
     p.pol_keep = T::policy_keep();
     p.pol_stream = T::policy_stream();
     for (int i = tid; i < 256; i += blockDim.x) {
@@ -347,22 +489,65 @@ __device__ __forceinline__ void tma_pipe_finish(TmaPipe &p, int *status) {
     }
 }
 
-template <int B, int XM>
-__global__ void __launch_bounds__(B * 16, 32 / B)
+// Dynamic shared memory of the kernel: stages, staging, twiddles, barriers; the tensor-core
+// form adds the split DFT matrix (64 KB) and one pass's operand (32 KB).
+template <int B, bool TC>
+__host__ __device__ constexpr size_t tma_kernel_smem() {
+    return tma_smem_bytes<B>() + (TC ? (size_t)1024 + 65536 + 32768 : 0);
+}
+
+template <int B, int XM, bool TC = false>
+__global__ void __launch_bounds__(B * 16, TC ? 1 : 32 / B)
 k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     constexpr size_t kTmaBuf = tma_buf_bytes<B>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ double s_red[B * 16 / 32];
     __shared__ uint32_t s_pending;
+    __shared__ uint32_t s_tmem;
     TmaPipe p;
+    if constexpr (TC) {
+        // split DFT matrix into shared memory, TMEM for the accumulators, per-lane radix-4 twiddles
+        unsigned char *gs = base + 3 * kTmaBuf + 256 * sizeof(float2) + 1024;
+        for (int i = threadIdx.x; i < 65536 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(gs)[i] = a.gmat[i];
+        if (threadIdx.x < 32) pm::tc::alloc(&s_tmem, 64);
+    }
     tma_pipe_init(p, base, (float2 *)(base + 3 * kTmaBuf), (uint64_t *)(base + 3 * kTmaBuf + 256 * sizeof(float2)),
                   &s_pending, s_red, blockIdx.x * 256);
+    if constexpr (TC) {
+        p.gs = base + 3 * kTmaBuf + 256 * sizeof(float2) + 1024;
+        p.op = p.gs + 65536;
+        if (threadIdx.x == 0) {
+            pm::tma::mbar_init(&p.bar[3], 1);
+            pm::tma::fence_barrier_init();
+        }
+        pm::tc::fence_before();
+        __syncthreads();
+        pm::tc::fence_after();
+        p.tmem = s_tmem;
+        const int u = 16 * ((threadIdx.x >> 5) & 3) + ((threadIdx.x & 31) >> 1);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            double sn, cs;
+            sincospi(-2.0 * (double)(q * u) / 256.0, &sn, &cs);
+            p.twq[q - 1] = make_float2((float)cs, (float)sn);
+        }
+    }
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
     if (a.inject_wait) tma_pipe_inject_wait(p);
     for (int iu = blockIdx.x; iu < units && !p.failed; iu += gridDim.x)
-        tma_apply(p, tma_unit<B, XM>(p, a, tm, (XM == XM_LIST) ? a.list[iu] : iu));
+        tma_apply(p, tma_unit<B, XM, TC>(p, a, tm, (XM == XM_LIST) ? a.list[iu] : iu));
     tma_pipe_finish(p, a.status);
+    if constexpr (TC) {
+        // an MMA whose completion wait gave up may still be running: wait once more (bounded),
+        // then release the TMEM columns
+        if (p.failed && threadIdx.x == 0) pm::tma::mbar_wait(&p.bar[3], p.mphase);
+        pm::tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            pm::tc::fence_after();
+            pm::tc::dealloc(p.tmem, 64);
+        }
+    }
 }
-

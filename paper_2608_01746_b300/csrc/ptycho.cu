@@ -35,6 +35,7 @@
 #include "dftgemm.h"
 #include "fft.cuh"
 #include "tma.cuh"
+#include "tcgen05.cuh"
 
 
 namespace {
@@ -830,7 +831,8 @@ struct ptycho_ctx {
     int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout
     TmaMaps tm;
     bool exit_tma = false;
-    bool fft_gemm = false;                                // split-BF16 tensor-core DFTs (N = 64)
+    bool fft_gemm = false;                                // split-BF16 tensor-core DFTs (N = 64, 128, 256)
+    const uint4 *gmat = nullptr;                          // N = 256 tensor-core form: the split DFT matrix
     int gemm_sms = 0;
     int tma_batch = 32;
     int grid_exit = 0, nchunk = 0, per_chunk = 0, nqt = 0, nred = 0;
@@ -900,11 +902,11 @@ int encode_2d(CUtensorMap *m, void *addr, CUtensorMapDataType dt, size_t esize, 
     return PTYCHO_OK;
 }
 
-template <int B, int XM>
+template <int B, int XM, bool TC = false>
 int setup_tma_kernel(ptycho_ctx *h, int *per_sm) {
-    const size_t smem = tma_smem_bytes<B>();
-    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_exit_wave_tma<B, XM>, B * 16, smem));
+    const size_t smem = tma_kernel_smem<B, TC>();
+    PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B, XM, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_exit_wave_tma<B, XM, TC>, B * 16, smem));
     if (*per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
     h->exit_smem = smem;
     return PTYCHO_OK;
@@ -933,6 +935,13 @@ int setup_exit_tma(ptycho_ctx *h) {
     } else if (h->algorithm == PTYCHO_ALG_EPIE_COLOUR) {
         h->tma_batch = 32;
         if ((rc = setup_tma_kernel<32, XM_LIST>(h, &per_sm))) return rc;
+    } else if (h->fft_gemm) {
+        // tensor-core form: 16-row stages, one CTA per SM (the DFT matrix and operand need room)
+        h->tma_batch = 16;
+        const void *gm = nullptr;
+        if ((rc = pm::dft64_matrix(&gm))) return rc;
+        h->gmat = static_cast<const uint4 *>(gm);
+        if ((rc = setup_tma_kernel<16, XM_FULL, true>(h, &per_sm))) return rc;
     } else if (h->tma_batch == 32) {
         if ((rc = setup_tma_kernel<32, XM_FULL>(h, &per_sm))) return rc;
     } else {
@@ -977,6 +986,7 @@ TmaArgs tma_args(ptycho_ctx *h) {
     a.J = h->J;
     a.Q = h->Q;
     a.inject_wait = h->inject_wait;
+    a.gmat = h->gmat;
     return a;
 }
 
@@ -985,6 +995,7 @@ int launch_exit_tma(ptycho_ctx *h, int xm) {
     if (xm == XM_FWD) k_exit_wave_tma<16, XM_FWD><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (xm == XM_INV) k_exit_wave_tma<16, XM_INV><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (xm == XM_LIST) k_exit_wave_tma<32, XM_LIST><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else if (h->fft_gemm) k_exit_wave_tma<16, XM_FULL, true><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (h->tma_batch == 32) k_exit_wave_tma<32, XM_FULL><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else k_exit_wave_tma<16, XM_FULL><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     PM_LAUNCHED("k_exit_wave_tma");
@@ -1090,7 +1101,7 @@ int setup_exit(ptycho_ctx *h) {
 }
 
 int launch_exit_pass(ptycho_ctx *h, int xm) {
-    if (h->fft_gemm) {
+    if (h->fft_gemm && h->N != 256) {
         pm::Dft64Exit e{h->d_obj, h->d_probe, h->d_amp, h->d_pos, h->d_psi, h->d_err_pos, h->d_status, h->M, h->J};
         if (h->N == 128) return pm::dft128_exit_launch(e, h->gemm_sms, h->st);
         return pm::dft64_exit_launch(e, h->gemm_sms, h->st);
@@ -1273,8 +1284,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (d->fft_path != PTYCHO_FFT_RADIX_FP32 && d->fft_path != PTYCHO_FFT_DFTGEMM_BF16X3)
         return pm::fail(PTYCHO_EINVAL, "ptycho_init: unknown fft_path %d", d->fft_path);
     if (d->fft_path == PTYCHO_FFT_DFTGEMM_BF16X3 &&
-        ((d->N != 64 && d->N != 128) || d->modes != 1 || d->algorithm != PTYCHO_ALG_AP))
-        return pm::fail(PTYCHO_EINVAL, "ptycho_init: the DFT-GEMM path needs N = 64 or 128, one mode and algorithm AP");
+        ((d->N != 64 && d->N != 128 && d->N != 256) || d->modes != 1 || d->algorithm != PTYCHO_ALG_AP))
+        return pm::fail(PTYCHO_EINVAL,
+                        "ptycho_init: the DFT-GEMM path needs N = 64, 128 or 256, one mode and algorithm AP");
     const int M = d->M, N = d->N, J = d->J, Q = d->modes;
     for (int j = 0; j < J; ++j) {
         const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
@@ -1498,7 +1510,7 @@ extern "C" int ptycho_stage_times(ptycho_handle h, double *ms, long long *launch
 
 extern "C" int ptycho_debug_wait_timeout(ptycho_handle h, int enable) {
     if (!h) return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: NULL handle");
-    if (!h->exit_tma || h->fft_gemm)
+    if (!h->exit_tma)
         return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: the handle's exit-wave kernel (N = %d) has no "
                                        "bounded waits to exercise; the hook needs N = 256", h->N);
     h->inject_wait = enable != 0;
@@ -1740,7 +1752,7 @@ int autotune(ptycho_batch_ctx *b) {
         std::string bkey = "tma:";
         bool any = false;
         for (ptycho_ctx *h : b->hs)
-            if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch) {
+            if (h->exit_tma && !h->fft_gemm && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch) {
                 bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
                 any = true;
             }
@@ -1806,7 +1818,8 @@ int autotune(ptycho_batch_ctx *b) {
     // rows per TMA stage of the N = 256 datasets (all together)
     std::vector<ptycho_ctx *> big;
     for (ptycho_ctx *h : b->hs)
-        if (h->exit_tma && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch) big.push_back(h);
+        if (h->exit_tma && !h->fft_gemm && h->Q == 1 && h->algorithm == PTYCHO_ALG_AP && !b->one_launch)
+            big.push_back(h);
     std::string bkey = "tma:";
     for (ptycho_ctx *h : big) bkey += std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
     int bcached = 0;

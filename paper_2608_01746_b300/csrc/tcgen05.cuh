@@ -7,10 +7,21 @@
 // contiguous along K (128 bytes apart) and 8-row groups are (K / 8) * 128 bytes apart.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace pm {
 namespace tc {
+
+// (re, im) -> packed BF16 hi word and lo word (re in the low half: the lower K index), with
+// hi = bf16(z) and lo = bf16(z - hi): the split of the 3-term split-BF16 products.
+__device__ __forceinline__ void split2(float2 z, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(z.x, z.y);
+    const float2 r = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(z.x - r.x, z.y - r.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);

@@ -87,7 +87,7 @@ def _desc(**kw):
                                 {"modes": 0}, {"modes": 9}, {"algorithm": 2},
                                 {"algorithm": 1, "modes": 2}, {"algorithm": 1, "epie_alpha": 0.0},
                                 {"probe_update_start": -1}, {"d_fused": None}, {"obj0": None},
-                                {"fft_path": 2}, {"fft_path": 1, "N": 16, "M": 64}, {"fft_path": 1, "N": 256, "M": 256},
+                                {"fft_path": 2}, {"fft_path": 1, "N": 16, "M": 64}, {"fft_path": 1, "N": 256, "M": 256, "modes": 2},
                                 {"fft_path": 1, "modes": 2}, {"fft_path": 1, "algorithm": 1}])
 def test_ptycho_init_rejects_bad_arguments(L, kw):
     d, _pos = _desc(**kw)

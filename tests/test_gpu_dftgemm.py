@@ -170,3 +170,37 @@ def test_n128_iteration_matches_oracle(api, subset):
     assert rel_l2(o, ro) <= EXIT_BOUND
     assert rel_l2(p, rp) <= EXIT_BOUND
     assert abs(e[0] - re[0]) <= EXIT_BOUND * re[0]
+
+
+@pytest.fixture(scope="module")
+def lab24():
+    """24 positions of the lab scan (N = 256), fused by the oracle."""
+    import dataclasses
+    cfg = dataclasses.replace(synth.CONFIGS["lab"], J=24)
+    sc = synth.make_scan_torch(cfg, seed=2024, device="cpu")
+    raw = sc["raw"].numpy()
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    sc["cfg"] = cfg
+    return sc, oracle.mnf_stack(raw, cfg.times, p).astype(np.float32)
+
+
+@pytest.mark.parametrize("n_iter,subset", [(1, None), (1, [0, 7, 23]), (3, None)])
+def test_n256_iterations_match_oracle(api, lab24, n_iter, subset):
+    """N = 256 on the tensor cores (each 256-point transform = four 64-point split-BF16 GEMMs
+    and a radix-4 epilogue, inside the TMA slot pipeline of the radix kernel): 1 and 3
+    iterations against the oracle, within the exit-wave bound per iteration."""
+    sc, fused = lab24
+    pos = sc["pos"] if subset is None else sc["pos"][subset]
+    fused = fused if subset is None else fused[subset]
+    M = sc["cfg"].M
+    rng = np.random.default_rng(3)
+    obj0 = (1.0 + 0.1 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))).astype(np.complex64)
+    probe0 = sc["probe"].astype(np.complex64)
+    o, p, e = _run(api, sc, fused, pos, obj0, probe0, n_iter, "dftgemm_bf16x3")
+    ro, rp, re = oracle.reconstruct(fused.astype(np.float64), pos, obj0.astype(np.complex128),
+                                    probe0.astype(np.complex128), n_iter, 1e-3, 1e-3, 0)
+    print(f"N=256 J={len(pos)} {n_iter} it: object {rel_l2(o, ro):.3e} probe {rel_l2(p, rp):.3e} "
+          f"error {abs(e[-1] - re[-1]) / re[-1]:.3e}")
+    assert rel_l2(o, ro) <= n_iter * EXIT_BOUND
+    assert rel_l2(p, rp) <= n_iter * EXIT_BOUND
+    np.testing.assert_allclose(e, re, rtol=n_iter * EXIT_BOUND)
