@@ -42,6 +42,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kTW = 32;          // tile width (columns) of the object gather and probe sums
+constexpr int kListChunk = 512;  // tile-list entries staged per chunk in the object gather
 constexpr int kTR = 8;           // tile height (rows): one register per row and lane
 
 enum { ST_EXIT = 0, ST_OBJECT = 1, ST_PROBE = 2, ST_ERROR = 3, ST_COUNT = 4 };
@@ -508,6 +509,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx, int Q) {
     __shared__ WarpTiles wt;
     __shared__ float s_max[kThreads / 32];
+    __shared__ int3 s_list[kListChunk];
     const int tile = torder[blockIdx.x];              // longest position lists first
     const int ty0 = (tile / ntx) * kTR, tx0 = (tile % ntx) * kTW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -517,35 +519,45 @@ __global__ void __launch_bounds__(kThreads, 3) k_object_gather(
     for (int r = 0; r < kTR; ++r) { acc[r] = make_float2(0.f, 0.f); dn[r] = 0.f; }
     unsigned hit = 0u;
     const size_t NN = (size_t)N * N;
-    const int e0 = tstart[tile] + warp, e1 = tstart[tile + 1];
-    int4 en = e0 < e1 ? tlist[e0] : make_int4(0, 0, 0, 0);    // (j, y, x, -)
-    for (int e = e0; e < e1; e += kThreads / 32) {
-        const int2 pj = make_int2(en.y, en.z);
-        const int j = en.x;
-        if (e + kThreads / 32 < e1) en = tlist[e + kThreads / 32];   // prefetch the next entry
-        const int lx = tx0 + lane - pj.y;
-        const bool okx = lx >= 0 && lx < N;
-        const int lxc = min(max(lx, 0), N - 1);
-        const int nq = QC ? QC : Q;
-        for (int m = 0; m < nq; ++m) {                   // probe modes (one for coherent data)
-            const float2 *psi_j = psi + ((size_t)j * nq + m) * NN;
-            const float2 *probe_m = probe + (size_t)m * NN;
-            // All loads first, from clamped (always valid) addresses, so they are in flight
-            // together; pixels outside the patch are masked out afterwards.
-            float2 pv[kTR], vv[kTR];
+    const int nq = QC ? QC : Q;                       // probe modes (one for coherent data)
+    // The tile's list is staged in shared memory in chunks (no entry prefetch in registers),
+    // and both operands share the in-plane offsets, so one 32-bit offset per row is live while
+    // the 16 loads are in flight: no spills at three blocks per SM.
+    const int l0 = tstart[tile], l1 = tstart[tile + 1];
+    for (int c0 = l0; c0 < l1; c0 += kListChunk) {
+        const int cn = min(kListChunk, l1 - c0);
+        __syncthreads();                              // the previous chunk is consumed
+        for (int i = threadIdx.x; i < cn; i += kThreads) {
+            const int4 v = tlist[c0 + i];
+            s_list[i] = make_int3(v.x, v.y, v.z);     // (j, y, x)
+        }
+        __syncthreads();
+        for (int i = warp; i < cn; i += kThreads / 32) {  // warp w: every 8th entry, ascending
+            const int j = s_list[i].x, py = s_list[i].y, px = s_list[i].z;
+            const int lx = tx0 + lane - px;
+            const int lxc = min(max(lx, 0), N - 1);
+            const int ly0 = ty0 - py;
+            for (int m = 0; m < nq; ++m) {
+                const float2 *psi_j = psi + ((size_t)j * nq + m) * NN;
+                const float2 *probe_m = probe + (size_t)m * NN;
+                // all loads first, from clamped (always valid) offsets, so they are in flight
+                // together; pixels outside the patch are masked out afterwards
+                float2 pv[kTR], vv[kTR];
 #pragma unroll
-            for (int r = 0; r < kTR; ++r) {
-                const int lyc = min(max(ty0 + r - pj.x, 0), N - 1);
-                pv[r] = __ldg(probe_m + lyc * N + lxc);
-                vv[r] = __ldg(psi_j + (size_t)lyc * N + lxc);
-            }
+                for (int r = 0; r < kTR; ++r) {
+                    const int off = min(max(ly0 + r, 0), N - 1) * N + lxc;
+                    pv[r] = __ldg(probe_m + off);
+                    vv[r] = __ldg(psi_j + off);
+                }
+                if (lx >= 0 && lx < N) {
 #pragma unroll
-            for (int r = 0; r < kTR; ++r) {
-                const int ly = ty0 + r - pj.x;
-                if (okx && ly >= 0 && ly < N) {
-                    acc[r] = cadd(acc[r], cmulc(pv[r], vv[r]));
-                    dn[r] += cabs2(pv[r]);
-                    hit |= 1u << r;
+                    for (int r = 0; r < kTR; ++r) {
+                        if ((unsigned)(ly0 + r) < (unsigned)N) {
+                            acc[r] = cadd(acc[r], cmulc(pv[r], vv[r]));
+                            dn[r] += cabs2(pv[r]);
+                            hit |= 1u << r;
+                        }
+                    }
                 }
             }
         }
