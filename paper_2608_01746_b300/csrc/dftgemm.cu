@@ -154,18 +154,18 @@ __device__ __forceinline__ void put_pair(uint8_t *bh, uint8_t *bl, int n, int c,
 // complex entries c, c + 1 (c = 4 i + 2 part) of its lane pair's vector: lanes 2h and 2h + 1
 // hold the real and imaginary rows of the same index h, and swap halves with one shuffle per
 // two entries.
+// The two 32-column halves are read one after the other (32 live registers, not 64).
 template <typename F>
 __device__ __forceinline__ void for_pairs(uint32_t lane_addr, int p, int part, F &&f) {
-    uint32_t v[2][32];
-    tc::ld_32cols(lane_addr + (uint32_t)(p * kN), v[0]);
-    tc::ld_32cols(lane_addr + (uint32_t)(p * kN + 32), v[1]);
-    tc::wait_ld();
 #pragma unroll
     for (int ch = 0; ch < 2; ++ch) {
+        uint32_t v[32];
+        tc::ld_32cols(lane_addr + (uint32_t)(p * kN + 32 * ch), v);
+        tc::wait_ld();
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
-            const float a0 = __uint_as_float(v[ch][i]), a1 = __uint_as_float(v[ch][i + 1]);
-            const float a2 = __uint_as_float(v[ch][i + 2]), a3 = __uint_as_float(v[ch][i + 3]);
+            const float a0 = __uint_as_float(v[i]), a1 = __uint_as_float(v[i + 1]);
+            const float a2 = __uint_as_float(v[i + 2]), a3 = __uint_as_float(v[i + 3]);
             const float y0 = __shfl_xor_sync(0xffffffffu, part ? a0 : a2, 1);
             const float y1 = __shfl_xor_sync(0xffffffffu, part ? a1 : a3, 1);
             const float2 z0 = part ? make_float2(y0, a2) : make_float2(a0, y0);
