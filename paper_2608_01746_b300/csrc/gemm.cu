@@ -3,10 +3,18 @@
 // warm-start network (forward, data gradient, weight gradient) are all of this form after
 // im2col.  M % 128 == 0, N % 64 == 0, K % 64 == 0 (callers pad with zeros).
 //
-// One CTA per 128 x 64 tile of C, 128 threads (thread r owns row r of the tile = TMEM lane r).
-// K is consumed in chunks of 64 through four shared-memory stages in the no-swizzle core-matrix
-// layout, filled with cp.async three chunks ahead of the tensor core.  Every wait is bounded; a
-// timeout sets *status.
+// One CTA per 128 x BN tile of C (BN = 256, 128 or 64, chosen from N), 192 threads in three
+// roles:
+//   warp 0   one lane issues the TMA loads of the 128 x 64 A chunk and the BN x 64 B chunk of
+//            every K step into a ring of shared-memory stages (128-byte swizzle, the layout the
+//            MMA descriptors read directly); a stage is refilled once the MMAs that read it
+//            have completed (its "empty" mbarrier, signalled by tcgen05.commit);
+//   warp 1   allocates the BN TMEM accumulator columns; one lane waits for each stage's
+//            "full" mbarrier (TMA transaction bytes) and issues the four 128 x BN x 16 MMAs;
+//   warps 2-5  (one per 32-lane TMEM quarter) wait for the last commit and store C.
+// Every wait is bounded; a timeout sets *status, and the CTA drains the loads and MMAs it
+// still has in flight (bounded) before it releases TMEM and exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -16,148 +24,136 @@
 #include "gemm.h"
 #include "tcgen05.cuh"
 #include "tma.cuh"
+#include "tmap.h"
 
 namespace {
 
 using namespace pm;
 
-constexpr int kBM = 128, kBN = 64, kBK = 64;
-constexpr int kThreads = 128;
-constexpr int kStages = 4;                      // chunks in flight
+constexpr int kBM = 128, kBK = 64;
+constexpr int kThreads = 192;
 constexpr uint32_t kABytes = kBM * kBK * 2;     // 16 KB
-constexpr uint32_t kBBytes = kBN * kBK * 2;     // 8 KB
-constexpr uint32_t kStage = kABytes + kBBytes;
-constexpr uint32_t kSmem = kStages * kStage + 1024;
-constexpr uint32_t kLBO = 128, kSBO = (kBK / 8) * 128;
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// This thread's share of chunk kc (A: row m0 + tid, 8 x 16 bytes; B: 4 x 16 bytes) into a stage,
-// in the core-matrix layout.
-__device__ __forceinline__ void load_chunk(const uint4 *__restrict__ A, const uint4 *__restrict__ B, int m0, int n0,
-                                           int k16, int kc, uint8_t *sa, uint8_t *sb) {
-    const int tid = threadIdx.x;
-    const uint4 *arow = A + (size_t)(m0 + tid) * k16 + kc * 8;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cp_async16(sa + ((tid >> 3) * 8 + q) * 128 + (tid & 7) * 16, arow + q);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int idx = tid + q * kThreads;     // 0 .. 511: 64 rows x 8 pieces
-        const int r = idx >> 3, c = idx & 7;
-        cp_async16(sb + ((r >> 3) * 8 + c) * 128 + (r & 7) * 16, B + (size_t)(n0 + r) * k16 + kc * 8 + c);
-    }
-}
+template <int BN>
+struct Cfg {
+    static constexpr int kStages = BN == 256 ? 4 : (BN == 128 ? 6 : 8);
+    static constexpr uint32_t kBBytes = BN * kBK * 2;
+    static constexpr uint32_t kStage = kABytes + kBBytes;
+    static constexpr uint32_t kSmem = kStages * kStage + 1024;   // + alignment slack
+    static constexpr uint32_t kTmemCols = BN;
+};
 
 // blockIdx.z selects a slice of K (split-K): chunks [z cps, min((z + 1) cps, K / 64)), written to
-// C + z M N (a partial product; the caller sums the slices).  Chunks stream through kStages
-// shared-memory stages with cp.async; a stage is refilled once the MMAs that read it have
-// committed (their mbarrier), so loads run kStages - 1 chunks ahead of the tensor core.
-__global__ void __launch_bounds__(kThreads)
-    k_gemm_bf16(const uint4 *__restrict__ A, const uint4 *__restrict__ B, float *__restrict__ C, int M, int N, int K,
-                int cps, int *status) {
+// C + z M N (a partial product; the caller sums the slices).
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, float *__restrict__ C,
+                int M, int N, int K, int cps, int *status) {
+    using G = Cfg<BN>;
+    constexpr int S = G::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar[kStages];
+    __shared__ uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-    if (warp == 0) tc::alloc(&tmem_slot, 64);
+    __shared__ int s_fail, s_issued, s_consumed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kc0 = blockIdx.z * cps;
+    const int kchunks = min(K / kBK, kc0 + cps) - kc0;
+    C += (size_t)blockIdx.z * M * N;
+    if (warp == 1) tc::alloc(&tmem_slot, G::kTmemCols);
     if (tid == 0) {
-        for (int q = 0; q < kStages; ++q) tma::mbar_init(&bar[q], 1);
+        for (int q = 0; q < S; ++q) {
+            tma::mbar_init(&full[q], 1);
+            tma::mbar_init(&empty[q], 1);
+        }
+        tma::mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
         tma::fence_barrier_init();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_slot;
-    const int kc0 = blockIdx.z * cps;
-    const int kchunks = min(K / kBK, kc0 + cps) - kc0;
-    const int k16 = K / 8;                       // uint4 per row
-    C += (size_t)blockIdx.z * M * N;
-    uint32_t phase[kStages] = {};
-    bool ok = true;
-    // prologue: chunks 0 .. kStages - 2 in flight (one commit group each, possibly empty)
-#pragma unroll
-    for (int q = 0; q < kStages - 1; ++q) {
-        if (q < kchunks) load_chunk(A, B, m0, n0, k16, kc0 + q, sm + q * kStage, sm + q * kStage + kABytes);
-        cp_async_commit();
-    }
-    for (int kc = 0; kc < kchunks; ++kc) {
-        const int s = kc % kStages;
-        uint8_t *sa = sm + s * kStage, *sb = sa + kABytes;
-        cp_async_wait<kStages - 2>();            // this thread's copies of chunk kc have landed
-        tma::fence_async_smem();
-        tc::fence_before();
-        __syncthreads();                         // ... and every thread's
-        if (tid == 0) {
-            tc::fence_after();
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kBN);
-            const uint32_t a0 = tc::smem_addr(sa), b0 = tc::smem_addr(sb);
-#pragma unroll
-            for (int ks = 0; ks < kBK / 16; ++ks)
-                tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 256, kLBO, kSBO), tc::smem_desc(b0 + ks * 256, kLBO, kSBO),
-                             idesc, (uint32_t)((kc | ks) != 0));
-            tc::commit(&bar[s]);
-        }
-        // refill the stage of chunk kc - 1 with chunk kc + kStages - 1 once its MMAs are done
-        const int nxt = kc + kStages - 1;
-        if (nxt < kchunks) {
-            const int sp = nxt % kStages;
-            if (kc >= 1) {
-                bool w = true;
-                if (warp == 0) w = tma::mbar_wait(&bar[sp], phase[sp]);
-                ok = __syncthreads_and(w) != 0;
-                if (!ok) break;
-                phase[sp] ^= 1;
+    auto stage_a = [&](int s) { return sm + s * G::kStage; };
+    if (warp == 0) {
+        if (lane == 0) {                                   // TMA producer
+            int kc = 0;
+            for (; kc < kchunks; ++kc) {
+                const int s = kc % S;
+                if (kc >= S && !tma::mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                tma::mbar_expect_tx(&full[s], G::kStage);
+                tma::load_2d(stage_a(s), &ta, (kc0 + kc) * kBK, m0, &full[s]);
+                tma::load_2d(stage_a(s) + kABytes, &tb, (kc0 + kc) * kBK, n0, &full[s]);
             }
-            load_chunk(A, B, m0, n0, k16, kc0 + nxt, sm + sp * kStage, sm + sp * kStage + kABytes);
+            s_issued = kc;
         }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    if (kchunks <= 0) {                          // empty slice: a zero partial
-        float *crow = C + (size_t)(m0 + tid) * N + n0;
-        for (int q = 0; q < kBN; ++q) crow[q] = 0.f;
-    } else if (ok) {
-        // the last commit covers every MMA issued before it
-        const int s = (kchunks - 1) % kStages;
-        bool w = true;
-        if (warp == 0) w = tma::mbar_wait(&bar[s], phase[s]);
-        ok = __syncthreads_and(w) != 0;
-        tc::fence_after();
-    }
-    if (ok && kchunks > 0) {
-        float *crow = C + (size_t)(m0 + tid) * N + n0;
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    } else if (warp == 1) {
+        if (lane == 0 && kchunks > 0) {                    // MMA issuer
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+            int kc = 0;
+            for (; kc < kchunks; ++kc) {
+                const int s = kc % S;
+                if (!tma::mbar_wait(&full[s], (kc / S) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t a0 = tc::smem_addr(stage_a(s)), b0 = a0 + kABytes;
 #pragma unroll
-        for (int ch = 0; ch < kBN / 32; ++ch) {
-            uint32_t v[32];
-            tc::ld_32cols(lane_addr + ch * 32, v);
-            tc::wait_ld();
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                reinterpret_cast<float4 *>(crow + ch * 32)[q] =
-                    make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
-                                __uint_as_float(v[4 * q + 3]));
+                for (int ks = 0; ks < kBK / 16; ++ks)
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(a0 + ks * 32), tc::smem_desc_sw128(b0 + ks * 32), idesc,
+                                 (uint32_t)((kc | ks) != 0));
+                tc::commit(&empty[s]);                     // stage s free once these MMAs are done
+            }
+            s_consumed = kc;
+            tc::commit(&done);                             // every MMA issued above
         }
-    } else if (!ok) {
-        if (tid == 0) atomicExch(status, 1);
-        // let MMAs still in flight finish before the columns are released (bounded)
-        if (warp == 0)
-            for (int q = 0; q < kStages; ++q) tma::mbar_wait(&bar[q], phase[q]);
+    } else {                                               // epilogue: warps 2..5
+        const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
+        float *crow = C + (size_t)(m0 + 32 * q + lane) * N + n0;
+        if (kchunks <= 0) {                                // empty slice: a zero partial
+            for (int c = 0; c < BN; c += 4) *reinterpret_cast<float4 *>(crow + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            bool w = true;
+            if (lane == 0) w = tma::mbar_wait(&done, 0);
+            w = __shfl_sync(0xffffffffu, (int)w, 0) != 0;
+            __syncwarp();
+            tc::fence_after();
+            if (!w) s_fail = 1;
+            else {
+                const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t v[32];
+                    tc::ld_32cols(lane_addr + ch * 32, v);
+                    tc::wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        reinterpret_cast<float4 *>(crow + ch * 32)[e] =
+                            make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                        __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                }
+            }
+        }
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (s_fail && tid == 0) {
+        atomicExch(status, 1);
+        // loads issued but never consumed, then the MMAs (bounded waits)
+        for (int kc = s_consumed; kc < s_issued; ++kc) tma::mbar_wait(&full[kc % S], (kc / S) & 1);
+        if (kchunks > 0) tma::mbar_wait(&done, 0);
+    }
+    __syncthreads();
+    if (warp == 1) {
         tc::fence_after();
-        tc::dealloc(tmem, 64);
+        tc::dealloc(tmem, G::kTmemCols);
     }
 }
 
@@ -179,17 +175,38 @@ bool g_attr_set[64] = {};
 
 namespace pm {
 
+template <int BN>
+int launch_bn(const CUtensorMap &ta, const void *B, float *C, int M, int N, int K, int cps, int slices,
+              int *d_status, cudaStream_t st) {
+    using G = Cfg<BN>;
+    CUtensorMap tb;
+    int rc = encode_2d(&tb, const_cast<void *>(B), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)K, (uint64_t)N,
+                       kBK, BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    dim3 grid(M / kBM, N / BN, slices);
+    k_gemm_bf16<BN><<<grid, kThreads, G::kSmem, st>>>(ta, tb, C, M, N, K, cps, d_status);
+    PM_LAUNCHED("k_gemm_bf16");
+    return PTYCHO_OK;
+}
+
 int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K, int *d_status, cudaStream_t st,
                      float *work, size_t work_floats) {
-    if (M % kBM || N % kBN || K % kBK || M < 0 || N < 0 || K < 0)
+    if (M % kBM || N % 64 || K % kBK || M < 0 || N < 0 || K < 0)
         return fail(PTYCHO_EINVAL, "gemm_bf16: M %% 128, N %% 64, K %% 64 must be 0 (M=%d N=%d K=%d)", M, N, K);
     if (M == 0 || N == 0) return PTYCHO_OK;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+        return fail(PTYCHO_EINVAL, "gemm_bf16: A and B must be 16-byte aligned");
     int dev = 0;
     PM_CUDA(cudaGetDevice(&dev));
     {
         std::lock_guard<std::mutex> lk(g_attr_mu);
         if (dev >= 64 || !g_attr_set[dev]) {
-            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<256>::kSmem));
+            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<128>::kSmem));
+            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<64>::kSmem));
             if (dev < 64) g_attr_set[dev] = true;
         }
     }
@@ -197,19 +214,28 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
         PM_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
         return PTYCHO_OK;
     }
+    // The widest tile that divides N and still gives two waves of CTAs; else 64 columns.
+    int BN = 64;
+    for (int cand : {256, 128})
+        if (N % cand == 0 && (M / kBM) * (N / cand) >= 2 * 148) { BN = cand; break; }
     // split K when the output tiles alone cannot fill the GPU (weight gradients: small M x N,
     // K = every pixel of the batch)
-    const int tiles = (M / kBM) * (N / kBN), kch = K / kBK;
+    const int tiles = (M / kBM) * (N / BN), kch = K / kBK;
     int slices = 1;
     if (work && tiles < 296 && kch >= 8) {
         slices = std::min(std::min((296 + tiles - 1) / tiles, kch / 4), 64);
         while (slices > 1 && (size_t)slices * M * N > work_floats) --slices;
     }
     const int cps = (kch + slices - 1) / slices;
-    dim3 grid(M / kBM, N / kBN, slices);
-    k_gemm_bf16<<<grid, kThreads, kSmem, st>>>(static_cast<const uint4 *>(A), static_cast<const uint4 *>(B),
-                                                slices > 1 ? work : C, M, N, K, cps, d_status);
-    PM_LAUNCHED("k_gemm_bf16");
+    CUtensorMap ta;
+    int rc = encode_2d(&ta, const_cast<void *>(A), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (uint64_t)K, (uint64_t)M, kBK,
+                       kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    float *dst = slices > 1 ? work : C;
+    if (BN == 256) rc = launch_bn<256>(ta, B, dst, M, N, K, cps, slices, d_status, st);
+    else if (BN == 128) rc = launch_bn<128>(ta, B, dst, M, N, K, cps, slices, d_status, st);
+    else rc = launch_bn<64>(ta, B, dst, M, N, K, cps, slices, d_status, st);
+    if (rc) return rc;
     if (slices > 1) {
         const size_t n = (size_t)M * N;
         k_sum_slices<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(work, slices, n, C);

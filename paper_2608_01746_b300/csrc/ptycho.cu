@@ -36,6 +36,7 @@
 #include "fft.cuh"
 #include "tma.cuh"
 #include "tcgen05.cuh"
+#include "tmap.h"
 
 
 namespace {
@@ -880,39 +881,7 @@ void free_ctx(ptycho_ctx *h) {
     delete h;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-int tensor_map_encoder(EncodeTiledFn *fn) {
-    static EncodeTiledFn cached = nullptr;
-    if (!cached) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        PM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !p)
-            return pm::fail(PTYCHO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-        cached = (EncodeTiledFn)p;
-    }
-    *fn = cached;
-    return PTYCHO_OK;
-}
-
-// Row-major 2-D tensor [outer][inner] of `esize`-byte elements, box {box_in, box_out}.
-int encode_2d(CUtensorMap *m, void *addr, CUtensorMapDataType dt, size_t esize, uint64_t inner, uint64_t outer,
-              uint32_t box_in, uint32_t box_out, CUtensorMapSwizzle sw) {
-    EncodeTiledFn enc;
-    int rc = tensor_map_encoder(&enc);
-    if (rc) return rc;
-    const cuuint64_t dims[2] = {inner, outer};
-    const cuuint64_t strides[1] = {inner * esize};
-    const cuuint32_t box[2] = {box_in, box_out};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(m, dt, 2, addr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return pm::fail(PTYCHO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return PTYCHO_OK;
-}
+using pm::encode_2d;
 
 template <int B, int XM, bool TC = false>
 int setup_tma_kernel(ptycho_ctx *h, int *per_sm) {

@@ -43,6 +43,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Descriptor of a K-major BF16 operand tile with the 128-byte swizzle, as a TMA load with
+// CU_TENSOR_MAP_SWIZZLE_128B and a 64-element inner box writes it: one 128-byte row per M (or N)
+// index, 8-row groups 1024 bytes apart, the tile on a 1024-byte boundary.  The swizzle is a
+// function of the address bits, so the k-th 16-element slice of the 64-element rows starts
+// 32 k bytes after the tile.  Leading byte offset unused (16); version 1; swizzle mode 2.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an FP32 accumulator
 // of M x N (M = 64 or 128; N a multiple of 16 up to 256).
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
