@@ -59,16 +59,30 @@ __device__ __forceinline__ float im2col_value(const bf16 *__restrict__ x, int ci
     return __bfloat162float(x[(((unsigned)b * cin + c) * hin + yi) * hin + xi]);
 }
 
-// Row layout out[p][k] (Pp x Kp): blockIdx.x = p, threads along k (64 per block, Kp % 64 == 0).
-// Transposed out[k][p] (Kp x Pp): blockIdx.x = k, threads along p.  The long dimension is on x
-// (grid y is limited to 65535).
+// Each thread writes 8 consecutive elements of one output row (one 16-byte store), and the
+// lanes of a warp take consecutive groups of the same row, so a warp writes 512 contiguous
+// bytes.  Row layout out[p][k] (Pp x Kp): groups along k; transposed out[k][p] (Kp x Pp): groups
+// along p (8 consecutive output pixels of one image row, read from one input row).  Pp % 128 == 0
+// and Kp % 64 == 0, so no group straddles a row.
 __global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int mode, int hout, int P, int K, int Pp,
                          int Kp, int transposed, bf16 *__restrict__ out) {
-    const int outer = blockIdx.x, inner = blockIdx.y * blockDim.x + threadIdx.x;
-    const int ninner = transposed ? Pp : Kp;
-    if (inner >= ninner) return;
-    const int p = transposed ? inner : outer, k = transposed ? outer : inner;
-    out[(size_t)outer * ninner + inner] = __float2bfloat16_rn(im2col_value(x, cin, hin, mode, hout, P, K, p, k));
+    const unsigned ninner = transposed ? (unsigned)Pp : (unsigned)Kp, groups = ninner / 8u;
+    const unsigned n = (transposed ? (unsigned)Kp : (unsigned)Pp) * groups;
+    for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const unsigned outer = g / groups, i0 = (g - outer * groups) * 8u;
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int p = transposed ? (int)(i0 + e) : (int)outer, k = transposed ? (int)outer : (int)(i0 + e);
+            v[e] = __float2bfloat16_rn(im2col_value(x, cin, hin, mode, hout, P, K, p, k));
+        }
+        *reinterpret_cast<uint4 *>(out + (size_t)outer * ninner + i0) = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+unsigned im2col_grid(int Pp, int Kp) {
+    const size_t groups = (size_t)Pp * Kp / 8;
+    return (unsigned)std::min<size_t>((groups + kT - 1) / kT, (size_t)148 * 16);
 }
 
 // col2im (adjoint of im2col) as a gather: dx[b][c][y][x] = sum of dcol[p][k] over the (p, k)
@@ -405,8 +419,8 @@ int forward(wsnet_ctx *n, const bf16 *x, int B, float *out) {
     for (size_t li = 0; li < n->L.size(); ++li) {
         auto &l = n->L[li];
         const int P = B * l.hout * l.hout, Pp = rup(P, 128);
-        k_im2col<<<dim3(Pp, l.Kp / 64), 64, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 0,
-                                                        n->col);
+        k_im2col<<<im2col_grid(Pp, l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 0,
+                                                          n->col);
         PM_LAUNCHED("k_im2col");
         if ((rc = pm::gemm_bf16_launch(n->col, l.wb, n->cbuf, Pp, l.Coutp, l.Kp, n->status, n->st))) return rc;
         const bool last = li + 1 == n->L.size();
@@ -442,8 +456,8 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
             PM_LAUNCHED("k_bias_sum");
         }
         // weight gradient: dW[Coutp128][Kp] = dzt[Coutp128][Pp] . colT[Kp][Pp]^T
-        k_im2col<<<dim3(l.Kp, (Pp + kT - 1) / kT), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp,
-                                                                   l.Kp, 1, n->col);
+        k_im2col<<<im2col_grid(Pp, l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 1,
+                                                          n->col);
         PM_LAUNCHED("k_im2col");
         if ((rc = pm::gemm_bf16_launch(n->dzt, n->col, n->cbuf, l.Coutp128, l.Kp, Pp, n->status, n->st, n->work,
                                        n->work_floats)))
@@ -571,6 +585,9 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
     n->out_channels = cout[nlayers - 1];
     n->out_side = side;
     const size_t nout = (size_t)max_batch * n->out_channels * side * side;
+    // the layout kernels index with 32-bit arithmetic
+    if (std::max(std::max(max_col, max_c), std::max(max_dz, std::max(max_act, nout))) >= ((size_t)1 << 31))
+        return bail(pm::fail(PTYCHO_EINVAL, "wsnet_create: a layer buffer would hold 2^31 or more elements"));
     if ((rc = nalloc(n, &n->col, max_col)) || (rc = nalloc(n, &n->cbuf, max_c)) || (rc = nalloc(n, &n->dz, max_dz)) ||
         (rc = nalloc(n, &n->dzt, max_dz)) || (rc = nalloc(n, &n->g0, max_act)) || (rc = nalloc(n, &n->g1, max_act)) ||
         (rc = nalloc(n, &n->pred, nout)) || (rc = nalloc(n, &n->dpred, nout)) || (rc = nalloc(n, &n->part, 1024)) ||
