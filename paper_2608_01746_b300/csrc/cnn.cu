@@ -5,7 +5,9 @@
 //
 // A 3 x 3 convolution layer is three GEMMs after im2col (P = batch x output pixels, K = 9 Cin):
 //   forward       Z[P][Cout]  = col[P][K] . W[Cout][K]^T           (+ bias, ReLU -> BF16)
-//   data grad     dcol[P][K]  = dZ[P][Cout] . W^T[K][Cout]^T        (then col2im, a gather)
+//   data grad     s1 / up: dX[P][Cin] = col(dZ)[P][9 Cout] . Wflip[Cin][9 Cout]^T, the
+//                 stride-1 convolution of dZ with the flipped kernel (then the 2 x 2 sum for up);
+//                 s2: dcol[P][K] = dZ[P][Cout] . W^T[K][Cout]^T, then col2im (a gather)
 //   weight grad   dW[Cout][K] = dZ^T[Cout][P] . col^T[K][P]^T
 // with every dimension zero-padded to the GEMM tile multiples.  Modes: s1 (stride 1), s2
 // (stride 2), up (nearest 2x up-sampling, then stride 1); zero padding of one pixel.
@@ -123,6 +125,59 @@ __global__ void k_col2im(const float *__restrict__ dcol, int Kp, int B, int cin,
     }
 }
 
+// Data gradient of a stride-1 or up-sampling layer as a stride-1 convolution of dZ with the
+// flipped, channel-transposed kernel, at the layer's output resolution:
+//   dx_c[b][c][y][x] = sum_{o, u', v'} dZ[b][o][y + u' - 1][x + v' - 1] W[o][c][2 - u'][2 - v']
+// (dx_c = dx for s1; for "up" it is the gradient of the up-sampled input, and dx is its 2 x 2
+// sum).  Operand col[p][k'] (Pp x K2p), p = (b, y, x) at hout, k' = o * 9 + u' * 3 + v', read
+// from dz[p][o] (Pp x Coutp, BF16): exact copies, zero outside the image and in the padding.
+__global__ void k_im2col_dz(const bf16 *__restrict__ dz, int Coutp, int cout, int hout, int P, int Pp, int K2p,
+                            bf16 *__restrict__ out) {
+    const unsigned groups = (unsigned)K2p / 8u, n = (unsigned)Pp * groups, hw = (unsigned)(hout * hout);
+    const int K2 = 9 * cout;
+    for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const unsigned p = g / groups, k0 = (g - p * groups) * 8u;
+        const unsigned b = p / hw, q = p - b * hw, i = q / (unsigned)hout, j = q - i * (unsigned)hout;
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = (int)k0 + e;
+            bf16 val = __float2bfloat16_rn(0.f);
+            if ((int)p < P && k < K2) {
+                const int o = k / 9, r = k - 9 * o, u = r / 3, w = r - 3 * u;
+                const int y = (int)i + u - 1, x = (int)j + w - 1;
+                if (y >= 0 && x >= 0 && y < hout && x < hout)
+                    val = dz[((size_t)b * hw + (unsigned)y * hout + (unsigned)x) * Coutp + o];
+            }
+            v[e] = val;
+        }
+        *reinterpret_cast<uint4 *>(out + (size_t)p * K2p + k0) = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+// dx[b][c][y][x] (FP32, NCHW, at hin) from the rows C[p][c] (Cinp columns) of the convolution
+// above: s1 copies; up sums the 2 x 2 block (2y + sy, 2x + sx) in the order (0,0) (0,1) (1,0) (1,1).
+__global__ void k_dx_from_rows(const float *__restrict__ C, int Cinp, int B, int cin, int hin, int mode, int hout,
+                               float *__restrict__ dx) {
+    const unsigned n = (unsigned)B * cin * hin * hin, hh = (unsigned)(hin * hin), ho = (unsigned)(hout * hout);
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const unsigned bc = e / hh, yx = e - bc * hh;
+        const unsigned y = yx / (unsigned)hin, x = yx - y * hin;
+        const unsigned b = bc / (unsigned)cin, c = bc - b * cin;
+        const float *row = C + (size_t)b * ho * Cinp + c;
+        float acc;
+        if (mode == WS_MODE_UP) {
+            acc = row[((2 * y) * hout + 2 * x) * (size_t)Cinp];
+            acc += row[((2 * y) * hout + 2 * x + 1) * (size_t)Cinp];
+            acc += row[((2 * y + 1) * hout + 2 * x) * (size_t)Cinp];
+            acc += row[((2 * y + 1) * hout + 2 * x + 1) * (size_t)Cinp];
+        } else {
+            acc = row[(y * hout + x) * (size_t)Cinp];
+        }
+        dx[e] = acc;
+    }
+}
+
 // Z[p][o] + bias -> ReLU -> BF16 activation y[b][o][i][j]; the last layer stores FP32.
 __global__ void k_fwd_epilogue(const float *__restrict__ C, int Coutp, const float *__restrict__ bias, int B, int cout,
                                int hout, int relu, bf16 *__restrict__ y, float *__restrict__ yf) {
@@ -193,6 +248,22 @@ __global__ void k_bias_sum(const float *__restrict__ part, int cout, int slices,
     float a = 0.f;
     for (int sl = 0; sl < slices; ++sl) a += part[o * slices + sl];
     db[o] = a;
+}
+
+// The flipped, channel-transposed BF16 kernel of the data-gradient convolution:
+// wf[c][o * 9 + u' * 3 + v'] = w[o][c * 9 + (2 - u') * 3 + (2 - v')]  (Cinp x K2p, zero padded).
+__global__ void k_weights_flip(const float *__restrict__ w, int cout, int cin, int Cinp, int K2p,
+                               bf16 *__restrict__ wf) {
+    const size_t n = (size_t)Cinp * K2p;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / K2p), k = (int)(e % K2p);
+        float val = 0.f;
+        if (c < cin && k < 9 * cout) {
+            const int o = k / 9, r = k - 9 * o, u = r / 3, v = r - 3 * u;
+            val = w[(size_t)o * (9 * cin) + c * 9 + (2 - u) * 3 + (2 - v)];
+        }
+        wf[e] = __float2bfloat16_rn(val);
+    }
 }
 
 // BF16 copies of the FP32 master weights w[o][k]: wb[o][k] (Coutp x Kp) and wt[k][o] (Kp x Coutp).
@@ -367,6 +438,8 @@ struct wsnet_ctx {
         float *w = nullptr, *b = nullptr, *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
         float *gw = nullptr, *gb = nullptr;
         bf16 *wb = nullptr, *wt = nullptr, *y = nullptr;
+        int Cinp = 0, K2p = 0;                 // data-gradient convolution (s1, up): Cinp x K2p kernel
+        bf16 *wf = nullptr;
     };
     std::vector<Layer> L;
     int in_side = 0, max_batch = 0, out_channels = 0, out_side = 0;
@@ -407,6 +480,10 @@ int refresh_weights(wsnet_ctx *n) {
     for (auto &l : n->L) {
         k_weights_bf16<<<nblk((size_t)l.Coutp * l.Kp), kT, 0, n->st>>>(l.w, l.cout, l.K, l.Coutp, l.Kp, l.wb, l.wt);
         PM_LAUNCHED("k_weights_bf16");
+        if (l.wf) {
+            k_weights_flip<<<nblk((size_t)l.Cinp * l.K2p), kT, 0, n->st>>>(l.w, l.cout, l.cin, l.Cinp, l.K2p, l.wf);
+            PM_LAUNCHED("k_weights_flip");
+        }
     }
     n->wdirty = false;
     return PTYCHO_OK;
@@ -465,12 +542,24 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
         k_copy_wgrad<<<nblk((size_t)l.cout * l.K), kT, 0, n->st>>>(n->cbuf, l.Kp, l.cout, l.K, l.gw);
         PM_LAUNCHED("k_copy_wgrad");
         if (li == 0) break;                      // no gradient for the network input
-        // data gradient: dcol[Pp][Kp] = dz[Pp][Coutp] . wt[Kp][Coutp]^T, then col2im
-        if ((rc = pm::gemm_bf16_launch(n->dz, l.wt, n->cbuf, Pp, l.Kp, l.Coutp, n->status, n->st))) return rc;
         float *gx = (g == n->g0) ? n->g1 : n->g0;
-        k_col2im<<<nblk((size_t)B * l.cin * l.hin * l.hin), kT, 0, n->st>>>(n->cbuf, l.Kp, B, l.cin, l.hin, l.mode,
-                                                                            l.hout, gx);
-        PM_LAUNCHED("k_col2im");
+        if (l.wf) {
+            // s1 / up: dx by the flipped-kernel convolution of dZ (rows C[Pp][Cinp]), then the
+            // 2 x 2 sum for up
+            k_im2col_dz<<<im2col_grid(Pp, l.K2p), kT, 0, n->st>>>(n->dz, l.Coutp, l.cout, l.hout, P, Pp, l.K2p,
+                                                                  n->col);
+            PM_LAUNCHED("k_im2col_dz");
+            if ((rc = pm::gemm_bf16_launch(n->col, l.wf, n->cbuf, Pp, l.Cinp, l.K2p, n->status, n->st))) return rc;
+            k_dx_from_rows<<<nblk((size_t)B * l.cin * l.hin * l.hin), kT, 0, n->st>>>(n->cbuf, l.Cinp, B, l.cin, l.hin,
+                                                                                     l.mode, l.hout, gx);
+            PM_LAUNCHED("k_dx_from_rows");
+        } else {
+            // s2: dcol[Pp][Kp] = dz[Pp][Coutp] . wt[Kp][Coutp]^T, then col2im
+            if ((rc = pm::gemm_bf16_launch(n->dz, l.wt, n->cbuf, Pp, l.Kp, l.Coutp, n->status, n->st))) return rc;
+            k_col2im<<<nblk((size_t)B * l.cin * l.hin * l.hin), kT, 0, n->st>>>(n->cbuf, l.Kp, B, l.cin, l.hin,
+                                                                                l.mode, l.hout, gx);
+            PM_LAUNCHED("k_col2im");
+        }
         g = gx;
     }
     if (h_loss) {
@@ -558,6 +647,12 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
         l.Coutp = rup(l.cout, 64);
         l.Coutp128 = rup(l.cout, 128);
         const size_t Pp = (size_t)rup(max_batch * l.hout * l.hout, 128);
+        const bool flipped = i > 0 && l.mode != WS_MODE_S2;      // data gradient by convolution of dZ
+        if (flipped) {
+            l.Cinp = rup(l.cin, 64);
+            l.K2p = rup(9 * l.cout, 64);
+            max_col = std::max(max_col, Pp * l.K2p);
+        }
         max_col = std::max(max_col, Pp * l.Kp);
         max_c = std::max(std::max(max_c, Pp * (size_t)l.Coutp), std::max(Pp * (size_t)l.Kp, (size_t)l.Coutp128 * l.Kp));
         max_dz = std::max(max_dz, Pp * l.Coutp128);
@@ -568,7 +663,8 @@ extern "C" int wsnet_create(wsnet *out, const int *cin, const int *cout, const i
             (rc = nalloc(n, &l.vw, nw)) || (rc = nalloc(n, &l.mb, l.cout)) || (rc = nalloc(n, &l.vb, l.cout)) ||
             (rc = nalloc(n, &l.gw, nw)) || (rc = nalloc(n, &l.gb, l.cout)) ||
             (rc = nalloc(n, &l.wb, (size_t)l.Coutp * l.Kp)) || (rc = nalloc(n, &l.wt, (size_t)l.Kp * l.Coutp)) ||
-            (rc = nalloc(n, &l.y, (size_t)max_batch * l.cout * l.hout * l.hout)))
+            (rc = nalloc(n, &l.y, (size_t)max_batch * l.cout * l.hout * l.hout)) ||
+            (flipped && (rc = nalloc(n, &l.wf, (size_t)l.Cinp * l.K2p))))
             return bail(rc);
         // He-normal initial weights (std sqrt(2 / fan_in)), zero biases and moments
         std::normal_distribution<float> nd(0.f, std::sqrt(2.f / (float)l.K));

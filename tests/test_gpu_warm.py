@@ -85,7 +85,8 @@ def test_one_layer_forward_and_gradients(api, mode):
 
 @pytest.mark.parametrize("mode,second", [(m, s) for m in ("s1", "s2", "up") for s in ("s1", "s2", "up")])
 def test_two_layers_input_gradient_path(api, mode, second):
-    """The data gradient (GEMM + col2im) of layer 1 reaches layer 0's weight gradient."""
+    """The data gradient of layer 1 (the flipped-kernel convolution of dZ for s1 / up, GEMM +
+    col2im for s2) reaches layer 0's weight gradient."""
     net, layers, params, x = _one_layer(api, mode, relu_follow=True, second=second)
     ry, acts, pre = cnn.network_forward(layers, params, x)
     y = api.wsnet_forward(net, to_dev_bf16(x)).cpu().numpy()
