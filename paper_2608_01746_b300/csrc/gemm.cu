@@ -3,7 +3,7 @@
 // warm-start network (forward, data gradient, weight gradient) are all of this form after
 // im2col.  M % 128 == 0, N % 64 == 0, K % 64 == 0 (callers pad with zeros).
 //
-// One CTA per 128 x BN tile of C (BN = 256, 128 or 64, chosen from N), 192 threads in three
+// One CTA per 128 x BN tile of C (BN = 256, 192, 128 or 64, chosen from N), 192 threads in three
 // roles:
 //   warp 0   one lane issues the TMA loads of the 128 x 64 A chunk and the BN x 64 B chunk of
 //            every K step into a ring of shared-memory stages (128-byte swizzle, the layout the
@@ -36,11 +36,12 @@ constexpr uint32_t kABytes = kBM * kBK * 2;     // 16 KB
 
 template <int BN>
 struct Cfg {
-    static constexpr int kStages = BN == 256 ? 4 : (BN == 128 ? 6 : 8);
+    static constexpr int kStages = BN == 256 ? 4 : (BN == 192 ? 5 : (BN == 128 ? 6 : 8));
     static constexpr uint32_t kBBytes = BN * kBK * 2;
     static constexpr uint32_t kStage = kABytes + kBBytes;
     static constexpr uint32_t kSmem = kStages * kStage + 1024;   // + alignment slack
-    static constexpr uint32_t kTmemCols = BN;
+    static constexpr uint32_t kTmemCols = BN == 192 ? 256 : BN;  // a power of two
+    static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
 // blockIdx.z selects a slice of K (split-K): chunks [z cps, min((z + 1) cps, K / 64)), written to
@@ -203,6 +204,8 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
         if (dev >= 64 || !g_attr_set[dev]) {
             PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<256>::kSmem));
+            PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg<192>::kSmem));
             PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg<128>::kSmem));
             PM_CUDA(cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -214,15 +217,24 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
         PM_CUDA(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
         return PTYCHO_OK;
     }
-    // The widest tile that divides N and still gives two waves of CTAs; else 64 columns.
+    // Tile width: the kernels are bound by operand traffic, which per K step is (128 + BN) rows
+    // for 128 BN outputs.  With a split-K workspace every width can fill the GPU, so the widest
+    // that divides N; otherwise the width with the least (waves of CTAs) x (128 + BN).
+    const int kch = K / kBK;
+    const bool can_split = work && kch >= 8;
     int BN = 64;
-    for (int cand : {256, 128})
-        if (N % cand == 0 && (M / kBM) * (N / cand) >= 2 * 148) { BN = cand; break; }
+    long best = -1;
+    for (int cand : {256, 192, 128, 64}) {
+        if (N % cand) continue;
+        const long t = (long)(M / kBM) * (N / cand);
+        const long cost = can_split ? 0 : ((t + 147) / 148) * (128 + cand);
+        if (best < 0 || cost < best) { best = cost; BN = cand; }
+    }
     // split K when the output tiles alone cannot fill the GPU (weight gradients: small M x N,
     // K = every pixel of the batch)
-    const int tiles = (M / kBM) * (N / BN), kch = K / kBK;
+    const int tiles = (M / kBM) * (N / BN);
     int slices = 1;
-    if (work && tiles < 296 && kch >= 8) {
+    if (can_split && tiles < 296) {
         slices = std::min(std::min((296 + tiles - 1) / tiles, kch / 4), 64);
         while (slices > 1 && (size_t)slices * M * N > work_floats) --slices;
     }
@@ -233,6 +245,7 @@ int gemm_bf16_launch(const void *A, const void *B, float *C, int M, int N, int K
     if (rc) return rc;
     float *dst = slices > 1 ? work : C;
     if (BN == 256) rc = launch_bn<256>(ta, B, dst, M, N, K, cps, slices, d_status, st);
+    else if (BN == 192) rc = launch_bn<192>(ta, B, dst, M, N, K, cps, slices, d_status, st);
     else if (BN == 128) rc = launch_bn<128>(ta, B, dst, M, N, K, cps, slices, d_status, st);
     else rc = launch_bn<64>(ta, B, dst, M, N, K, cps, slices, d_status, st);
     if (rc) return rc;

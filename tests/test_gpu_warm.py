@@ -42,9 +42,9 @@ def to_dev_bf16(a):
     return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
 
 
-# The last two shapes have enough output tiles for the 128- and 256-column tile kernels.
+# The last three shapes have enough output tiles for the 128-, 256- and 192-column tile kernels.
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 128, 192), (384, 192, 1152), (38016, 128, 320),
-                                   (19072, 512, 192)])
+                                   (19072, 512, 192), (18944, 192, 256)])
 def test_gemm_matches_fp64(api, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = bf16(rng.standard_normal((M, K)))
