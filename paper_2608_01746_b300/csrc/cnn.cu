@@ -37,46 +37,60 @@ unsigned nblk(size_t n) { return (unsigned)std::min<size_t>((n + kT - 1) / kT, (
 // im2col: element (p, k), p = (b, i, j) output pixel, k = c * 9 + u * 3 + v, of the conv input
 // x_in[b][c][s i + u - 1][s j + v - 1] (zero outside; for "up", x_in = nearest up-sampling).
 // Index arithmetic is 32-bit (every buffer holds fewer than 2^31 elements).
-__device__ __forceinline__ float im2col_value(const bf16 *__restrict__ x, int cin, int hin, int mode, int hout,
-                                              int P, int K, int p, int k) {
-    if (p >= P || k >= K) return 0.f;
-    const unsigned c = (unsigned)k / 9u, r = (unsigned)k - 9u * c, u = r / 3u, v = r - 3u * u;
-    const unsigned hw = (unsigned)(hout * hout);
-    const unsigned b = (unsigned)p / hw, q = (unsigned)p - b * hw, i = q / (unsigned)hout, j = q - i * (unsigned)hout;
+// Input element read by im2col entry (b, c, i, j, u, v) for layer mode MODE (zero outside).
+template <int MODE>
+__device__ __forceinline__ bf16 conv_tap(const bf16 *__restrict__ x, int cin, int hin, int b, int c, int i, int j,
+                                         int u, int v) {
     int yi, xi;
-    if (mode == WS_MODE_S2) {
-        yi = 2 * (int)i + (int)u - 1;
-        xi = 2 * (int)j + (int)v - 1;
-        if (yi < 0 || xi < 0 || yi >= hin || xi >= hin) return 0.f;
-    } else if (mode == WS_MODE_UP) {
-        const int yu = (int)i + (int)u - 1, xu = (int)j + (int)v - 1;
-        if (yu < 0 || xu < 0 || yu >= 2 * hin || xu >= 2 * hin) return 0.f;
+    if (MODE == WS_MODE_S2) {
+        yi = 2 * i + u - 1;
+        xi = 2 * j + v - 1;
+    } else if (MODE == WS_MODE_UP) {
+        const int yu = i + u - 1, xu = j + v - 1;
+        if (yu < 0 || xu < 0 || yu >= 2 * hin || xu >= 2 * hin) return __float2bfloat16_rn(0.f);
         yi = yu >> 1;
         xi = xu >> 1;
     } else {
-        yi = (int)i + (int)u - 1;
-        xi = (int)j + (int)v - 1;
-        if (yi < 0 || xi < 0 || yi >= hin || xi >= hin) return 0.f;
+        yi = i + u - 1;
+        xi = j + v - 1;
     }
-    return __bfloat162float(x[(((unsigned)b * cin + c) * hin + yi) * hin + xi]);
+    if (yi < 0 || xi < 0 || yi >= hin || xi >= hin) return __float2bfloat16_rn(0.f);
+    return x[(((unsigned)b * cin + c) * hin + yi) * hin + xi];
 }
 
 // Each thread writes 8 consecutive elements of one output row (one 16-byte store), and the
 // lanes of a warp take consecutive groups of the same row, so a warp writes 512 contiguous
-// bytes.  Row layout out[p][k] (Pp x Kp): groups along k; transposed out[k][p] (Kp x Pp): groups
-// along p (8 consecutive output pixels of one image row, read from one input row).  Pp % 128 == 0
-// and Kp % 64 == 0, so no group straddles a row.
-__global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int mode, int hout, int P, int K, int Pp,
-                         int Kp, int transposed, bf16 *__restrict__ out) {
-    const unsigned ninner = transposed ? (unsigned)Pp : (unsigned)Kp, groups = ninner / 8u;
-    const unsigned n = (transposed ? (unsigned)Kp : (unsigned)Pp) * groups;
+// bytes.  Row layout out[p][k] (Pp x Kp): groups along k = c * 9 + u * 3 + v; transposed
+// out[k][p] (Kp x Pp): groups along p = (b, i, j).  Pp % 128 == 0 and Kp % 64 == 0, so no group
+// straddles a row; the indices of a group's first element are decomposed once and then stepped.
+// The values are exact copies of the (BF16) input, zero outside the image and in the padding.
+template <int MODE, bool TRANSPOSED>
+__global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int hout, int P, int K, int Pp, int Kp,
+                         bf16 *__restrict__ out) {
+    const unsigned ninner = TRANSPOSED ? (unsigned)Pp : (unsigned)Kp, groups = ninner / 8u;
+    const unsigned n = (TRANSPOSED ? (unsigned)Kp : (unsigned)Pp) * groups, hw = (unsigned)(hout * hout);
     for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
         const unsigned outer = g / groups, i0 = (g - outer * groups) * 8u;
+        const unsigned p0 = TRANSPOSED ? i0 : outer, k0 = TRANSPOSED ? outer : i0;
+        int b = (int)(p0 / hw);
+        const unsigned q = p0 - (unsigned)b * hw;
+        int i = (int)(q / (unsigned)hout), j = (int)(q - (unsigned)i * hout);
+        int c = (int)(k0 / 9u), r = (int)(k0 - 9u * c);
         __align__(16) bf16 v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int p = transposed ? (int)(i0 + e) : (int)outer, k = transposed ? (int)outer : (int)(i0 + e);
-            v[e] = __float2bfloat16_rn(im2col_value(x, cin, hin, mode, hout, P, K, p, k));
+            const int p = (int)p0 + (TRANSPOSED ? e : 0), k = (int)k0 + (TRANSPOSED ? 0 : e);
+            const int u = (r >= 3) + (r >= 6), w = r - 3 * u;
+            v[e] = (p < P && k < K) ? conv_tap<MODE>(x, cin, hin, b, c, i, j, u, w) : __float2bfloat16_rn(0.f);
+            if (TRANSPOSED) {                                  // next pixel
+                if (++j == hout) {
+                    j = 0;
+                    if (++i == hout) { i = 0; ++b; }
+                }
+            } else if (++r == 9) {                             // next tap
+                r = 0;
+                ++c;
+            }
         }
         *reinterpret_cast<uint4 *>(out + (size_t)outer * ninner + i0) = *reinterpret_cast<const uint4 *>(v);
     }
@@ -85,6 +99,18 @@ __global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int mode,
 unsigned im2col_grid(int Pp, int Kp) {
     const size_t groups = (size_t)Pp * Kp / 8;
     return (unsigned)std::min<size_t>((groups + kT - 1) / kT, (size_t)148 * 16);
+}
+
+template <bool TRANSPOSED>
+int launch_im2col(const bf16 *x, int cin, int hin, int mode, int hout, int P, int K, int Pp, int Kp, bf16 *out,
+                  cudaStream_t st) {
+    const unsigned grid = im2col_grid(Pp, Kp);
+    if (mode == WS_MODE_S2) k_im2col<WS_MODE_S2, TRANSPOSED><<<grid, kT, 0, st>>>(x, cin, hin, hout, P, K, Pp, Kp, out);
+    else if (mode == WS_MODE_UP)
+        k_im2col<WS_MODE_UP, TRANSPOSED><<<grid, kT, 0, st>>>(x, cin, hin, hout, P, K, Pp, Kp, out);
+    else k_im2col<WS_MODE_S1, TRANSPOSED><<<grid, kT, 0, st>>>(x, cin, hin, hout, P, K, Pp, Kp, out);
+    PM_LAUNCHED("k_im2col");
+    return PTYCHO_OK;
 }
 
 // col2im (adjoint of im2col) as a gather: dx[b][c][y][x] = sum of dcol[p][k] over the (p, k)
@@ -157,59 +183,95 @@ __global__ void k_im2col_dz(const bf16 *__restrict__ dz, int Coutp, int cout, in
 
 // dx[b][c][y][x] (FP32, NCHW, at hin) from the rows C[p][c] (Cinp columns) of the convolution
 // above: s1 copies; up sums the 2 x 2 block (2y + sy, 2x + sx) in the order (0,0) (0,1) (1,0) (1,1).
+// Block = 32 output pixels x 32 channels through a shared-memory tile: C is read along c and dx
+// written along the pixels (both coalesced).  Grid (ceil(B hin^2 / 32), Cinp / 32).
 __global__ void k_dx_from_rows(const float *__restrict__ C, int Cinp, int B, int cin, int hin, int mode, int hout,
                                float *__restrict__ dx) {
-    const unsigned n = (unsigned)B * cin * hin * hin, hh = (unsigned)(hin * hin), ho = (unsigned)(hout * hout);
-    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const unsigned bc = e / hh, yx = e - bc * hh;
-        const unsigned y = yx / (unsigned)hin, x = yx - y * hin;
-        const unsigned b = bc / (unsigned)cin, c = bc - b * cin;
-        const float *row = C + (size_t)b * ho * Cinp + c;
-        float acc;
-        if (mode == WS_MODE_UP) {
-            acc = row[((2 * y) * hout + 2 * x) * (size_t)Cinp];
-            acc += row[((2 * y) * hout + 2 * x + 1) * (size_t)Cinp];
-            acc += row[((2 * y + 1) * hout + 2 * x) * (size_t)Cinp];
-            acc += row[((2 * y + 1) * hout + 2 * x + 1) * (size_t)Cinp];
-        } else {
-            acc = row[(y * hout + x) * (size_t)Cinp];
+    __shared__ float t[32][33];                            // [pixel][channel]
+    const unsigned hh = (unsigned)(hin * hin), npix = (unsigned)B * hh;
+    const unsigned q0 = blockIdx.x * 32u, c0 = blockIdx.y * 32u;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned e = q0 + r;
+        float acc = 0.f;
+        if (e < npix) {
+            const unsigned b = e / hh, yx = e - b * hh, y = yx / (unsigned)hin, x = yx - y * hin;
+            const float *row = C + ((size_t)b * hout * hout) * Cinp + c0 + tx;
+            if (mode == WS_MODE_UP) {
+                acc = row[((2 * y) * hout + 2 * x) * (size_t)Cinp];
+                acc += row[((2 * y) * hout + 2 * x + 1) * (size_t)Cinp];
+                acc += row[((2 * y + 1) * hout + 2 * x) * (size_t)Cinp];
+                acc += row[((2 * y + 1) * hout + 2 * x + 1) * (size_t)Cinp];
+            } else {
+                acc = row[(y * hout + x) * (size_t)Cinp];
+            }
         }
-        dx[e] = acc;
+        t[r][tx] = acc;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned c = c0 + r, e = q0 + tx;
+        if (c < (unsigned)cin && e < npix) {
+            const unsigned b = e / hh, yx = e - b * hh;
+            dx[((size_t)b * cin + c) * hh + yx] = t[tx][r];
+        }
     }
 }
 
-// Z[p][o] + bias -> ReLU -> BF16 activation y[b][o][i][j]; the last layer stores FP32.
+// Z[p][o] + bias -> ReLU -> BF16 activation y[b][o][i][j]; the last layer stores FP32.  Block =
+// 32 pixels x 32 channels through a shared-memory tile (C read along o, y written along the
+// pixels).  Grid (ceil(B hout^2 / 32), Coutp / 32).
 __global__ void k_fwd_epilogue(const float *__restrict__ C, int Coutp, const float *__restrict__ bias, int B, int cout,
                                int hout, int relu, bf16 *__restrict__ y, float *__restrict__ yf) {
-    const size_t hw = (size_t)hout * hout, n = (size_t)B * cout * hw;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t q = e % hw;
-        const int o = (int)((e / hw) % cout), b = (int)(e / (hw * cout));
-        float z = C[((size_t)b * hw + q) * Coutp + o] + bias[o];
-        if (relu) z = fmaxf(z, 0.f);
-        if (yf) yf[e] = z;
-        else y[e] = __float2bfloat16_rn(z);
+    __shared__ float t[32][33];                            // [pixel][channel]
+    const unsigned hw = (unsigned)(hout * hout), P = (unsigned)B * hw;
+    const unsigned p0 = blockIdx.x * 32u, o0 = blockIdx.y * 32u;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned p = p0 + r;
+        t[r][tx] = p < P ? C[(size_t)p * Coutp + o0 + tx] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned o = o0 + r, p = p0 + tx;
+        if (o < (unsigned)cout && p < P) {
+            float z = t[tx][r] + bias[o];
+            if (relu) z = fmaxf(z, 0.f);
+            const unsigned b = p / hw, q = p - b * hw;
+            const size_t e = ((size_t)b * cout + o) * hw + q;
+            if (yf) yf[e] = z;
+            else y[e] = __float2bfloat16_rn(z);
+        }
     }
 }
 
 // dZ = dL/dy * relu'(y) in the two GEMM layouts, zero-padded: dz[p][o] (Pp x Coutp) and
-// dzt[o][p] (Coutp128 x Pp).
+// dzt[o][p] (Coutp128 x Pp).  Block = 32 channels x 32 pixels: g and y are read along the
+// pixels and dzt written along them; dz is written along the channels from a shared-memory
+// tile.  Grid (Pp / 32, Coutp128 / 32).
 __global__ void k_bwd_dz(const float *__restrict__ g, const bf16 *__restrict__ y, int relu, int B, int cout, int hout,
                          int Pp, int Coutp, int Coutp128, bf16 *__restrict__ dz, bf16 *__restrict__ dzt) {
-    const size_t hw = (size_t)hout * hout, P = (size_t)B * hw;
-    const size_t n = (size_t)Pp * Coutp128;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const int o = (int)(e / Pp);
-        const size_t p = e % Pp;
+    __shared__ bf16 t[32][34];                             // [channel][pixel]
+    const unsigned hw = (unsigned)(hout * hout), P = (unsigned)B * hw;
+    const unsigned p0 = blockIdx.x * 32u, o0 = blockIdx.y * 32u;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned o = o0 + r, p = p0 + tx;
         float d = 0.f;
-        if (p < P && o < cout) {
-            const size_t idx = ((p / hw) * cout + o) * hw + p % hw;
+        if (p < P && o < (unsigned)cout) {
+            const unsigned b = p / hw, q = p - b * hw;
+            const size_t idx = ((size_t)b * cout + o) * hw + q;
             d = g[idx];
             if (relu && !(__bfloat162float(y[idx]) > 0.f)) d = 0.f;
         }
         const bf16 h = __float2bfloat16_rn(d);
-        dzt[e] = h;
-        if (o < Coutp) dz[p * Coutp + o] = h;
+        dzt[(size_t)o * Pp + p] = h;
+        t[r][tx] = h;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += kT / 32) {
+        const unsigned p = p0 + r, o = o0 + tx;
+        if (o < (unsigned)Coutp) dz[(size_t)p * Coutp + o] = t[tx][r];
     }
 }
 
@@ -496,12 +558,10 @@ int forward(wsnet_ctx *n, const bf16 *x, int B, float *out) {
     for (size_t li = 0; li < n->L.size(); ++li) {
         auto &l = n->L[li];
         const int P = B * l.hout * l.hout, Pp = rup(P, 128);
-        k_im2col<<<im2col_grid(Pp, l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 0,
-                                                          n->col);
-        PM_LAUNCHED("k_im2col");
+        if ((rc = launch_im2col<false>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, n->col, n->st))) return rc;
         if ((rc = pm::gemm_bf16_launch(n->col, l.wb, n->cbuf, Pp, l.Coutp, l.Kp, n->status, n->st))) return rc;
         const bool last = li + 1 == n->L.size();
-        k_fwd_epilogue<<<nblk((size_t)B * l.cout * l.hout * l.hout), kT, 0, n->st>>>(
+        k_fwd_epilogue<<<dim3((unsigned)((P + 31) / 32), (unsigned)(l.Coutp / 32)), kT, 0, n->st>>>(
             n->cbuf, l.Coutp, l.b, B, l.cout, l.hout, l.relu, l.y, last ? out : nullptr);
         PM_LAUNCHED("k_fwd_epilogue");
         in = l.y;
@@ -522,8 +582,8 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
         auto &l = n->L[li];
         const int P = B * l.hout * l.hout, Pp = rup(P, 128);
         const bf16 *in = li == 0 ? x : n->L[li - 1].y;
-        k_bwd_dz<<<nblk((size_t)Pp * l.Coutp128), kT, 0, n->st>>>(g, l.y, l.relu, B, l.cout, l.hout, Pp, l.Coutp,
-                                                                  l.Coutp128, n->dz, n->dzt);
+        k_bwd_dz<<<dim3((unsigned)(Pp / 32), (unsigned)(l.Coutp128 / 32)), kT, 0, n->st>>>(
+            g, l.y, l.relu, B, l.cout, l.hout, Pp, l.Coutp, l.Coutp128, n->dz, n->dzt);
         PM_LAUNCHED("k_bwd_dz");
         {
             const int slices = std::max(1, std::min(kBiasSlices, B * l.hout * l.hout / (4 * kT)));
@@ -533,9 +593,7 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
             PM_LAUNCHED("k_bias_sum");
         }
         // weight gradient: dW[Coutp128][Kp] = dzt[Coutp128][Pp] . colT[Kp][Pp]^T
-        k_im2col<<<im2col_grid(Pp, l.Kp), kT, 0, n->st>>>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, 1,
-                                                          n->col);
-        PM_LAUNCHED("k_im2col");
+        if ((rc = launch_im2col<true>(in, l.cin, l.hin, l.mode, l.hout, P, l.K, Pp, l.Kp, n->col, n->st))) return rc;
         if ((rc = pm::gemm_bf16_launch(n->dzt, n->col, n->cbuf, l.Coutp128, l.Kp, Pp, n->status, n->st, n->work,
                                        n->work_floats)))
             return rc;
@@ -550,8 +608,8 @@ int backward(wsnet_ctx *n, const bf16 *x, const float *t, int B, double *h_loss)
                                                                   n->col);
             PM_LAUNCHED("k_im2col_dz");
             if ((rc = pm::gemm_bf16_launch(n->col, l.wf, n->cbuf, Pp, l.Cinp, l.K2p, n->status, n->st))) return rc;
-            k_dx_from_rows<<<nblk((size_t)B * l.cin * l.hin * l.hin), kT, 0, n->st>>>(n->cbuf, l.Cinp, B, l.cin, l.hin,
-                                                                                     l.mode, l.hout, gx);
+            k_dx_from_rows<<<dim3((unsigned)((B * l.hin * l.hin + 31) / 32), (unsigned)(l.Cinp / 32)), kT, 0,
+                             n->st>>>(n->cbuf, l.Cinp, B, l.cin, l.hin, l.mode, l.hout, gx);
             PM_LAUNCHED("k_dx_from_rows");
         } else {
             // s2: dcol[Pp][Kp] = dz[Pp][Coutp] . wt[Kp][Coutp]^T, then col2im
