@@ -58,19 +58,29 @@ __device__ __forceinline__ bf16 conv_tap(const bf16 *__restrict__ x, int cin, in
     return x[(((unsigned)b * cin + c) * hin + yi) * hin + xi];
 }
 
-// Each thread writes 8 consecutive elements of one output row (one 16-byte store), and the
-// lanes of a warp take consecutive groups of the same row, so a warp writes 512 contiguous
-// bytes.  Row layout out[p][k] (Pp x Kp): groups along k = c * 9 + u * 3 + v; transposed
-// out[k][p] (Kp x Pp): groups along p = (b, i, j).  Pp % 128 == 0 and Kp % 64 == 0, so no group
-// straddles a row; the indices of a group's first element are decomposed once and then stepped.
-// The values are exact copies of the (BF16) input, zero outside the image and in the padding.
+// Each thread writes 8 consecutive elements of one output row (one 16-byte store).  Row layout
+// out[p][k] (Pp x Kp), groups along k = c * 9 + u * 3 + v: the lanes of a warp take one k group
+// of 32 consecutive pixels (each load instruction reads consecutive input pixels of one channel
+// tap) and consecutive warps the next k groups of the same pixels.  Transposed out[k][p]
+// (Kp x Pp), groups along p = (b, i, j): the lanes take consecutive pixel groups of one k (a warp
+// writes 512 contiguous bytes).  Pp % 128 == 0 and Kp % 64 == 0, so no group straddles a row;
+// the indices of a group's first element are decomposed once and then stepped.  The values are
+// exact copies of the (BF16) input, zero outside the image and in the padding.
 template <int MODE, bool TRANSPOSED>
 __global__ void k_im2col(const bf16 *__restrict__ x, int cin, int hin, int hout, int P, int K, int Pp, int Kp,
                          bf16 *__restrict__ out) {
     const unsigned ninner = TRANSPOSED ? (unsigned)Pp : (unsigned)Kp, groups = ninner / 8u;
     const unsigned n = (TRANSPOSED ? (unsigned)Kp : (unsigned)Pp) * groups, hw = (unsigned)(hout * hout);
     for (unsigned g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        const unsigned outer = g / groups, i0 = (g - outer * groups) * 8u;
+        unsigned outer, i0;
+        if (TRANSPOSED) {
+            outer = g / groups;
+            i0 = (g - outer * groups) * 8u;
+        } else {                                               // warp = (32-pixel block, k group)
+            const unsigned w = g >> 5, pblk = w / groups;
+            outer = pblk * 32u + (g & 31u);
+            i0 = (w - pblk * groups) * 8u;
+        }
         const unsigned p0 = TRANSPOSED ? i0 : outer, k0 = TRANSPOSED ? outer : i0;
         int b = (int)(p0 / hw);
         const unsigned q = p0 - (unsigned)b * hw;
