@@ -66,8 +66,8 @@ __device__ __forceinline__ void dit_stage(float2 (&y)[R]) {
         for (int k = 0; k < LEN / 2; ++k) {
             const float2 a = y[i + k];
             const float2 b = rot16<SIGN>(y[i + k + LEN / 2], k * (16 / LEN));
-            y[i + k] = cadd(a, b);
-            y[i + k + LEN / 2] = csub(a, b);
+            y[i + k] = cadd_x2(a, b);
+            y[i + k + LEN / 2] = csub_x2(a, b);
         }
     }
     if constexpr (LEN < R) dit_stage<R, SIGN, LEN * 2>(y);
