@@ -71,12 +71,14 @@ constexpr int kInP = kIn + 1;         // padded pitch
 
 // Level 0 -> level 1 for every exposure: blockIdx.z = position, tile of 16 x 16 outputs.
 // Each input pixel's K weights (Eq. 5, normalised) and radiances are computed once into shared
-// memory, then every plane is blurred separably (rows, then columns) and decimated.
-template <int K>
-__global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ raw,
-                                                 float *__restrict__ ge1, float *__restrict__ gw1,
-                                                 FuseDev f) {
-    extern __shared__ float sm[];
+// memory, then every plane is blurred separably (rows, then columns) and decimated.  FULL: a
+// whole 16 x 16 tile, whose loop bounds are compile-time constants (the index divisions become
+// multiply-shifts); the partial tiles at the edge of an N / 2 not divisible by 16 take the
+// general body.  Both compute the same values.
+template <int K, bool FULL>
+__device__ __forceinline__ void reduce0_body(const uint16_t *__restrict__ raw, float *__restrict__ ge1,
+                                             float *__restrict__ gw1, const FuseDev &f, float *sm, int outs_y,
+                                             int outs_x) {
     float *s_e = sm;                              // [K][kIn][kInP]
     float *s_w = s_e + K * kIn * kInP;            // [K][kIn][kInP]
     float *h_e = s_w + K * kIn * kInP;            // [K][kIn][kTile]  row-filtered, decimated
@@ -86,7 +88,10 @@ __global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ ra
     const int j = blockIdx.z;
     const uint16_t *raw_j = raw + (size_t)j * K * NN;
     const int oy0 = blockIdx.y * kTile, ox0 = blockIdx.x * kTile;
-    const int outs_y = min(kTile, n1 - oy0), outs_x = min(kTile, n1 - ox0);
+    if (FULL) {
+        outs_y = kTile;
+        outs_x = kTile;
+    }
     const int rows = 2 * outs_y + 3, cols = 2 * outs_x + 3;
     const int tid = threadIdx.x;
     for (int e = tid; e < rows * cols; e += blockDim.x) {
@@ -130,6 +135,17 @@ __global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ ra
         ge1[o] = ae;
         gw1[o] = aw;
     }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_reduce0(const uint16_t *__restrict__ raw,
+                                                 float *__restrict__ ge1, float *__restrict__ gw1,
+                                                 FuseDev f) {
+    extern __shared__ float sm[];
+    const int n1 = f.N >> 1;
+    const int outs_y = min(kTile, n1 - (int)blockIdx.y * kTile), outs_x = min(kTile, n1 - (int)blockIdx.x * kTile);
+    if (outs_y == kTile && outs_x == kTile) reduce0_body<K, true>(raw, ge1, gw1, f, sm, outs_y, outs_x);
+    else reduce0_body<K, false>(raw, ge1, gw1, f, sm, outs_y, outs_x);
 }
 
 template <int K>
@@ -243,18 +259,19 @@ __global__ void __launch_bounds__(256) k_collapse(const float *__restrict__ ge, 
         const int py = oy0 + e / kCT, px = ox0 + e % kCT;
         if (py >= n || px >= n) continue;
         // U2 taps: even m = 2i -> (1/8, 6/8, 1/8) at i-1, i, i+1; odd m = 2i+1 -> (1/2, 1/2) at i, i+1
-        const int ly = (py >> 1) - cy0, lx = (px >> 1) - cx0;     // local coarse index of i
-        float wy[3], wx[3];
-        int y0, x0, ny, nx;
-        if (py & 1) { y0 = ly; ny = 2; wy[0] = wy[1] = 0.5f; }
-        else { y0 = ly - 1; ny = 3; wy[0] = 0.125f; wy[1] = 0.75f; wy[2] = 0.125f; }
-        if (px & 1) { x0 = lx; nx = 2; wx[0] = wx[1] = 0.5f; }
-        else { x0 = lx - 1; nx = 3; wx[0] = 0.125f; wx[1] = 0.75f; wx[2] = 0.125f; }
+        // Three taps at i - 1, i, i + 1 on both parities: the odd case's leading tap has weight
+        // 0, which leaves every partial sum as the two-tap sum would have it.
+        const int y0 = (py >> 1) - cy0 - 1, x0 = (px >> 1) - cx0 - 1;
+        const float wy0 = (py & 1) ? 0.f : 0.125f, wy1 = (py & 1) ? 0.5f : 0.75f, wy2 = (py & 1) ? 0.5f : 0.125f;
+        const float wx0 = (px & 1) ? 0.f : 0.125f, wx1 = (px & 1) ? 0.5f : 0.75f, wx2 = (px & 1) ? 0.5f : 0.125f;
         auto up = [&](int pl) {
+            const float wy[3] = {wy0, wy1, wy2}, wx[3] = {wx0, wx1, wx2};
             float acc = 0.f;
-            for (int a = 0; a < ny; ++a) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
                 float r = 0.f;
-                for (int b = 0; b < nx; ++b) r += wx[b] * s_c[pl][y0 + a][x0 + b];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) r += wx[b] * s_c[pl][y0 + a][x0 + b];
                 acc += wy[a] * r;
             }
             return acc;
