@@ -30,6 +30,14 @@ struct TmaArgs {
     int M, J, Q;
     int inject_wait;         // test hook: wait on a barrier nothing arrives on (short limit) first
     const uint4 *gmat;       // tensor-core form: the split 64-point DFT matrix (64 KB, global)
+    // Tail split (XM_FULL without a list): the first launch takes units [0, tail_base); a second,
+    // cooperative launch shares each unit tail_base .. J-1 among `split` consecutive CTAs, part q
+    // taking batches [q NB / split, (q + 1) NB / split) of every phase, with two hand-offs
+    // through tail_sync[unit - tail_base] (zeroed before that launch); the parts' per-batch error
+    // sums meet in tail_err[(unit - tail_base) * 16 + batch].  Unsplit: tail_base = J.
+    int split, tail_base;
+    int *tail_sync;
+    double *tail_err;
 };
 
 struct TmaMaps {
@@ -154,6 +162,27 @@ __device__ __forceinline__ bool tc_dft256(float2 *buf, bool inverse, const TmaPi
 // position with B = 32).  One unit: position j (or (j, m) for the mixed-state forms).  After a
 // wait gives up the unit returns with p.failed set (uniformly) before waiting again, so the parity
 // of a stage whose wait failed stays that of the load still in flight (tma_pipe_finish drains it).
+// Hand-off between the CTAs sharing a tail unit (thread 0; its bulk stores of the phase have
+// completed): release one arrival on the counter, then wait (bounded, ~1 s) until `target`
+// arrivals, with async-proxy fences on both sides so that the partners' TMA stores are seen by
+// this CTA's TMA loads.  Returns false when the wait gave up.
+__device__ __forceinline__ bool tail_handoff(int *ctr, int target) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");
+    const long long start = clock64();
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            return true;
+        }
+        if (clock64() - start > (1ll << 31)) break;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Returns the updated mutable state: bits 0-1 parity, bit 2 failed, bit 3 timed out, bit 4 the
 // MMA barrier's phase parity (tensor-core form).
 __host__ __device__ constexpr uint32_t tma_state(uint32_t parity, bool failed, bool timed_out, uint32_t mphase = 0) {
@@ -162,8 +191,12 @@ __host__ __device__ constexpr uint32_t tma_state(uint32_t parity, bool failed, b
 
 // TC: the 256-point transforms on the tensor cores (tc_dft256) instead of the FP32 radix FFT;
 // 16-row stages, one-mode XM_FULL only.
-template <int B, int XM, bool TC = false>
-__device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a, const TmaMaps &tm, int u) {
+// SPLIT: part q of S of a tail unit (the CTAs blockIdx / S of the tail launch share it; its slot
+// at slot_override); otherwise the whole unit with a compile-time batch range.  The Fourier error is summed per batch (warps in order, then
+// batches in order), so a split and an unsplit unit give the same error bit for bit.
+template <int B, int XM, bool TC = false, bool SPLIT = false>
+__device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a, const TmaMaps &tm, int u,
+                                             int q = 0, int S = 1, int slot_override = -1) {
     static_assert(!TC || (B == 16 && XM == XM_FULL), "tensor-core form: 16-row stages, XM_FULL");
     constexpr int R = 16, N = 256, NB = N / B;
     constexpr int kTmaThreads = B * 16, kTmaBatch = B;
@@ -213,29 +246,50 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             T::load_2d_hint(bin(s), map, x, y, &bar[s], pol);
         }
     };
-    const int slot_col = p.slot_col;
+    const int slot_col = slot_override >= 0 ? slot_override : p.slot_col;
     const int j = kFull ? u : u / a.Q;
     const int prow0 = kFull ? 0 : (u % a.Q) * N;                  // first probe row of the mode
-    float err = 0.f;
+    const int b0 = SPLIT ? q * (NB / S) : 0, b1 = SPLIT ? b0 + NB / S : NB;   // this part's batches
+    // (only b0 and b1 stay live: the split, its factor and the tail index are derived from them)
+    auto parts = [&]() { return NB / (b1 - b0); };
+    auto tail_index = [&]() { return (int)blockIdx.x / parts(); };
+    double *s_wsum = p.s_red;                                     // [2][32] warp sums, by batch parity
+    double *s_berr = p.s_red + 64;                                // [NB] per-batch error sums
+    // per-batch error: warp sums in FP32, then the batch's sum over warps in order (double)
+    auto batch_error = [&](float eb, int b) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) eb += __shfl_xor_sync(0xffffffffu, eb, o);
+        if ((tid & 31) == 0) s_wsum[(b & 1) * 32 + (tid >> 5)] = (double)eb;
+    };
+    auto batch_error_sum = [&](int b) {                           // thread 0, after a block barrier
+        double e = 0.0;
+        for (int w = 0; w < kTmaThreads / 32; ++w) e += s_wsum[(b & 1) * 32 + w];
+        s_berr[b] = e;
+    };
+    auto handoff = [&](int target) {                              // every thread; uniform result
+        bool ok = true;
+        if (tid == 0) ok = tail_handoff(a.tail_sync + tail_index(), target);
+        if (__syncthreads_or(!ok)) failed = true;
+    };
     if constexpr (XM != XM_INV) {
         const int2 pj = a.pos[j];
         // ---- phase R: forward row FFTs -> slot (column-major)
-        prefetch(0, &tm.prow, 0, prow0, p.pol_keep);
-        prefetch(1, &tm.prow, 0, prow0 + kTmaBatch, p.pol_keep);
+        prefetch(0, &tm.prow, 0, prow0 + kTmaBatch * b0, p.pol_keep);
+        prefetch(1, &tm.prow, 0, prow0 + kTmaBatch * (b0 + 1), p.pol_keep);
         float2 pO[R];                                             // object row of the next batch
         {
-            const float2 *orow = a.obj + (size_t)(pj.x + g) * M + pj.y;
+            const float2 *orow = a.obj + (size_t)(pj.x + kTmaBatch * b0 + g) * M + pj.y;
 #pragma unroll
             for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
         }
-        for (int b = 0; b < NB; ++b) {
+        for (int b = b0; b < b1; ++b) {
             const int s = b & 1;
             wait_stage(s);
             float2 *row = bin(s) + g * 256;
             float2 d[R];
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = cmul(row[t + R * m], pO[m]);
-            if (b + 1 < NB) {
+            if (b + 1 < b1) {
                 const float2 *orow = a.obj + (size_t)(pj.x + kTmaBatch * (b + 1) + g) * M + pj.y;
 #pragma unroll
                 for (int m = 0; m < R; ++m) pO[m] = __ldg(orow + t + R * m);
@@ -254,23 +308,27 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             }
             barrier_a();
             if (failed) return tma_state(parity, failed, timed_out, mphase);
-            if (b + 2 < NB) prefetch(s, &tm.prow, 0, prow0 + kTmaBatch * (b + 2), p.pol_keep);
+            if (b + 2 < b1) prefetch(s, &tm.prow, 0, prow0 + kTmaBatch * (b + 2), p.pol_keep);
             float2 *ob = bout + h * 4096;
 #pragma unroll
             for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
             publish(&tm.slot_r, kTmaBatch * b, slot_col, 16, 0, p.pol_keep);
         }
         if (tid == 0) T::wait_all<0>();                          // slot complete before phase C reads it
-        prefetch(0, &tm.slot_c, 0, slot_col, p.pol_stream);
-        prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch, p.pol_stream);
+        if (b1 - b0 < NB) {
+            handoff(parts());                                    // every part's rows are in the slot
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
+        }
+        prefetch(0, &tm.slot_c, 0, slot_col + kTmaBatch * b0, p.pol_stream);
+        prefetch(1, &tm.slot_c, 0, slot_col + kTmaBatch * (b0 + 1), p.pol_stream);
         // ---- phase C: column FFTs (modulus replacement and inverse column FFTs in XM_FULL)
         float4 An[R / 4];                                         // amplitudes of the next column
         if constexpr (kFull) {
-            const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + g) * N + t * R);
+            const float4 *amp = reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + kTmaBatch * b0 + g) * N + t * R);
 #pragma unroll
             for (int v = 0; v < R / 4; ++v) An[v] = T::ldg_hint(amp + v, p.pol_stream);
         }
-        for (int b = 0; b < NB; ++b) {
+        for (int b = b0; b < b1; ++b) {
             const int s = b & 1;
             const int c = kTmaBatch * b + g;
             float A[R];                                           // A[k2] = |F psi| target at ky = t + 16 k2
@@ -279,7 +337,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
                 for (int v = 0; v < R / 4; ++v) {
                     A[4 * v] = An[v].x; A[4 * v + 1] = An[v].y; A[4 * v + 2] = An[v].z; A[4 * v + 3] = An[v].w;
                 }
-                if (b + 1 < NB) {
+                if (b + 1 < b1) {
                     const float4 *amp =
                         reinterpret_cast<const float4 *>(a.amp + ((size_t)j * N + c + kTmaBatch) * N + t * R);
 #pragma unroll
@@ -303,6 +361,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
                 // d = N Psi (unnormalised transforms).  The projection A Psi / |Psi| does not
                 // depend on the scale of Psi, and the inverse transform's 1/N is folded into the
                 // projected amplitude, so neither unitary scaling costs a pass of its own.
+                float eb = 0.f;
 #pragma unroll
                 for (int m = 0; m < R; ++m) {
                     const float2 X = d[m];
@@ -310,13 +369,14 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
                     if (mag2 > 0.f) {
                         const float inv = rsqrtf(mag2);
                         const float dm = mag2 * inv * invN - A[m];
-                        err += dm * dm;
+                        eb += dm * dm;
                         d[m] = cscale(X, A[m] * invN * inv);
                     } else {
-                        err += A[m] * A[m];
+                        eb += A[m] * A[m];
                         d[m] = make_float2(A[m] * invN, 0.f);
                     }
                 }
+                batch_error(eb, b);
                 if constexpr (TC) {
 #pragma unroll
                     for (int m = 0; m < R; ++m) col[t + R * m] = d[m];
@@ -335,7 +395,8 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             }
             barrier_a();
             if (failed) return tma_state(parity, failed, timed_out, mphase);
-            if (b + 2 < NB) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2), p.pol_stream);
+            if (kFull && tid == 0) batch_error_sum(b);
+            if (b + 2 < b1) prefetch(s, &tm.slot_c, 0, slot_col + kTmaBatch * (b + 2), p.pol_stream);
             float2 *ob = bout + h * 4096;
 #pragma unroll
             for (int m = 0; m < R; ++m) ob[T::swz128_index(t + R * m, gl)] = d[m];
@@ -375,10 +436,19 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
     }
     if constexpr (XM != XM_FWD) {
         if (tid == 0) T::wait_all<0>();                          // psi columns complete before R'
-        prefetch(0, &tm.psi_r, 0, u * N, p.pol_stream);
-        prefetch(1, &tm.psi_r, 0, u * N + kTmaBatch, p.pol_stream);
+        if (b1 - b0 < NB) {
+            if (kFull && tid == 0)
+                for (int b = b0; b < b1; ++b) a.tail_err[tail_index() * 16 + b] = s_berr[b];
+            handoff(2 * parts());                                // every part's columns are in psi
+            if (failed) return tma_state(parity, failed, timed_out, mphase);
+            if (kFull && b0 == 0 && tid == 0)
+                for (int b = 0; b < NB; ++b)
+                    if (b >= b1) s_berr[b] = __ldcg(a.tail_err + tail_index() * 16 + b);
+        }
+        prefetch(0, &tm.psi_r, 0, u * N + kTmaBatch * b0, p.pol_stream);
+        prefetch(1, &tm.psi_r, 0, u * N + kTmaBatch * (b0 + 1), p.pol_stream);
         // ---- phase R': inverse row FFTs of psi[u] -> psi'
-        for (int b = 0; b < NB; ++b) {
+        for (int b = b0; b < b1; ++b) {
             const int s = b & 1;
             wait_stage(s);
             float2 *row = bin(s) + g * 256;
@@ -395,7 +465,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             if constexpr (!TC) pm::fft_group_xs<R, +1>(d, row, tw, t);
             barrier_a();
             if (failed) return tma_state(parity, failed, timed_out, mphase);
-            if (b + 2 < NB) prefetch(s, &tm.psi_r, 0, u * N + kTmaBatch * (b + 2), p.pol_stream);
+            if (b + 2 < b1) prefetch(s, &tm.psi_r, 0, u * N + kTmaBatch * (b + 2), p.pol_stream);
             if constexpr (kFull) {                               // 1/N already applied in phase C
 #pragma unroll
                 for (int m = 0; m < R; ++m) bout[g * 256 + t + R * m] = d[m];
@@ -407,14 +477,9 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
         }
     }
     if constexpr (kFull) {
-        double e = (double)err;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((tid & 31) == 0) p.s_red[tid >> 5] = e;
-        __syncthreads();
-        if (tid == 0) {
+        if (b0 == 0 && tid == 0) {
             double sum = 0.0;
-            for (int w = 0; w < kTmaThreads / 32; ++w) sum += p.s_red[w];
+            for (int b = 0; b < NB; ++b) sum += s_berr[b];
             a.err[j] = sum;
         }
     }
@@ -496,13 +561,17 @@ __host__ __device__ constexpr size_t tma_kernel_smem() {
     return tma_smem_bytes<B>() + (TC ? (size_t)1024 + 65536 + 32768 : 0);
 }
 
-template <int B, int XM, bool TC = false>
+// TAIL = false: the units [0, tail_base) (all of them unless the tail is split), persistent,
+// one CTA per unit.  TAIL = true (XM_FULL, a separate launch after it, cooperative, split CTAs
+// per tail unit): CTA c takes part c mod split of unit tail_base + c / split, in the slot of
+// CTA (c / split) * split, which the finished first launch no longer uses.
+template <int B, int XM, bool TC = false, bool TAIL = false>
 __global__ void __launch_bounds__(B * 16, TC ? 1 : 32 / B)
 k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     constexpr size_t kTmaBuf = tma_buf_bytes<B>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ double s_red[B * 16 / 32];
+    __shared__ double s_red[96];                  // warp sums [2][32], per-batch error sums [NB]
     __shared__ uint32_t s_pending;
     __shared__ uint32_t s_tmem;
     TmaPipe p;
@@ -536,8 +605,17 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
     if (a.inject_wait) tma_pipe_inject_wait(p);
-    for (int iu = blockIdx.x; iu < units && !p.failed; iu += gridDim.x)
-        tma_apply(p, tma_unit<B, XM, TC>(p, a, tm, (XM == XM_LIST) ? a.list[iu] : iu));
+    if constexpr (TAIL) {
+        static_assert(XM == XM_FULL, "split tails: XM_FULL only");
+        const int ti = (int)blockIdx.x / a.split;
+        if (!p.failed && a.tail_base + ti < units)
+            tma_apply(p, tma_unit<B, XM, TC, true>(p, a, tm, a.tail_base + ti, (int)blockIdx.x % a.split, a.split,
+                                                   ti * a.split * 256));
+    } else {
+        const int nunits = (XM == XM_FULL && a.list == nullptr) ? a.tail_base : units;
+        for (int iu = blockIdx.x; iu < nunits && !p.failed; iu += gridDim.x)
+            tma_apply(p, tma_unit<B, XM, TC>(p, a, tm, (XM == XM_LIST) ? a.list[iu] : iu));
+    }
     tma_pipe_finish(p, a.status);
     if constexpr (TC) {
         // an MMA whose completion wait gave up may still be running: wait once more (bounded),

@@ -442,7 +442,7 @@ k_exit_wave_all(const int4 *__restrict__ units, int nunits, const ExitArgs *__re
     float2 *tw256 = (float2 *)(base + kAllScratch);
     float2 *tw128 = tw256 + 256, *tw64 = tw128 + 128, *tw16 = tw64 + 64;
     __shared__ uint64_t s_bar[4];
-    __shared__ double s_red[kAllThreads / 32];
+    __shared__ double s_red[96];                  // the N = 256 unit: warp sums [2][32], batch sums [8]
     __shared__ uint32_t s_pending;
     const int tid = threadIdx.x;
     TmaPipe p;
@@ -841,6 +841,8 @@ struct ptycho_ctx {
     int4 *d_tlist = nullptr;                              // tile lists: (j, y, x, 0)
     int ntx = 0, ntiles = 0;
     int *d_status = nullptr;
+    int *d_tail_sync = nullptr;                           // N = 256 tail split: hand-off counters
+    double *d_tail_err = nullptr;                         // ... and per-batch error sums [grid / 2][16]
     int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout
     TmaMaps tm;
     bool exit_tma = false;
@@ -874,6 +876,7 @@ void free_ctx(ptycho_ctx *h) {
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
                     h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder,
+                    h->d_tail_sync, h->d_tail_err,
                     h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -887,6 +890,9 @@ template <int B, int XM, bool TC = false>
 int setup_tma_kernel(ptycho_ctx *h, int *per_sm) {
     const size_t smem = tma_kernel_smem<B, TC>();
     PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B, XM, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (XM == XM_FULL)
+        PM_CUDA(cudaFuncSetAttribute(k_exit_wave_tma<B, XM, TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_exit_wave_tma<B, XM, TC>, B * 16, smem));
     if (*per_sm < 1) return pm::fail(PTYCHO_ECUDA, "TMA exit-wave kernel cannot be resident");
     h->exit_smem = smem;
@@ -950,8 +956,23 @@ int encode_tma_maps(TmaMaps *tm, float2 *probe, float2 *psi, float2 *slot, int Q
     return encode_2d(&tm->psi_w, psi, c64, 8, N, psi_rows, 256, 16, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
+// Slots of the N = 256 kernel: one per CTA (a split tail reuses the slots of the first launch).
+int exit_slots(int grid) { return grid; }
+
 int encode_exit_tma(ptycho_ctx *h) {
-    return encode_tma_maps(&h->tm, h->d_probe, h->d_psi, h->d_slot, h->Q, h->J, h->grid_exit, h->tma_batch);
+    return encode_tma_maps(&h->tm, h->d_probe, h->d_psi, h->d_slot, h->Q, h->J, exit_slots(h->grid_exit),
+                           h->tma_batch);
+}
+
+int alloc_tail(ptycho_ctx *h) {
+    if (h->d_tail_sync) PM_CUDA(cudaFree(h->d_tail_sync));
+    if (h->d_tail_err) PM_CUDA(cudaFree(h->d_tail_err));
+    h->d_tail_sync = nullptr;
+    h->d_tail_err = nullptr;
+    const int cap = std::max(1, h->grid_exit / 2);
+    int rc = dalloc(&h->d_tail_sync, (size_t)cap);
+    if (!rc) rc = dalloc(&h->d_tail_err, (size_t)cap * 16);
+    return rc;
 }
 
 TmaArgs tma_args(ptycho_ctx *h) {
@@ -968,7 +989,53 @@ TmaArgs tma_args(ptycho_ctx *h) {
     a.Q = h->Q;
     a.inject_wait = h->inject_wait;
     a.gmat = h->gmat;
+    a.split = 1;
+    a.tail_base = h->J;
+    a.tail_sync = h->d_tail_sync;
+    a.tail_err = h->d_tail_err;
     return a;
+}
+
+// Split factor of the last, partial round of a full-batch launch over J positions on `grid`
+// persistent CTAs: the T = J mod grid leftover positions are each shared by S CTAs (a power of
+// two with S T <= grid and at least two batches per part), so the round takes ~1/S of a
+// position's time instead of one.  1 = no split (no leftover, fewer positions than CTAs, a
+// stream being captured, or the test hook).
+int tail_split(const ptycho_ctx *h, int nb) {
+    const int G = h->grid_exit, J = h->J;
+    if (h->inject_wait || J <= G || J % G == 0 || !h->d_tail_sync) return 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 1;
+    const int T = J % G;
+    int S = 1;
+    while (2 * S * T <= G && 2 * S <= nb / 2) S *= 2;
+    return S;
+}
+
+// Full-batch launch: the whole rounds, then (split tail) the leftover units over S CTAs each in
+// a second, cooperative launch, so that every part of a tail unit is resident; if the driver
+// refuses the cooperative launch, one unsplit launch takes the tail instead.
+template <int B, bool TC>
+int launch_full_split(ptycho_ctx *h, TmaArgs a) {
+    const int S = tail_split(h, 256 / B);
+    if (S > 1) {
+        const int G = h->grid_exit, T = h->J % G;
+        a.split = S;
+        a.tail_base = h->J - T;
+        k_exit_wave_tma<B, XM_FULL, TC><<<G, B * 16, h->exit_smem, h->st>>>(a, h->tm);
+        PM_LAUNCHED("k_exit_wave_tma");
+        PM_CUDA(cudaMemsetAsync(h->d_tail_sync, 0, (size_t)T * sizeof(int), h->st));
+        void *args[] = {(void *)&a, (void *)&h->tm};
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_exit_wave_tma<B, XM_FULL, TC, true>,
+                                                          dim3(S * T), dim3(B * 16), args, h->exit_smem, h->st);
+        if (e == cudaSuccess) return PTYCHO_OK;
+        (void)cudaGetLastError();                          // not launched: the tail unsplit,
+        a.split = 1;                                       // one CTA per leftover unit
+        k_exit_wave_tma<B, XM_FULL, TC, true><<<T, B * 16, h->exit_smem, h->st>>>(a, h->tm);
+        return PTYCHO_OK;
+    }
+    k_exit_wave_tma<B, XM_FULL, TC><<<h->grid_exit, B * 16, h->exit_smem, h->st>>>(a, h->tm);
+    return PTYCHO_OK;
 }
 
 int launch_exit_tma(ptycho_ctx *h, int xm) {
@@ -976,9 +1043,13 @@ int launch_exit_tma(ptycho_ctx *h, int xm) {
     if (xm == XM_FWD) k_exit_wave_tma<16, XM_FWD><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (xm == XM_INV) k_exit_wave_tma<16, XM_INV><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
     else if (xm == XM_LIST) k_exit_wave_tma<32, XM_LIST><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
-    else if (h->fft_gemm) k_exit_wave_tma<16, XM_FULL, true><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
-    else if (h->tma_batch == 32) k_exit_wave_tma<32, XM_FULL><<<h->grid_exit, 32 * 16, h->exit_smem, h->st>>>(a, h->tm);
-    else k_exit_wave_tma<16, XM_FULL><<<h->grid_exit, 16 * 16, h->exit_smem, h->st>>>(a, h->tm);
+    else {
+        int rc;
+        if (h->fft_gemm) rc = launch_full_split<16, true>(h, a);
+        else if (h->tma_batch == 32) rc = launch_full_split<32, false>(h, a);
+        else rc = launch_full_split<16, false>(h, a);
+        if (rc) return rc;
+    }
     PM_LAUNCHED("k_exit_wave_tma");
     return PTYCHO_OK;
 }
@@ -1349,7 +1420,8 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_obj, MM);
     if (!rc) rc = dalloc(&h->d_probe, NN * Q);
     if (!rc) rc = dalloc(&h->d_psi, (size_t)J * Q * NN);
-    if (!rc && h->exit_tma) rc = dalloc(&h->d_slot, (size_t)h->grid_exit * NN);
+    if (!rc && h->exit_tma) rc = dalloc(&h->d_slot, (size_t)exit_slots(h->grid_exit) * NN);
+    if (!rc && h->exit_tma) rc = alloc_tail(h);
     if (!rc) rc = dalloc(&h->d_status, 1);
     if (!rc) rc = dalloc(&h->d_num_o, MM);
     if (!rc) rc = dalloc(&h->d_den_o, MM);
@@ -1681,7 +1753,8 @@ int retune_tma(ptycho_ctx *h, int B) {
         if (h->d_slot) PM_CUDA(cudaFree(h->d_slot));
         h->d_slot = nullptr;
         h->grid_exit = grid;
-        if ((rc = dalloc(&h->d_slot, (size_t)grid * h->N * h->N))) return rc;
+        if ((rc = dalloc(&h->d_slot, (size_t)exit_slots(grid) * h->N * h->N))) return rc;
+        if ((rc = alloc_tail(h))) return rc;
     }
     return encode_exit_tma(h);
 }
