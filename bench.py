@@ -208,8 +208,8 @@ def iteration_flops_per_update(N: int) -> float:
 # positions, one launch: dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256, first 16 hex digits).  A changed kernel
 # reports traffic null until it is captured again.
-EXIT_TRAFFIC = {"sources_sha16": "df4316ddbf651827", "bytes_per_position": 1854406,
-                "capture": "ncu, k_exit_wave_tma<16, FULL>, one launch over 400 lab positions"}
+EXIT_TRAFFIC = {"sources_sha16": "24cc1b503c7493a0", "bytes_per_position": 2146538,
+                "capture": "ncu, k_exit_wave_tma<16, FULL>, one launch over 888 lab positions = three whole rounds of 296 CTAs"}
 
 
 def exit_kernel_sources_sha16() -> str:
