@@ -844,6 +844,7 @@ struct ptycho_ctx {
     int *d_tail_sync = nullptr;                           // N = 256 tail split: hand-off counters
     double *d_tail_err = nullptr;                         // ... and per-batch error sums [grid / 2][16]
     int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout
+    int exit_kernels = 1;                                 // kernels of the last full-batch exit pass
     TmaMaps tm;
     bool exit_tma = false;
     bool fft_gemm = false;                                // split-BF16 tensor-core DFTs (N = 64, 128, 256)
@@ -1018,6 +1019,7 @@ int tail_split(const ptycho_ctx *h, int nb) {
 template <int B, bool TC>
 int launch_full_split(ptycho_ctx *h, TmaArgs a) {
     const int S = tail_split(h, 256 / B);
+    h->exit_kernels = S > 1 ? 2 : 1;
     if (S > 1) {
         const int G = h->grid_exit, T = h->J % G;
         a.split = S;
@@ -1172,8 +1174,10 @@ int launch_exit_pass(ptycho_ctx *h, int xm) {
 int launch_exit_any(ptycho_ctx *h, int *launches) {
     int rc;
     if (h->Q == 1) {
-        *launches = 1;
-        return launch_exit_pass(h, XM_FULL);
+        h->exit_kernels = 1;
+        rc = launch_exit_pass(h, XM_FULL);
+        *launches = h->exit_kernels;                      // 2 when the last round was split
+        return rc;
     }
     *launches = 3;
     if ((rc = launch_exit_pass(h, XM_FWD))) return rc;
