@@ -677,7 +677,11 @@ def run_ours(args, world, rank, local):
         conv = [time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, it,
                               probe_update_start=0),
                 time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, it,
-                              probe_update_start=fixed)]
+                              probe_update_start=fixed),
+                # the harder start: the probe's aperture alone (its modulus, no phase curvature)
+                time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0,
+                              probe0.abs().to(probe0.dtype), stream, it, probe_update_start=0,
+                              probe_label="aperture-only probe (the true probe's modulus)")]
         for fusion in ("mnf_no_quantiser", "mnf_weighted_base", "sli", "ideal"):
             conv.append(time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream,
                                       5 * it if fusion in ("sli", "ideal") else it, chunk=20,
@@ -754,10 +758,11 @@ def nrmse_host(obj, truth, mask):
 
 def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, max_iters, chunk=10,
                   target=1e-2, probe_update_start=0, fusion="mnf", algorithm="ap", fft_path="radix_fp32",
-                  alpha=1e-3):
-    """FP32 reconstruction of the benchmarked scan from a flat object with the known probe:
-    NRMSE to the ground truth every `chunk` iterations.  Device time counts the fusion, set-up
-    and iterations (CUDA events), not the NRMSE evaluation."""
+                  alpha=1e-3, probe_label="true probe"):
+    """FP32 reconstruction of the benchmarked scan from a flat object with the given probe (the
+    known probe, or its aperture alone): NRMSE to the ground truth every `chunk` iterations.
+    Device time counts the fusion, set-up and iterations (CUDA events), not the NRMSE
+    evaluation."""
     import torch
     M = cfg.M
     mask = illuminated_mask(sc["probe"], pos, M)
@@ -803,8 +808,8 @@ def time_to_nrmse(api, sc, cfg, raw, params, fused, pos, obj0, probe0, stream, m
             "still_falling": traj[-1][2] <= floor * (1 + 1e-4),
             "goal_used": round(goal, 5), "iterations": hit[0],
             "seconds": round(hit[1] / 1e3, 4),
-            "start": "flat object, true probe, " + ("probe updates on" if probe_update_start == 0
-                                                     else "probe fixed"),
+            "start": f"flat object, {probe_label}, " + ("probe updates on" if probe_update_start == 0
+                                                         else "probe fixed"),
             f"trajectory_every_{chunk * every}": [round(v, 5) for _, _, v in traj[every - 1::every]]}
 
 

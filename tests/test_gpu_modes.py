@@ -55,6 +55,37 @@ def test_mixed_state_small_matches_oracle(api, n_iter, pus):
     np.testing.assert_allclose(e, re, rtol=1e-5)
 
 
+def test_mixed_state_workload_each_iteration_matches_oracle(api):
+    """The mixed-state workload as specified (the small scan with 8 probe modes, 100 iterations
+    from a flat object, probe updates on), followed step by step: after every GPU iteration the
+    FP64 oracle takes one iteration from the GPU's own object and probe modes, and the GPU's next
+    state must agree with it (bound 1e-5 on the first step from the flat object, 1e-6 after)."""
+    sc = synth.make_scan("mixed_small")
+    cfg = sc["cfg"]
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    fused = oracle.mnf_stack(sc["raw"], sc["times"], p).astype(np.float32)
+    f64 = fused.astype(np.float64)
+    A = oracle.amplitudes(f64)
+    M = cfg.M
+    o0 = np.ones((M, M), np.complex64)
+    p0 = sc["probe"].astype(np.complex64)
+    h = api.ptycho_init(torch.from_numpy(fused).cuda(), sc["pos"], o0, p0, probe_update_start=0)
+    obj, probes = o0.astype(np.complex128), p0.astype(np.complex128)
+    worst = [0.0, 0.0]
+    n_iter = 100                                   # the mixed-state workload's iteration count
+    for k in range(n_iter):
+        e = api.ptycho_iterate(h, 1)
+        go, gp = api.ptycho_get_object(h), api.ptycho_get_probe(h)
+        ro, rp, re = oracle.reconstruct_modes(f64, sc["pos"], obj, probes, 1, 1e-3, 1e-3, 0, A=A)
+        d = max(rel_l2(go, ro), rel_l2(gp, rp))
+        assert d <= (1e-5 if k == 0 else 1e-6), (k, d)
+        assert abs(e[0] - re[0]) <= 1e-6 * re[0], k
+        worst[min(k, 1)] = max(worst[min(k, 1)], d)
+        obj, probes = go.astype(np.complex128), gp.astype(np.complex128)
+    api.ptycho_destroy(h)
+    print(f"first step {worst[0]:.2e}, worst later step {worst[1]:.2e} over {n_iter} iterations")
+
+
 def test_mixed_state_256_matches_oracle(api):
     """The N = 256 forward / modulus / inverse kernels: lab geometry, 120 positions, 4 modes,
     two iterations."""
