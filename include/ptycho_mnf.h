@@ -187,6 +187,12 @@ int ptycho_init(ptycho_handle *out, const ptycho_desc *d);
  * With h_err the call synchronises and returns PTYCHO_ENONFINITE if any error is NaN/Inf, or
  * PTYCHO_ETIMEDOUT if a bounded device wait of an exit-wave kernel gave up (that status stays
  * set for the life of the handle); without it the call is asynchronous.
+ * Launches (N = 256, one mode, AP): when J is not a multiple of the persistent grid G of the
+ * exit-wave kernel and J mod G <= G / 2, the J mod G leftover positions of each iteration run
+ * in a second, cooperative launch (a memset of the hand-off counters, then 2-8 CTAs per
+ * position), so that the last round takes a fraction of a position's time; a cooperative launch
+ * waits until the whole grid is resident, i.e. for other work on the device to leave room.  Not
+ * used while the stream is being captured (graphs) — the results are the same either way.
  */
 int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err);
 
