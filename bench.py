@@ -582,8 +582,8 @@ def run_ours(args, world, rank, local):
         raw_d = torch.empty_like(raw)
 
         def e2e_step():
-            raw_d.copy_(raw_h, non_blocking=True)
-            api.fuse_stack(raw_d, cfg.times, params, out=fused, stream=stream)
+            # host stack -> device in chunks, each fused as it lands (fuse_stack_host)
+            api.fuse_stack_host(raw_h, raw_d, cfg.times, params, out=fused, stream=stream)
             h = api.ptycho_init(fused, pos, obj_h, probe_h, stream=stream, fft_path=args.fft)
             api.ptycho_iterate(h, n_iter, errors=False)
             api.ptycho_get_object(h, out_o)

@@ -95,6 +95,26 @@ int fuse_stack_noalloc(const uint16_t *d_raw, int J, int K, int N, const float *
                        const fuse_params *p, float *d_fused, void *cuda_stream);
 
 /*
+ * fuse_stack_host -- fuse_stack for a stack that is still in host memory: the same fusion and
+ * results (bit for bit), with the host-to-device copy overlapped with the fusion.  Positions
+ * are copied in chunks on a copy stream of the library (one per device, created by the first
+ * call) and each chunk is fused on cuda_stream as soon as it has landed, so the copy of one
+ * chunk runs under the fusion of the previous one.  The paper has no counterpart: this is a
+ * deployment variant of the library for data arriving from the host.
+ *   h_raw            host, uint16 [J][K][N][N], read-only, caller-owned; page-locked (pinned)
+ *                    memory is needed for the copies to overlap the fusion (pageable memory
+ *                    works, with copies that do not overlap)
+ *   d_raw            device, uint16 [J][K][N][N], caller-owned staging buffer, overwritten
+ *   chunk_positions  positions per chunk, > 0; 0 = J / 8 (eight chunks)
+ *   others           as fuse_stack
+ * Ordering: the copies start after the work already queued on cuda_stream (d_raw may still be
+ * in use), and work queued on cuda_stream after the call runs after every copy and the whole
+ * fusion.  h_raw must stay valid and unchanged until then.  Asynchronous.
+ */
+int fuse_stack_host(const uint16_t *h_raw, uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                    const fuse_params *p, float *d_fused, int chunk_positions, void *cuda_stream);
+
+/*
  * fuse_sli -- Standard Linear Integration, the linear HDR comparator the paper evaluates MNF
  * against (§1, §2.2, "SLI"): per pixel t_max * sum_{k: I_k < clip} I_k / sum_{k: I_k < clip} t_k
  * (count rate over the unsaturated exposures, in longest-exposure units); a pixel saturated in

@@ -25,7 +25,7 @@ BASE_MODES = {"mean": 0, "sum": 1, "weighted": 2}
 ALGORITHMS = {"ap": 0, "epie_colour": 1}
 DOMAINS = {"radiance": 0, "raw": 1}
 
-EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "fuse_sli", "ptycho_init", "ptycho_iterate",
+EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "fuse_stack_host", "fuse_sli", "ptycho_init", "ptycho_iterate",
            "ptycho_get_object", "ptycho_get_probe", "ptycho_get_colouring", "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
 
 
@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
     L.fuse_stack.restype = ci
     L.fuse_stack_noalloc.argtypes = L.fuse_stack.argtypes
     L.fuse_stack_noalloc.restype = ci
+    L.fuse_stack_host.argtypes = [vp, vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(FuseParamsC),
+                                  vp, ci, vp]
+    L.fuse_stack_host.restype = ci
     L.fuse_sli.argtypes = [vp, ci, ci, ci, ctypes.POINTER(ctypes.c_float), ctypes.c_float, vp, vp]
     L.ptycho_batch_create.restype = ci
     L.ptycho_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ci, ci, vp]
@@ -179,6 +182,30 @@ def fuse_stack(raw, times, params: FuseParamsC, out=None, stream=None):
     t = (ctypes.c_float * K)(*[float(x) for x in times])
     _check(lib().fuse_stack(ctypes.c_void_p(raw.data_ptr()), J, K, N, t, ctypes.byref(params),
                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def fuse_stack_host(raw_host, raw_dev, times, params: FuseParamsC, out=None, stream=None, chunk_positions=0):
+    """MNF of a host-resident stack: raw_host (torch.uint16 CPU tensor [J][K][N][N], pinned for
+    overlap) is copied into raw_dev (torch.uint16 CUDA tensor of the same shape) chunk by chunk
+    while the chunks already copied are fused into out[J][N][N] (float32 CUDA)."""
+    import torch
+    if raw_host.dtype != torch.uint16 or raw_host.is_cuda or not raw_host.is_contiguous():
+        raise ValueError("raw_host must be a contiguous torch.uint16 CPU tensor [J][K][N][N]")
+    if raw_dev.dtype != torch.uint16 or not raw_dev.is_cuda or not raw_dev.is_contiguous() or \
+            tuple(raw_dev.shape) != tuple(raw_host.shape):
+        raise ValueError("raw_dev must be a contiguous torch.uint16 CUDA tensor shaped like raw_host")
+    J, K, N, N2 = raw_host.shape
+    if N != N2:
+        raise ValueError("frames must be square")
+    if out is None:
+        out = torch.empty((J, N, N), dtype=torch.float32, device=raw_dev.device)
+    if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (J, N, N):
+        raise ValueError("out must be a contiguous float32 tensor [J][N][N]")
+    t = (ctypes.c_float * K)(*[float(x) for x in times])
+    _check(lib().fuse_stack_host(ctypes.c_void_p(raw_host.data_ptr()), ctypes.c_void_p(raw_dev.data_ptr()), J, K, N,
+                                 t, ctypes.byref(params), ctypes.c_void_p(out.data_ptr()), int(chunk_positions),
+                                 ctypes.c_void_p(_stream_ptr(stream))))
     return out
 
 

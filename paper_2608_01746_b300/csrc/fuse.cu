@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -444,6 +445,89 @@ extern "C" int fuse_stack(const uint16_t *d_raw, int J, int K, int N, const floa
         cudaError_t e = cudaFreeAsync(scratch, st);
         if (rc == PTYCHO_OK && e != cudaSuccess) return pm::cuda_fail(e, "cudaFreeAsync");
     }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fusion from a host-resident stack: the copies of chunks of positions run on a copy stream of
+// the library (one per device, created on first use) and the fusion of each chunk on the
+// caller's stream as soon as that chunk has landed, so the copy of chunk c + 1 overlaps the
+// fusion of chunk c.  The copy stream first waits for the caller's stream (d_raw may still be in
+// use by earlier work), and the caller's stream waits for every copy before it fuses.
+namespace {
+
+std::mutex g_copy_mu;
+cudaStream_t g_copy_stream[64] = {};
+
+int copy_stream(cudaStream_t *out) {
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return pm::fail(PTYCHO_EINVAL, "fuse_stack_host: device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    if (!g_copy_stream[dev]) PM_CUDA(cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking));
+    *out = g_copy_stream[dev];
+    return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" int fuse_stack_host(const uint16_t *h_raw, uint16_t *d_raw, int J, int K, int N, const float *h_t,
+                               const fuse_params *p, float *d_fused, int chunk_positions, void *cuda_stream) {
+    pm::NvtxRange range("fuse_stack_host");
+    FuseDev f;
+    int rc = pm::validate_fuse(d_raw, J, K, N, h_t, p, d_fused, &f);
+    if (rc != PTYCHO_OK || J == 0) return rc;
+    if (!h_raw) return pm::fail(PTYCHO_EINVAL, "fuse_stack_host: host raw pointer is NULL");
+    if (chunk_positions < 0) return pm::fail(PTYCHO_EINVAL, "fuse_stack_host: chunk_positions %d < 0", chunk_positions);
+    cudaStream_t st = (cudaStream_t)cuda_stream, cs = nullptr;
+    if ((rc = copy_stream(&cs))) return rc;
+    const size_t per_pos = scratch_floats_per_position(K, N, f.L);
+    const size_t cap_floats = ((size_t)2 << 30) / sizeof(float);
+    int chunk = chunk_positions > 0 ? chunk_positions : (J + 7) / 8;          // default: 8 chunks
+    if (per_pos > 0) chunk = (int)std::min<size_t>((size_t)chunk, std::max<size_t>(1, cap_floats / per_pos));
+    chunk = std::max(1, std::min(std::min(chunk, J), 65535 / K));
+    const int nchunks = (J + chunk - 1) / chunk;
+    const size_t NN = (size_t)N * N, pos_elems = (size_t)K * NN;
+    std::vector<cudaEvent_t> ev(nchunks + 1, nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);                        // released once complete
+    };
+    for (auto &e : ev) {
+        const cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (err != cudaSuccess) { e = nullptr; cleanup(); return pm::cuda_fail(err, "cudaEventCreate"); }
+    }
+    cudaError_t err = cudaEventRecord(ev[nchunks], st);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(cs, ev[nchunks], 0);
+    for (int c = 0; c < nchunks && err == cudaSuccess; ++c) {
+        const int j0 = c * chunk, jn = std::min(chunk, J - j0);
+        err = cudaMemcpyAsync(d_raw + (size_t)j0 * pos_elems, h_raw + (size_t)j0 * pos_elems,
+                              (size_t)jn * pos_elems * sizeof(uint16_t), cudaMemcpyHostToDevice, cs);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[c], cs);
+    }
+    if (err != cudaSuccess) { cleanup(); return pm::cuda_fail(err, "fuse_stack_host: copies"); }
+    float *scratch = nullptr;
+    if (per_pos > 0) {
+        err = pm::dev_malloc_async((void **)&scratch, per_pos * chunk * sizeof(float), st);
+        if (err != cudaSuccess) {
+            for (int c = 0; c < nchunks; ++c) cudaStreamWaitEvent(st, ev[c], 0);   // d_raw stays ordered
+            cleanup();
+            return pm::cuda_fail(err, "fuse_stack_host: scratch");
+        }
+    }
+    for (int c = 0; c < nchunks && rc == PTYCHO_OK; ++c) {
+        const int j0 = c * chunk, jn = std::min(chunk, J - j0);
+        err = cudaStreamWaitEvent(st, ev[c], 0);
+        if (err != cudaSuccess) { rc = pm::cuda_fail(err, "cudaStreamWaitEvent"); break; }
+        rc = pm::fuse_dispatch(d_raw + (size_t)j0 * pos_elems, jn, K, N, f, d_fused + (size_t)j0 * NN, scratch, st);
+    }
+    if (rc != PTYCHO_OK)
+        for (int c = 0; c < nchunks; ++c) cudaStreamWaitEvent(st, ev[c], 0);       // later work after every copy
+    if (scratch) {
+        err = cudaFreeAsync(scratch, st);
+        if (rc == PTYCHO_OK && err != cudaSuccess) rc = pm::cuda_fail(err, "cudaFreeAsync");
+    }
+    cleanup();
     return rc;
 }
 

@@ -69,6 +69,18 @@ def test_fuse_stack_rejects_bad_times_and_modes(L):
     assert L.fuse_stack(ctypes.c_void_p(16), 1, 3, 64, t, None, ctypes.c_void_p(16), None) == api.PTYCHO_EINVAL
 
 
+def test_fuse_stack_host_rejects_bad_arguments(L):
+    t = (ctypes.c_float * 3)(1, 10, 100)
+    p = ctypes.byref(_params())
+    # no host stack, negative chunk, and the fuse_stack checks (NULL device buffers)
+    assert L.fuse_stack_host(None, ctypes.c_void_p(16), 1, 3, 64, t, p, ctypes.c_void_p(16), 0, None) == api.PTYCHO_EINVAL
+    assert "host raw" in api.last_error()
+    assert L.fuse_stack_host(ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 3, 64, t, p, ctypes.c_void_p(16), -1,
+                             None) == api.PTYCHO_EINVAL
+    assert L.fuse_stack_host(ctypes.c_void_p(16), None, 1, 3, 64, t, p, ctypes.c_void_p(16), 0, None) == api.PTYCHO_EINVAL
+    assert L.fuse_stack_host(None, None, 0, 3, 64, t, p, None, 0, None) == api.PTYCHO_OK      # J = 0: no-op
+
+
 def test_fuse_stack_zero_positions_is_noop(L):
     t = (ctypes.c_float * 3)(1, 10, 100)
     assert L.fuse_stack(None, 0, 3, 64, t, ctypes.byref(_params()), None, None) == api.PTYCHO_OK
