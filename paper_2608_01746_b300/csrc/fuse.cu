@@ -45,14 +45,15 @@ __device__ __forceinline__ float wg(int a) {
     return a == 2 ? 0.375f : ((a == 1 || a == 3) ? 0.25f : 0.0625f);
 }
 
-// Exposure weights (Eq. 5, normalised over k) and radiance of one level-0 pixel.
+// Exposure weights (Eq. 5, normalised over k) and radiance of one level-0 pixel from its K
+// raw counts.
 template <int K>
-__device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, size_t p,
-                                             const FuseDev &f, float (&E)[K], float (&W)[K]) {
+__device__ __forceinline__ void level0_counts(const uint16_t (&c)[K], const FuseDev &f, float (&E)[K],
+                                              float (&W)[K]) {
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float v = (float)__ldg(raw_j + k * NN + p);
+        const float v = (float)c[k];
         E[k] = v * f.tscale[k];
         const float d = fminf(v, f.clip) / f.clip - f.mu;
         W[k] = expf(-d * d * f.inv2s2);
@@ -60,6 +61,15 @@ __device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, s
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) W[k] = (s > 0.f) ? W[k] / s : 1.0f / K;
+}
+
+template <int K>
+__device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, size_t p,
+                                             const FuseDev &f, float (&E)[K], float (&W)[K]) {
+    uint16_t c[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) c[k] = __ldg(raw_j + k * NN + p);
+    level0_counts<K>(c, f, E, W);
 }
 
 __device__ __forceinline__ float quantise(float x, float delta) {
@@ -95,15 +105,46 @@ __device__ __forceinline__ void reduce0_body(const uint16_t *__restrict__ raw, f
     }
     const int rows = 2 * outs_y + 3, cols = 2 * outs_x + 3;
     const int tid = threadIdx.x;
-    for (int e = tid; e < rows * cols; e += blockDim.x) {
-        const int a = e / cols, b = e % cols;
-        const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
-        float E[K], W[K];
-        level0_pixel<K>(raw_j, NN, p, f, E, W);
+    if (FULL) {
+        // every raw count of this thread's pixels first (all loads in flight together), then
+        // the weights and radiances (blockDim.x = 256)
+        constexpr int kPix = kIn * kIn, kPer = (kPix + 255) / 256;
+        uint16_t c[kPer][K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            s_e[(k * kIn + a) * kInP + b] = E[k];
-            s_w[(k * kIn + a) * kInP + b] = W[k];
+        for (int i = 0; i < kPer; ++i) {
+            const int e = tid + 256 * i;
+            if (e < kPix) {
+                const int a = e / kIn, b = e % kIn;
+                const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
+#pragma unroll
+                for (int k = 0; k < K; ++k) c[i][k] = __ldg(raw_j + k * NN + p);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int e = tid + 256 * i;
+            if (e < kPix) {
+                const int a = e / kIn, b = e % kIn;
+                float E[K], W[K];
+                level0_counts<K>(c[i], f, E, W);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    s_e[(k * kIn + a) * kInP + b] = E[k];
+                    s_w[(k * kIn + a) * kInP + b] = W[k];
+                }
+            }
+        }
+    } else {
+        for (int e = tid; e < rows * cols; e += blockDim.x) {
+            const int a = e / cols, b = e % cols;
+            const size_t p = (size_t)refl(2 * oy0 - 2 + a, N) * N + refl(2 * ox0 - 2 + b, N);
+            float E[K], W[K];
+            level0_pixel<K>(raw_j, NN, p, f, E, W);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                s_e[(k * kIn + a) * kInP + b] = E[k];
+                s_w[(k * kIn + a) * kInP + b] = W[k];
+            }
         }
     }
     __syncthreads();
