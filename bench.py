@@ -621,7 +621,12 @@ def run_ours(args, world, rank, local):
     names = ["k_exit_wave", "object update (k_object_gather + k_apply)",
              "probe update (k_probe_partial + k_probe_reduce + k_apply)", "k_error_reduce"]
     Q = cfg.modes
-    exit_ms = stage_ms[0] / max(stage_n[0], 1) * (3 if Q > 1 else 1)   # per iteration
+    # the exit-wave stage per iteration: one launch over all J positions, or (N = 256, split last
+    # round) the whole-round launch plus the cooperative tail launch; with modes the forward,
+    # modulus and inverse launches
+    n_timed = args.steps * n_iter
+    exit_ms = float(stage_ms[0]) / n_timed
+    exit_launches = float(stage_n[0]) / n_timed
     iter_ms = float(stage_ms.sum()) / (args.steps * n_iter)
     fma = api.measure_fp32_fma_tflops(device=dev)
     flops = Q * exit_wave_flops_per_position(N) * J / (exit_ms / 1e3) / 1e12
@@ -637,12 +642,18 @@ def run_ours(args, world, rank, local):
     roof = {"kernel": kname, "bound": "hbm",
             "achieved": round(hbm_algo, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(hbm_algo / hbm_peak, 4), "peak_kind": peak_kind,
-            "bytes_per_position": exit_wave_bytes_per_position(N), "positions_per_launch": J,
+            "bytes_per_position": exit_wave_bytes_per_position(N), "positions_per_iteration": J,
             "traffic": traffic,
             "traffic_note": (f"ncu DRAM bytes per position {EXIT_TRAFFIC['bytes_per_position']} x {J} positions "
                              f"({EXIT_TRAFFIC['capture']})" if traffic else
                              "null: no ncu capture of the current kernel sources"),
-            "avg_launch_ms": round(exit_ms, 4),
+            "ms_per_iteration": round(exit_ms, 4),
+            "launches_per_iteration": round(exit_launches, 2),
+            "launch_note": ("the whole rounds in one launch and the J mod grid leftover positions in a second, "
+                            "cooperative launch (several CTAs per position); achieved = J positions' bytes over "
+                            "the two launches' time" if exit_launches > 1.5 and Q == 1 else
+                            "one launch per iteration" if Q == 1 else
+                            "forward, modulus and inverse launches per iteration"),
             "alu_view": {"achieved_tflops": round(flops, 2), "peak_tflops": round(fma["tflops"], 2),
                          "peak_kind": "measured: the library's FP32 FMA kernel, best of 5 launches",
                          "frac": round(flops / fma["tflops"], 4),
@@ -663,7 +674,8 @@ def run_ours(args, world, rank, local):
                 "achieved": round(tflops, 2), "peak": bf16_peak, "unit": "TFLOP/s",
                 "frac": round(tflops / bf16_peak, 4), "peak_kind": bf16_kind,
                 "flops_per_position": dftgemm_flops_per_position(N),
-                "traffic": None, "avg_launch_ms": round(exit_ms, 4),
+                "traffic": None, "ms_per_iteration": round(exit_ms, 4),
+                "launches_per_iteration": round(exit_launches, 2),
                 "fp32_fft_equivalent_tflops": round(flops, 2),
                 "hbm_view": {"achieved_gbs": round(hbm_algo, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                              "frac": round(hbm_algo / hbm_peak, 4),
