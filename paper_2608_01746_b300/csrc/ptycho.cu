@@ -504,7 +504,7 @@ __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const fl
 // Warp w takes every 8th position of the tile's (ascending) list; lane = tile column, and
 // each lane keeps its column's kTR pixels in registers.
 template <int QC>   // QC = 1: one probe mode (compile-time); 0: Q modes at run time
-__global__ void __launch_bounds__(kThreads, 3) k_object_gather(
+__global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
     const int *__restrict__ tstart, const int4 *__restrict__ tlist, const int *__restrict__ torder,
     float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx, int Q) {
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
 // Probe partial sums: block (kTR x 32 probe tile, chunk of positions) -> partial[chunk][q].
 // Warp w takes every 8th position of the chunk; lane = tile column, kTR rows in registers.
 template <int QC>   // QC = 1: one probe mode (compile-time); 0: Q modes at run time
-__global__ void __launch_bounds__(kThreads, 3) k_probe_partial(
+__global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
     float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk, int Q) {
     __shared__ WarpTiles wt;
