@@ -279,12 +279,17 @@ const char *ptycho_last_error(void);
 
 /*
  * Test hooks for the failure paths (no counterpart in the paper; for the library's own tests).
- *   ptycho_debug_wait_timeout  enable != 0: every later exit-wave launch of the handle first
+ *   ptycho_debug_wait_timeout  enable = 1: every later exit-wave launch of the handle first
  *       waits, with a limit of about 2^20 SM cycles, on a barrier that nothing arrives on, before
  *       it issues any copy; the wait gives up, the kernel sets the handle's status word and
- *       returns, and ptycho_iterate with h_err reports PTYCHO_ETIMEDOUT.  The device context stays
- *       usable.  The status word is sticky: the handle keeps reporting the timeout, so destroy
- *       it.  Handles whose exit-wave kernel has no bounded waits (N != 256) get PTYCHO_EINVAL.
+ *       returns, and ptycho_iterate with h_err reports PTYCHO_ETIMEDOUT.  enable = 2: in the
+ *       split last round of an iteration (see ptycho_iterate), the first CTA of every leftover
+ *       position does not arrive at its first hand-off, so the other CTAs' waits (limit about
+ *       2^31 SM cycles, ~1 s) give up: PTYCHO_ETIMEDOUT the same way (a handle whose positions
+ *       leave no split round runs normally).  enable = 0 switches the hook off.  The device
+ *       context stays usable.  The status word is sticky: the handle keeps reporting the
+ *       timeout, so destroy it.  Handles whose exit-wave kernel has no bounded waits (N != 256)
+ *       get PTYCHO_EINVAL.
  *   ptycho_debug_fail_alloc  nth > 0: the nth device allocation the library makes from now on
  *       (any entry point, any thread) fails as if the device were out of memory, and the call
  *       that made it returns PTYCHO_ENOMEM after releasing what it had allocated; nth = 0

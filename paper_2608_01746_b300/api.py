@@ -359,9 +359,11 @@ def ptycho_destroy(h: PtychoHandle) -> None:
     h.close()
 
 
-def ptycho_debug_wait_timeout(h: PtychoHandle, enable: bool) -> None:
-    """Test hook: the handle's exit-wave launches first wait on a barrier nothing arrives on."""
-    _check(lib().ptycho_debug_wait_timeout(h.ptr, int(bool(enable))))
+def ptycho_debug_wait_timeout(h: PtychoHandle, enable) -> None:
+    """Test hook: 1 (or True) = the handle's exit-wave launches first wait on a barrier nothing
+    arrives on; 2 = in the split last round, the first CTA of each leftover position skips its
+    first hand-off arrival, so its partners' bounded waits run out; 0 = off."""
+    _check(lib().ptycho_debug_wait_timeout(h.ptr, int(enable)))
 
 
 def ptycho_debug_fail_alloc(nth: int) -> None:

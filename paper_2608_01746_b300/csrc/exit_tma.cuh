@@ -28,7 +28,8 @@ struct TmaArgs {
     const int *list;         // XM_FULL: if not NULL, process positions list[0 .. count)
     int count;
     int M, J, Q;
-    int inject_wait;         // test hook: wait on a barrier nothing arrives on (short limit) first
+    int inject_wait;         // test hook: 1 = wait on a barrier nothing arrives on (short limit)
+                             // first; 2 = part 0 of every split tail unit skips its first arrival
     const uint4 *gmat;       // tensor-core form: the split 64-point DFT matrix (64 KB, global)
     // Tail split (XM_FULL without a list): the first launch takes units [0, tail_base); a second,
     // cooperative launch shares each unit tail_base .. J-1 among `split` consecutive CTAs, part q
@@ -166,9 +167,10 @@ __device__ __forceinline__ bool tc_dft256(float2 *buf, bool inverse, const TmaPi
 // completed): release one arrival on the counter, then wait (bounded, ~1 s) until `target`
 // arrivals, with async-proxy fences on both sides so that the partners' TMA stores are seen by
 // this CTA's TMA loads.  Returns false when the wait gave up.
-__device__ __forceinline__ bool tail_handoff(int *ctr, int target) {
+// skip_arrival (test hook only): wait without arriving, so that the partners' waits run out.
+__device__ __forceinline__ bool tail_handoff(int *ctr, int target, bool skip_arrival = false) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
-    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");
+    if (!skip_arrival) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(ctr) : "memory");
     const long long start = clock64();
     for (uint32_t i = 0; i < (1u << 26); ++i) {
         int v;
@@ -268,7 +270,8 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
     };
     auto handoff = [&](int target) {                              // every thread; uniform result
         bool ok = true;
-        if (tid == 0) ok = tail_handoff(a.tail_sync + tail_index(), target);
+        if (tid == 0)
+            ok = tail_handoff(a.tail_sync + tail_index(), target, a.inject_wait == 2 && b0 == 0 && target == parts());
         if (__syncthreads_or(!ok)) failed = true;
     };
     if constexpr (XM != XM_INV) {
@@ -604,7 +607,7 @@ k_exit_wave_tma(TmaArgs a, const __grid_constant__ TmaMaps tm) {
     }
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int units = (XM == XM_LIST) ? a.count : (kFull ? a.J : a.J * a.Q);
-    if (a.inject_wait) tma_pipe_inject_wait(p);
+    if (a.inject_wait == 1) tma_pipe_inject_wait(p);
     if constexpr (TAIL) {
         static_assert(XM == XM_FULL, "split tails: XM_FULL only");
         const int ti = (int)blockIdx.x / a.split;

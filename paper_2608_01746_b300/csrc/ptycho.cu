@@ -843,7 +843,7 @@ struct ptycho_ctx {
     int *d_status = nullptr;
     int *d_tail_sync = nullptr;                           // N = 256 tail split: hand-off counters
     double *d_tail_err = nullptr;                         // ... and per-batch error sums [grid / 2][16]
-    int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout
+    int inject_wait = 0;                                  // test hook, see ptycho_debug_wait_timeout (0, 1, 2)
     int exit_kernels = 1;                                 // kernels of the last full-batch exit pass
     TmaMaps tm;
     bool exit_tma = false;
@@ -1004,7 +1004,7 @@ TmaArgs tma_args(ptycho_ctx *h) {
 // stream being captured, or the test hook).
 int tail_split(const ptycho_ctx *h, int nb) {
     const int G = h->grid_exit, J = h->J;
-    if (h->inject_wait || J <= G || J % G == 0 || !h->d_tail_sync) return 1;
+    if (h->inject_wait == 1 || J <= G || J % G == 0 || !h->d_tail_sync) return 1;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(h->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 1;
     const int T = J % G;
@@ -1570,7 +1570,9 @@ extern "C" int ptycho_debug_wait_timeout(ptycho_handle h, int enable) {
     if (!h->exit_tma)
         return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: the handle's exit-wave kernel (N = %d) has no "
                                        "bounded waits to exercise; the hook needs N = 256", h->N);
-    h->inject_wait = enable != 0;
+    if (enable < 0 || enable > 2)
+        return pm::fail(PTYCHO_EINVAL, "ptycho_debug_wait_timeout: enable = %d not in {0, 1, 2}", enable);
+    h->inject_wait = enable;
     return PTYCHO_OK;
 }
 

@@ -1,6 +1,7 @@
 """Failure paths of the C ABI on the GPU, made without faulting the device: a bounded wait that
-runs out (a barrier nothing arrives on, limited to ~2^20 cycles) must come back as
-PTYCHO_ETIMEDOUT with the context still usable, and a device allocation that fails (host-side
+runs out (a barrier nothing arrives on, limited to ~2^20 cycles; a hand-off counter a partner
+never completes, limited to ~2^31 cycles) must come back as PTYCHO_ETIMEDOUT with the context
+still usable, and a device allocation that fails (host-side
 hook) must come back as PTYCHO_ENOMEM with everything the call had allocated released."""
 import dataclasses
 
@@ -60,6 +61,39 @@ def test_wait_timeout_reports_etimedout_and_context_survives(api, lab8):
     # the context is intact: a fresh handle gives exactly the reference result
     h = _init(api, lab8)
     e = api.ptycho_iterate(h, 2)
+    o = api.ptycho_get_object(h)
+    api.ptycho_destroy(h)
+    assert np.array_equal(e, e_ref)
+    assert np.array_equal(o, o_ref)
+
+
+def test_split_tail_handoff_timeout(api):
+    """The hand-off of the split last round (CTAs sharing a leftover position meet on a global
+    counter) gives up after its bounded wait when a partner never arrives (hook 2: the first CTA
+    of each leftover position skips its first arrival): PTYCHO_ETIMEDOUT, and a fresh handle on
+    the same data then reproduces the reference bit for bit."""
+    G = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    cfg = dataclasses.replace(synth.CONFIGS["lab"], J=G + 40)        # 40 leftover positions: split
+    sc = synth.make_scan_torch(cfg, seed=99)
+    fused = api.fuse_stack(sc["raw"], cfg.times, api.fuse_params(levels=cfg.levels, clip=float(cfg.clip)))
+    del sc["raw"]
+    torch.cuda.synchronize()
+    d = dict(fused=fused, pos=sc["pos"], obj0=np.ones((cfg.M, cfg.M), np.complex64),
+             probe0=sc["probe"].astype(np.complex64))
+    ref = _init(api, d)
+    e_ref = api.ptycho_iterate(ref, 1)
+    o_ref = api.ptycho_get_object(ref)
+    api.ptycho_destroy(ref)
+
+    h = _init(api, d)
+    api.ptycho_debug_wait_timeout(h, 2)
+    with pytest.raises(api.PtychoError) as ei:
+        api.ptycho_iterate(h, 1)
+    assert ei.value.code == api.PTYCHO_ETIMEDOUT
+    api.ptycho_destroy(h)
+
+    h = _init(api, d)
+    e = api.ptycho_iterate(h, 1)
     o = api.ptycho_get_object(h)
     api.ptycho_destroy(h)
     assert np.array_equal(e, e_ref)
