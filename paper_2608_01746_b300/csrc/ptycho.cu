@@ -506,7 +506,7 @@ __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const fl
 template <int QC>   // QC = 1: one probe mode (compile-time); 0: Q modes at run time
 __global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_object_gather(
     const float2 *__restrict__ psi, const float2 *__restrict__ probe, const int2 *__restrict__ pos,
-    const int *__restrict__ tstart, const int4 *__restrict__ tlist, const int *__restrict__ torder,
+    const int4 *__restrict__ tlist, const int *__restrict__ torder, const int2 *__restrict__ trange,
     float2 *__restrict__ num, float *__restrict__ den, float *__restrict__ tile_max, int M, int N, int ntx, int Q) {
     __shared__ WarpTiles wt;
     __shared__ float s_max[kThreads / 32];
@@ -524,7 +524,8 @@ __global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_object_gather(
     // The tile's list is staged in shared memory in chunks (no entry prefetch in registers),
     // and both operands share the in-plane offsets, so one 32-bit offset per row is live while
     // the 16 loads are in flight: no spills at three blocks per SM.
-    const int l0 = tstart[tile], l1 = tstart[tile + 1];
+    const int2 lr = trange[blockIdx.x];               // the tile's list [l0, l1), in block order
+    const int l0 = lr.x, l1 = lr.y;
     for (int c0 = l0; c0 < l1; c0 += kListChunk) {
         const int cn = min(kListChunk, l1 - c0);
         __syncthreads();                              // the previous chunk is consumed
@@ -837,7 +838,9 @@ struct ptycho_ctx {
     // Error slot of batch iterations: allocated once at init and never replaced, so a captured
     // batch graph may keep its address while ptycho_iterate grows d_err.
     double *d_err_batch = nullptr;
-    int *d_tstart = nullptr, *d_torder = nullptr;
+    int *d_tstart = nullptr;
+    int *d_torder = nullptr;                              // per gather block: its tile (longest lists first)
+    int2 *d_trange = nullptr;                             // per gather block: its tile's list range
     int4 *d_tlist = nullptr;                              // tile lists: (j, y, x, 0)
     int ntx = 0, ntiles = 0;
     int *d_status = nullptr;
@@ -876,7 +879,7 @@ void free_ctx(ptycho_ctx *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
-                    h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder,
+                    h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder, h->d_trange,
                     h->d_tail_sync, h->d_tail_err,
                     h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
@@ -1259,13 +1262,13 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
     if (h->Q == 1)
-        k_object_gather<1><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
-                                                              h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max,
-                                                              h->M, h->N, h->ntx, 1);
+        k_object_gather<1><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tlist, h->d_torder,
+                                                              h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N,
+                                                              h->ntx, 1);
     else
-        k_object_gather<0><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tstart, h->d_tlist,
-                                                              h->d_torder, h->d_num_o, h->d_den_o, h->d_tile_max,
-                                                              h->M, h->N, h->ntx, h->Q);
+        k_object_gather<0><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tlist, h->d_torder,
+                                                              h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N,
+                                                              h->ntx, h->Q);
     PM_LAUNCHED("k_object_gather");
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
@@ -1444,6 +1447,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
     if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
     if (!rc) rc = dalloc(&h->d_torder, (size_t)h->ntiles);
+    if (!rc) rc = dalloc(&h->d_trange, (size_t)h->ntiles);
     if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_colour_list, (size_t)J);
     if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_epie_part, (size_t)max_colour_size * NN);
     if (!rc && h->exit_tma) rc = encode_exit_tma(h);
@@ -1460,8 +1464,12 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
         return fail_cuda(e, "copy positions");
     if ((e = cudaMemcpyAsync(h->d_tstart, tstart.data(), tstart.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile starts");
+    std::vector<int2> trange(h->ntiles);
+    for (int i = 0; i < h->ntiles; ++i) trange[i] = make_int2(tstart[torder[i]], tstart[torder[i] + 1]);
     if ((e = cudaMemcpyAsync(h->d_torder, torder.data(), torder.size() * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy tile order");
+    if ((e = cudaMemcpyAsync(h->d_trange, trange.data(), trange.size() * sizeof(int2), cudaMemcpyHostToDevice, h->st)))
+        return fail_cuda(e, "copy tile ranges");
     if (h->d_colour_list &&
         (e = cudaMemcpyAsync(h->d_colour_list, colour_list.data(), J * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy colour lists");
