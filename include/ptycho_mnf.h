@@ -224,11 +224,27 @@ int ptycho_get_probe(ptycho_handle h, void *dst, int dst_on_device);
 /* EPIE_COLOUR handles: the colour of every position (host [J]) and the number of colours. */
 int ptycho_get_colouring(ptycho_handle h, int32_t *h_colour, int *n_colours);
 
-/* Release every device resource of the handle (waits for its stream).  NULL is a no-op. */
+/* Release every device resource of the handle (waits for its stream; work of other streams
+ * on the handle's buffers, e.g. a batch, must be finished or destroyed first).  The buffers go
+ * back to the library's memory pool (see ptycho_release_memory).  NULL is a no-op. */
 void ptycho_destroy(ptycho_handle h);
 
+/*
+ * ptycho_release_memory -- the library's stream-ordered device allocations (reconstruction
+ * buffers of ptycho_init, scratch of fuse_stack / fuse_stack_host and of the warm-start
+ * stitching) come from one memory pool per device that keeps freed memory for the next
+ * allocation instead of returning it to the device, so that creating a reconstruction after
+ * destroying one, or fusing the next scan, maps no new pages.  This call hands the memory that
+ * no handle or call in flight holds back to the device (memory that live handles hold stays
+ * theirs and returns to the pool when they are destroyed).  The pools live as long as the
+ * process: the library is not usable across a cudaDeviceReset.  Returns PTYCHO_OK or
+ * PTYCHO_ECUDA.
+ */
+int ptycho_release_memory(void);
+
 /* Per-stage device timing with CUDA events on the handle's stream (for measurement only).
- * While enabled, ptycho_iterate records events around each stage and synchronises at its end.
+ * While enabled, ptycho_iterate records events at the stage boundaries (one event between two
+ * consecutive stages) and synchronises at its end.
  * Stages: 0 exit-wave kernel (patch, FFT, modulus, inverse FFT), 1 object update,
  * 2 probe update, 3 error reduction.  ms[s] is the summed device time of stage s and
  * launches[s] the number of kernel launches it made since timing was (re-)enabled. */

@@ -26,7 +26,7 @@ ALGORITHMS = {"ap": 0, "epie_colour": 1}
 DOMAINS = {"radiance": 0, "raw": 1}
 
 EXPORTS = ("fuse_stack", "fuse_stack_noalloc", "fuse_stack_host", "fuse_sli", "ptycho_init", "ptycho_iterate",
-           "ptycho_get_object", "ptycho_get_probe", "ptycho_get_colouring", "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_last_error")
+           "ptycho_get_object", "ptycho_get_probe", "ptycho_get_colouring", "ptycho_destroy", "ptycho_set_timing", "ptycho_stage_times", "ptycho_release_memory", "ptycho_last_error")
 
 
 class FuseParamsC(ctypes.Structure):
@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
     L.ptycho_debug_wait_timeout.restype = ci
     L.ptycho_debug_fail_alloc.argtypes = [ci]
     L.ptycho_debug_fail_alloc.restype = ci
+    L.ptycho_release_memory.argtypes = []
+    L.ptycho_release_memory.restype = ci
     L.measure_fp32_fma.argtypes = [ci, ci, vp, ctypes.POINTER(cd), vp]
     L.measure_fp32_fma.restype = ci
     L.measure_fma_threads_per_block.argtypes = []
@@ -364,6 +366,11 @@ def ptycho_debug_wait_timeout(h: PtychoHandle, enable) -> None:
     arrives on; 2 = in the split last round, the first CTA of each leftover position skips its
     first hand-off arrival, so its partners' bounded waits run out; 0 = off."""
     _check(lib().ptycho_debug_wait_timeout(h.ptr, int(enable)))
+
+
+def ptycho_release_memory() -> None:
+    """Hand the memory kept by the library's per-device pools back to the device."""
+    _check(lib().ptycho_release_memory())
 
 
 def ptycho_debug_fail_alloc(nth: int) -> None:

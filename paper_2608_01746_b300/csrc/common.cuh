@@ -14,8 +14,9 @@ int fail(int code, const char *fmt, ...);
 // Records a CUDA failure ("<what>: <cuda error string>") and returns PTYCHO_ECUDA, or
 // PTYCHO_ENOMEM for cudaErrorMemoryAllocation.
 int cuda_fail(cudaError_t e, const char *what);
-// Every device allocation of the library goes through these two (cudaMalloc / cudaMallocAsync),
-// so that ptycho_debug_fail_alloc can make the n-th one report cudaErrorMemoryAllocation.
+// Every device allocation of the library goes through these two (cudaMalloc; stream-ordered from
+// the library's per-device pool, which keeps freed memory for reuse), so that
+// ptycho_debug_fail_alloc can make the n-th one report cudaErrorMemoryAllocation.
 cudaError_t dev_malloc(void **p, size_t bytes);
 cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
 

@@ -861,6 +861,7 @@ struct ptycho_ctx {
     double stage_ms[ST_COUNT] = {};
     long long stage_launches[ST_COUNT] = {};
     std::vector<cudaEvent_t> ev;
+    size_t ev_last = SIZE_MAX;           // index of the last event recorded (shared stage bounds)
 };
 
 namespace {
@@ -874,6 +875,25 @@ int dalloc(T **p, size_t count) {
     return PTYCHO_OK;
 }
 
+// Buffers of a handle: stream-ordered on the handle's stream, from the library's pool (freed
+// memory is kept there for the next handle).  Another stream may use them once the handle's
+// stream has passed the allocation (ptycho_init and the re-allocations below synchronise it).
+template <typename T>
+int halloc(ptycho_ctx *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = pm::dev_malloc_async((void **)p, count * sizeof(T), h->st);
+    if (e != cudaSuccess) return pm::cuda_fail(e, "device allocation");
+    return PTYCHO_OK;
+}
+
+template <typename T>
+int hfree(ptycho_ctx *h, T **p) {
+    cudaError_t e = *p ? cudaFreeAsync(*p, h->st) : cudaSuccess;
+    *p = nullptr;
+    return e == cudaSuccess ? PTYCHO_OK : pm::cuda_fail(e, "cudaFreeAsync");
+}
+
 void free_ctx(ptycho_ctx *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
@@ -883,7 +903,7 @@ void free_ctx(ptycho_ctx *h) {
                     h->d_tail_sync, h->d_tail_err,
                     h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, h->st);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
 }
@@ -969,13 +989,11 @@ int encode_exit_tma(ptycho_ctx *h) {
 }
 
 int alloc_tail(ptycho_ctx *h) {
-    if (h->d_tail_sync) PM_CUDA(cudaFree(h->d_tail_sync));
-    if (h->d_tail_err) PM_CUDA(cudaFree(h->d_tail_err));
-    h->d_tail_sync = nullptr;
-    h->d_tail_err = nullptr;
+    int rc = hfree(h, &h->d_tail_sync);
+    if (!rc) rc = hfree(h, &h->d_tail_err);
     const int cap = std::max(1, h->grid_exit / 2);
-    int rc = dalloc(&h->d_tail_sync, (size_t)cap);
-    if (!rc) rc = dalloc(&h->d_tail_err, (size_t)cap * 16);
+    if (!rc) rc = halloc(h, &h->d_tail_sync, (size_t)cap);
+    if (!rc) rc = halloc(h, &h->d_tail_err, (size_t)cap * 16);
     return rc;
 }
 
@@ -1193,17 +1211,21 @@ int launch_exit_any(ptycho_ctx *h, int *launches) {
 const char *const kStageNames[ST_COUNT] = {"ptycho: exit waves", "ptycho: object update", "ptycho: probe update",
                                            "ptycho: error"};
 
-int stage_begin(ptycho_ctx *h, int s, size_t idx) {
+// Iteration i owns events [i (ST_COUNT + 1), (i + 1) (ST_COUNT + 1)): event s marks where stage
+// s begins and event s + 1 where it ends, so that consecutive stages share one event (each
+// recorded event costs the stream a short serialisation).
+int stage_begin(ptycho_ctx *h, int s, size_t base) {
     nvtxRangePushA(kStageNames[s]);
     if (!h->timing) return PTYCHO_OK;
-    PM_CUDA(cudaEventRecord(h->ev[2 * idx], h->st));
+    if (h->ev_last != base + s) PM_CUDA(cudaEventRecord(h->ev[base + s], h->st));
     return PTYCHO_OK;
 }
 
-int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
+int stage_end(ptycho_ctx *h, int s, size_t base, int launches) {
     nvtxRangePop();
     if (!h->timing) return PTYCHO_OK;
-    PM_CUDA(cudaEventRecord(h->ev[2 * idx + 1], h->st));
+    PM_CUDA(cudaEventRecord(h->ev[base + s + 1], h->st));
+    h->ev_last = base + s + 1;
     h->stage_launches[s] += launches;
     return PTYCHO_OK;
 }
@@ -1213,7 +1235,7 @@ int stage_end(ptycho_ctx *h, int s, size_t idx, int launches) {
 // step.  The whole colour loop is timed as stage 0.
 int iterate_one_epie(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_probe) {
     int rc;
-    if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
+    if ((rc = stage_begin(h, ST_EXIT, ev_base))) return rc;
     const size_t NN = (size_t)h->N * h->N;
     const int ncol = (int)h->colour_start.size() - 1;
     int launches = 0;
@@ -1236,15 +1258,15 @@ int iterate_one_epie(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update
             ++launches;
         }
     }
-    if ((rc = stage_end(h, ST_EXIT, ev_base + 0, launches))) return rc;
+    if ((rc = stage_end(h, ST_EXIT, ev_base, launches))) return rc;
     for (int st = ST_OBJECT; st <= ST_PROBE; ++st) {
-        if ((rc = stage_begin(h, st, ev_base + st))) return rc;
-        if ((rc = stage_end(h, st, ev_base + st, 0))) return rc;
+        if ((rc = stage_begin(h, st, ev_base))) return rc;
+        if ((rc = stage_end(h, st, ev_base, 0))) return rc;
     }
-    if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
+    if ((rc = stage_begin(h, ST_ERROR, ev_base))) return rc;
     k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, err_dst);
     PM_LAUNCHED("k_error_reduce");
-    return stage_end(h, ST_ERROR, ev_base + 3, 1);
+    return stage_end(h, ST_ERROR, ev_base, 1);
 }
 
 // err_dst: device slot of this iteration's Fourier error.  exit_done: the exit waves of this
@@ -1254,13 +1276,13 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     int rc;
     // exit waves
     if (!exit_done) {
-        if ((rc = stage_begin(h, ST_EXIT, ev_base + 0))) return rc;
+        if ((rc = stage_begin(h, ST_EXIT, ev_base))) return rc;
         int exit_launches = 1;
         if ((rc = launch_exit_any(h, &exit_launches))) return rc;
-        if ((rc = stage_end(h, ST_EXIT, ev_base + 0, exit_launches))) return rc;
+        if ((rc = stage_end(h, ST_EXIT, ev_base, exit_launches))) return rc;
     }
     // object
-    if ((rc = stage_begin(h, ST_OBJECT, ev_base + 1))) return rc;
+    if ((rc = stage_begin(h, ST_OBJECT, ev_base))) return rc;
     if (h->Q == 1)
         k_object_gather<1><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tlist, h->d_torder,
                                                               h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N,
@@ -1275,9 +1297,9 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     k_apply<<<gapply, kThreads, 0, h->st>>>(h->d_obj, h->d_num_o, h->d_den_o, h->d_tile_max, h->ntiles, MM,
                                             h->alpha_O);
     PM_LAUNCHED("k_apply(object)");
-    if ((rc = stage_end(h, ST_OBJECT, ev_base + 1, 2))) return rc;
+    if ((rc = stage_end(h, ST_OBJECT, ev_base, 2))) return rc;
     // probe
-    if ((rc = stage_begin(h, ST_PROBE, ev_base + 2))) return rc;
+    if ((rc = stage_begin(h, ST_PROBE, ev_base))) return rc;
     if (update_probe) {
         const int NN = h->N * h->N * h->Q;                // all probe modes
         if (h->Q == 1)
@@ -1295,12 +1317,12 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
                                             h->alpha_P);
         PM_LAUNCHED("k_apply(probe)");
     }
-    if ((rc = stage_end(h, ST_PROBE, ev_base + 2, update_probe ? 3 : 0))) return rc;
+    if ((rc = stage_end(h, ST_PROBE, ev_base, update_probe ? 3 : 0))) return rc;
     // error
-    if ((rc = stage_begin(h, ST_ERROR, ev_base + 3))) return rc;
+    if ((rc = stage_begin(h, ST_ERROR, ev_base))) return rc;
     k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, err_dst);
     PM_LAUNCHED("k_error_reduce");
-    if ((rc = stage_end(h, ST_ERROR, ev_base + 3, 1))) return rc;
+    if ((rc = stage_end(h, ST_ERROR, ev_base, 1))) return rc;
     return PTYCHO_OK;
 }
 
@@ -1423,33 +1445,33 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
 
     rc = setup_exit(h);
     if (!rc && h->fft_gemm) rc = pm::dft64_prepare(&h->gemm_sms);
-    if (!rc) rc = dalloc(&h->d_pos, J);
-    if (!rc) rc = dalloc(&h->d_obj, MM);
-    if (!rc) rc = dalloc(&h->d_probe, NN * Q);
-    if (!rc) rc = dalloc(&h->d_psi, (size_t)J * Q * NN);
-    if (!rc && h->exit_tma) rc = dalloc(&h->d_slot, (size_t)exit_slots(h->grid_exit) * NN);
+    if (!rc) rc = halloc(h, &h->d_pos, J);
+    if (!rc) rc = halloc(h, &h->d_obj, MM);
+    if (!rc) rc = halloc(h, &h->d_probe, NN * Q);
+    if (!rc) rc = halloc(h, &h->d_psi, (size_t)J * Q * NN);
+    if (!rc && h->exit_tma) rc = halloc(h, &h->d_slot, (size_t)exit_slots(h->grid_exit) * NN);
     if (!rc && h->exit_tma) rc = alloc_tail(h);
-    if (!rc) rc = dalloc(&h->d_status, 1);
-    if (!rc) rc = dalloc(&h->d_num_o, MM);
-    if (!rc) rc = dalloc(&h->d_den_o, MM);
-    if (!rc) rc = dalloc(&h->d_tile_max, h->ntiles);
-    if (!rc) rc = dalloc(&h->d_num_p, NN * Q);
-    if (!rc) rc = dalloc(&h->d_den_p, NN * Q);
-    if (!rc) rc = dalloc(&h->d_pnum, (size_t)h->nchunk * Q * NN);
-    if (!rc) rc = dalloc(&h->d_pden, (size_t)h->nchunk * Q * NN);
-    if (!rc) rc = dalloc(&h->d_pmax, h->nred);
-    if (!rc) rc = dalloc(&h->d_amp, (size_t)J * NN);
-    if (!rc && Q > 1) rc = dalloc(&h->d_amp_nat, (size_t)J * NN);
-    if (!rc) rc = dalloc(&h->d_err_pos, (size_t)J);
-    if (!rc) rc = dalloc(&h->d_a2, J);
-    if (!rc) rc = dalloc(&h->d_inv_norm, 1);
-    if (!rc) rc = dalloc(&h->d_err_batch, 1);
-    if (!rc) rc = dalloc(&h->d_tstart, h->ntiles + 1);
-    if (!rc) rc = dalloc(&h->d_tlist, tlist.size());
-    if (!rc) rc = dalloc(&h->d_torder, (size_t)h->ntiles);
-    if (!rc) rc = dalloc(&h->d_trange, (size_t)h->ntiles);
-    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_colour_list, (size_t)J);
-    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = dalloc(&h->d_epie_part, (size_t)max_colour_size * NN);
+    if (!rc) rc = halloc(h, &h->d_status, 1);
+    if (!rc) rc = halloc(h, &h->d_num_o, MM);
+    if (!rc) rc = halloc(h, &h->d_den_o, MM);
+    if (!rc) rc = halloc(h, &h->d_tile_max, h->ntiles);
+    if (!rc) rc = halloc(h, &h->d_num_p, NN * Q);
+    if (!rc) rc = halloc(h, &h->d_den_p, NN * Q);
+    if (!rc) rc = halloc(h, &h->d_pnum, (size_t)h->nchunk * Q * NN);
+    if (!rc) rc = halloc(h, &h->d_pden, (size_t)h->nchunk * Q * NN);
+    if (!rc) rc = halloc(h, &h->d_pmax, h->nred);
+    if (!rc) rc = halloc(h, &h->d_amp, (size_t)J * NN);
+    if (!rc && Q > 1) rc = halloc(h, &h->d_amp_nat, (size_t)J * NN);
+    if (!rc) rc = halloc(h, &h->d_err_pos, (size_t)J);
+    if (!rc) rc = halloc(h, &h->d_a2, J);
+    if (!rc) rc = halloc(h, &h->d_inv_norm, 1);
+    if (!rc) rc = halloc(h, &h->d_err_batch, 1);
+    if (!rc) rc = halloc(h, &h->d_tstart, h->ntiles + 1);
+    if (!rc) rc = halloc(h, &h->d_tlist, tlist.size());
+    if (!rc) rc = halloc(h, &h->d_torder, (size_t)h->ntiles);
+    if (!rc) rc = halloc(h, &h->d_trange, (size_t)h->ntiles);
+    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = halloc(h, &h->d_colour_list, (size_t)J);
+    if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = halloc(h, &h->d_epie_part, (size_t)max_colour_size * NN);
     if (!rc && h->exit_tma) rc = encode_exit_tma(h);
     if (rc) { free_ctx(h); return rc; }
     auto fail_cuda = [&](cudaError_t e, const char *what) {
@@ -1494,17 +1516,14 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
     if (n_iter < 0) return pm::fail(PTYCHO_EINVAL, "ptycho_iterate: n_iter = %d < 0", n_iter);
     if (n_iter == 0) return PTYCHO_OK;
     if (n_iter > h->err_cap) {
-        if (h->d_err) {
-            PM_CUDA(cudaStreamSynchronize(h->st));
-            PM_CUDA(cudaFree(h->d_err));
-            h->d_err = nullptr;
-        }
-        int rc = dalloc(&h->d_err, (size_t)n_iter);
+        int rc = hfree(h, &h->d_err);
+        if (!rc) rc = halloc(h, &h->d_err, (size_t)n_iter);
         if (rc) { h->err_cap = 0; return rc; }
         h->err_cap = n_iter;
     }
     if (h->timing) {
-        const size_t need = (size_t)n_iter * ST_COUNT * 2;
+        const size_t need = (size_t)n_iter * (ST_COUNT + 1);
+        h->ev_last = SIZE_MAX;
         while (h->ev.size() < need) {
             cudaEvent_t ev;
             PM_CUDA(cudaEventCreate(&ev));
@@ -1513,16 +1532,16 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
     }
     for (int i = 0; i < n_iter; ++i) {
         const bool upd = h->iter >= h->probe_update_start;
-        int rc = iterate_one(h, h->d_err + i, (size_t)i * ST_COUNT, upd);
+        int rc = iterate_one(h, h->d_err + i, (size_t)i * (ST_COUNT + 1), upd);
         if (rc) return rc;
         ++h->iter;
     }
     if (h->timing) {
-        PM_CUDA(cudaEventSynchronize(h->ev[(size_t)n_iter * ST_COUNT * 2 - 1]));
+        PM_CUDA(cudaEventSynchronize(h->ev[(size_t)n_iter * (ST_COUNT + 1) - 1]));
         for (int i = 0; i < n_iter; ++i)
             for (int s = 0; s < ST_COUNT; ++s) {
                 float ms = 0.f;
-                const size_t b = ((size_t)i * ST_COUNT + s) * 2;
+                const size_t b = (size_t)i * (ST_COUNT + 1) + s;
                 PM_CUDA(cudaEventElapsedTime(&ms, h->ev[b], h->ev[b + 1]));
                 h->stage_ms[s] += ms;
             }
@@ -1764,11 +1783,11 @@ int retune_tma(ptycho_ctx *h, int B) {
     const int grid = std::max(1, std::min(h->J, sms * per_sm));
     if (grid != h->grid_exit) {
         PM_CUDA(cudaStreamSynchronize(h->st));
-        if (h->d_slot) PM_CUDA(cudaFree(h->d_slot));
-        h->d_slot = nullptr;
+        if ((rc = hfree(h, &h->d_slot))) return rc;
         h->grid_exit = grid;
-        if ((rc = dalloc(&h->d_slot, (size_t)exit_slots(grid) * h->N * h->N))) return rc;
+        if ((rc = halloc(h, &h->d_slot, (size_t)exit_slots(grid) * h->N * h->N))) return rc;
         if ((rc = alloc_tail(h))) return rc;
+        PM_CUDA(cudaStreamSynchronize(h->st));         // the batch's streams use the new buffers
     }
     return encode_exit_tma(h);
 }
