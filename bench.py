@@ -371,7 +371,7 @@ def run_batched(args, world, rank, local):
                          "frac": round(flops / fma["tflops"], 4)}}
     by_n = {n: sum(1 for c in cfgs if c.N == n) for n in sorted({c.N for c in cfgs})}
     launches_per_iter = (len(by_n) - 1 + sum(1 for c in cfgs if c.N == 256)  # class launches + N=256 exits
-                         + 2 * len(cfgs) + 3 * len(cfgs) + len(cfgs))   # object (2), probe (3), error (1)
+                         + 2 * len(cfgs) + 3 * len(cfgs))   # object (2, the error inside), probe (3)
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
@@ -619,7 +619,8 @@ def run_ours(args, world, rank, local):
     hbm_peak, peak_kind = peaks()
     dom = int(np.argmax(stage_ms))
     names = ["k_exit_wave", "object update (k_object_gather + k_apply)",
-             "probe update (k_probe_partial + k_probe_reduce + k_apply)", "k_error_reduce"]
+             "probe update (k_probe_partial + k_probe_reduce + k_apply)",
+             "error (formed in block 0 of the object step's k_apply; empty stage)"]
     Q = cfg.modes
     # the exit-wave stage per iteration: one launch over all J positions, or (N = 256, split last
     # round) the whole-round launch plus the cooperative tail launch; with modes the forward,

@@ -18,8 +18,10 @@
 //   k_probe_partial / k_probe_reduce / k_apply
 //                  P = sum_j conj(O_j) psi_j' / (sum_j |O_j|^2 + alpha_P max), with the new
 //                  object, as fixed-order partial sums over position chunks.
-//   k_error_reduce   per-iteration Fourier error in FP64, fixed order.
+//   k_error_reduce   per-iteration Fourier error in FP64, fixed order (ePIE by colour; the
+//                    alternating projections form it in block 0 of the object step's k_apply).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -500,6 +502,34 @@ __device__ __forceinline__ void combine_warps(const float2 (&acc)[kTR], const fl
     }
 }
 
+// Position lists of the object tiles: tile t's list holds (j, y, x, 0) for every position j
+// whose N x N patch touches the tile, in ascending j, at tlist[tstart[t] ..).  One warp per
+// tile walks the positions 32 at a time and packs the hits in order (ballot + prefix count).
+// The host sized each list with the same test; an entry past the list's end is dropped.
+__global__ void __launch_bounds__(kThreads) k_tile_lists(const int2 *__restrict__ pos, int J, int N, int ntx,
+                                                         int ntiles, const int *__restrict__ tstart,
+                                                         int4 *__restrict__ tlist) {
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;                                   // whole warps
+    const int ty = t / ntx, tx = t % ntx;
+    const int base = tstart[t], cap = tstart[t + 1] - base;
+    int k = 0;
+    for (int j0 = 0; j0 < J; j0 += 32) {
+        const int j = j0 + lane;
+        int2 p = make_int2(0, 0);
+        bool hit = false;
+        if (j < J) {
+            p = pos[j];
+            hit = p.x / kTR <= ty && ty <= (p.x + N - 1) / kTR && p.y / kTW <= tx && tx <= (p.y + N - 1) / kTW;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const int slot = k + __popc(m & ((1u << lane) - 1u));
+        if (hit && slot < cap) tlist[base + slot] = make_int4(j, p.x, p.y, 0);
+        k += __popc(m);
+    }
+}
+
 // Owner-computes object numerator and denominator, one kTR x 32 object tile per block.
 // Warp w takes every 8th position of the tile's (ascending) list; lane = tile column, and
 // each lane keeps its column's kTR pixels in registers.
@@ -652,11 +682,31 @@ __device__ float block_max(const float *v, int n) {
     return r;
 }
 
+// Fourier error of an iteration: sum_j err[j] * inv_norm, by one block of kThreads threads
+// (thread t sums err[t], err[t + kThreads], ...; then a fixed tree over the threads).
+__device__ void error_sum_block(const double *__restrict__ err, int J, const double *__restrict__ inv_norm,
+                                double *__restrict__ out) {
+    __shared__ double s[kThreads];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < J; i += kThreads) a += err[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0] * inv_norm[0];
+}
+
 // x = num / (den + alpha max den) where den >= 0 (the pixel lies in some patch; -1 marks
 // pixels outside every patch) and den + alpha max den > 0; elsewhere x keeps its value.
+// With err_out, block 0 also forms the iteration's Fourier error from the per-position errors
+// of the exit waves (which precede this kernel on the stream), saving a launch of its own.
 __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, const float2 *__restrict__ num,
                                                     const float *__restrict__ den, const float *__restrict__ partial_max,
-                                                    int nmax, size_t n, float alpha) {
+                                                    int nmax, size_t n, float alpha, const double *__restrict__ err,
+                                                    int J, const double *__restrict__ inv_norm,
+                                                    double *__restrict__ err_out) {
     const float reg = alpha * block_max(partial_max, nmax);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float d = den[i];
@@ -665,6 +715,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
             x[i] = cscale(num[i], s);
         }
     }
+    if (err_out && blockIdx.x == 0) error_sum_block(err, J, inv_norm, err_out);
 }
 
 // Probe partial sums: block (kTR x 32 probe tile, chunk of positions) -> partial[chunk][q].
@@ -753,18 +804,10 @@ __global__ void __launch_bounds__(kThreads) k_probe_reduce(const float2 *__restr
 }
 
 // Per-iteration error: sum_j err[j] (fixed order) * inv_norm.
-__global__ void k_error_reduce(const double *__restrict__ err, int J, const double *__restrict__ inv_norm,
-                               double *__restrict__ out) {
-    __shared__ double s[kThreads];
-    double a = 0.0;
-    for (int i = threadIdx.x; i < J; i += blockDim.x) a += err[i];
-    s[threadIdx.x] = a;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = s[0] * inv_norm[0];
+__global__ void __launch_bounds__(kThreads) k_error_reduce(const double *__restrict__ err, int J,
+                                                           const double *__restrict__ inv_norm,
+                                                           double *__restrict__ out) {
+    error_sum_block(err, J, inv_norm, out);
 }
 
 // A = sqrt(max(I, 0)) with DC moved from the centre to index 0, stored per position column by
@@ -1295,7 +1338,7 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
     k_apply<<<gapply, kThreads, 0, h->st>>>(h->d_obj, h->d_num_o, h->d_den_o, h->d_tile_max, h->ntiles, MM,
-                                            h->alpha_O);
+                                            h->alpha_O, h->d_err_pos, h->J, h->d_inv_norm, err_dst);
     PM_LAUNCHED("k_apply(object)");
     if ((rc = stage_end(h, ST_OBJECT, ev_base, 2))) return rc;
     // probe
@@ -1314,15 +1357,14 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
         PM_LAUNCHED("k_probe_reduce");
         const unsigned gp = (unsigned)std::min<int>((NN + kThreads - 1) / kThreads, 148 * 4);
         k_apply<<<gp, kThreads, 0, h->st>>>(h->d_probe, h->d_num_p, h->d_den_p, h->d_pmax, h->nred, (size_t)NN,
-                                            h->alpha_P);
+                                            h->alpha_P, nullptr, 0, nullptr, nullptr);
         PM_LAUNCHED("k_apply(probe)");
     }
     if ((rc = stage_end(h, ST_PROBE, ev_base, update_probe ? 3 : 0))) return rc;
-    // error
+    // error: formed by block 0 of the object step's k_apply (an empty stage, so that every
+    // iteration has the same stage boundaries)
     if ((rc = stage_begin(h, ST_ERROR, ev_base))) return rc;
-    k_error_reduce<<<1, kThreads, 0, h->st>>>(h->d_err_pos, h->J, h->d_inv_norm, err_dst);
-    PM_LAUNCHED("k_error_reduce");
-    if ((rc = stage_end(h, ST_ERROR, ev_base, 1))) return rc;
+    if ((rc = stage_end(h, ST_ERROR, ev_base, 0))) return rc;
     return PTYCHO_OK;
 }
 
@@ -1418,24 +1460,40 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     h->ntx = (M + kTW - 1) / kTW;
     const int nty = (M + kTR - 1) / kTR;
     h->ntiles = h->ntx * nty;
-    std::vector<int> tstart(h->ntiles + 1, 0), torder;
-    std::vector<int4> tlist;
+    // list lengths on the host (each patch adds one to a rectangle of tiles: a 2-D difference
+    // array and its prefix sums), the lists themselves on the device (k_tile_lists)
+    std::vector<int> tstart(h->ntiles + 1, 0), torder(h->ntiles);
+    std::vector<long long> count(h->ntiles, 0);
     {
-        std::vector<std::vector<int>> lists(h->ntiles);
+        const int ntx = h->ntx;
+        std::vector<long long> diff((size_t)(nty + 1) * (ntx + 1), 0);
         for (int j = 0; j < J; ++j) {
             const int y = d->h_pos[2 * j], x = d->h_pos[2 * j + 1];
             const int ty0 = y / kTR, ty1 = (y + N - 1) / kTR, tx0 = x / kTW, tx1 = (x + N - 1) / kTW;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) lists[ty * h->ntx + tx].push_back(j);
+            diff[(size_t)ty0 * (ntx + 1) + tx0] += 1;
+            diff[(size_t)ty0 * (ntx + 1) + tx1 + 1] -= 1;
+            diff[(size_t)(ty1 + 1) * (ntx + 1) + tx0] -= 1;
+            diff[(size_t)(ty1 + 1) * (ntx + 1) + tx1 + 1] += 1;
         }
-        for (int t = 0; t < h->ntiles; ++t) tstart[t + 1] = tstart[t] + (int)lists[t].size();
-        tlist.reserve(tstart[h->ntiles]);
-        for (int t = 0; t < h->ntiles; ++t)
-            for (int j : lists[t]) tlist.push_back(make_int4(j, d->h_pos[2 * j], d->h_pos[2 * j + 1], 0));
-        torder.resize(h->ntiles);
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                long long c = diff[(size_t)ty * (ntx + 1) + tx];
+                if (ty > 0) c += count[(size_t)(ty - 1) * ntx + tx];
+                if (tx > 0) c += count[(size_t)ty * ntx + tx - 1];
+                if (ty > 0 && tx > 0) c -= count[(size_t)(ty - 1) * ntx + tx - 1];
+                count[(size_t)ty * ntx + tx] = c;
+            }
+        long long total = 0;
+        for (int t = 0; t < h->ntiles; ++t) {
+            total += count[t];
+            if (total > INT_MAX) {
+                delete h;
+                return pm::fail(PTYCHO_EINVAL, "ptycho_init: more than 2^31 tile-list entries");
+            }
+            tstart[t + 1] = (int)total;
+        }
         for (int t = 0; t < h->ntiles; ++t) torder[t] = t;
-        std::stable_sort(torder.begin(), torder.end(),
-                         [&](int a, int b) { return lists[a].size() > lists[b].size(); });
+        std::stable_sort(torder.begin(), torder.end(), [&](int a, int b) { return count[a] > count[b]; });
     }
     // probe partial-sum layout
     h->nqt = ((N + kTW - 1) / kTW) * ((N + kTR - 1) / kTR);
@@ -1467,7 +1525,7 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = halloc(h, &h->d_inv_norm, 1);
     if (!rc) rc = halloc(h, &h->d_err_batch, 1);
     if (!rc) rc = halloc(h, &h->d_tstart, h->ntiles + 1);
-    if (!rc) rc = halloc(h, &h->d_tlist, tlist.size());
+    if (!rc) rc = halloc(h, &h->d_tlist, (size_t)tstart[h->ntiles]);
     if (!rc) rc = halloc(h, &h->d_torder, (size_t)h->ntiles);
     if (!rc) rc = halloc(h, &h->d_trange, (size_t)h->ntiles);
     if (!rc && h->algorithm == PTYCHO_ALG_EPIE_COLOUR) rc = halloc(h, &h->d_colour_list, (size_t)J);
@@ -1495,9 +1553,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (h->d_colour_list &&
         (e = cudaMemcpyAsync(h->d_colour_list, colour_list.data(), J * sizeof(int), cudaMemcpyHostToDevice, h->st)))
         return fail_cuda(e, "copy colour lists");
-    if (!tlist.empty() &&
-        (e = cudaMemcpyAsync(h->d_tlist, tlist.data(), tlist.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st)))
-        return fail_cuda(e, "copy tile lists");
+    k_tile_lists<<<(unsigned)(((size_t)h->ntiles * 32 + kThreads - 1) / kThreads), kThreads, 0, h->st>>>(
+        h->d_pos, J, N, h->ntx, h->ntiles, h->d_tstart, h->d_tlist);
+    if ((e = cudaGetLastError())) return fail_cuda(e, "k_tile_lists");
     if ((rc = copy_in_complex(h->d_obj, d->obj0, MM, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
     if ((rc = copy_in_complex(h->d_probe, d->probe0, NN * Q, d->init_on_device != 0, h->st))) { free_ctx(h); return rc; }
     if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st))) return fail_cuda(e, "clear status");

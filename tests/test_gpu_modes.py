@@ -113,5 +113,6 @@ def test_mixed_state_stage_launches(api):
     api.ptycho_set_timing(h, True)
     api.ptycho_iterate(h, 2)
     _, launches = api.ptycho_stage_times(h)
-    assert launches == [6, 4, 6, 2]          # forward, modulus, inverse per iteration
+    assert launches == [6, 4, 6, 0]          # forward, modulus, inverse per iteration; the error
+                                             # is formed inside the object step's k_apply
     api.ptycho_destroy(h)

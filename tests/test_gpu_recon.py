@@ -210,8 +210,9 @@ def test_stage_timing(api):
     api.ptycho_set_timing(h, True)
     api.ptycho_iterate(h, 3)
     ms, launches = api.ptycho_stage_times(h)
-    assert launches == [3, 6, 9, 3]
-    assert all(m > 0 for m in ms)
+    # the error is formed inside the object step's k_apply: the error stage launches nothing
+    assert launches == [3, 6, 9, 0]
+    assert all(m > 0 for m in ms[:3]) and ms[3] >= 0
     api.ptycho_destroy(h)
 
 
