@@ -246,7 +246,8 @@ int ptycho_release_memory(void);
  * While enabled, ptycho_iterate records events at the stage boundaries (one event between two
  * consecutive stages) and synchronises at its end.
  * Stages: 0 exit-wave kernel (patch, FFT, modulus, inverse FFT), 1 object update,
- * 2 probe update, 3 error reduction.  ms[s] is the summed device time of stage s and
+ * 2 probe update, 3 error reduction (ePIE by colour only: the alternating projections form the
+ * error inside stage 1).  ms[s] is the summed device time of stage s and
  * launches[s] the number of kernel launches it made since timing was (re-)enabled. */
 int ptycho_set_timing(ptycho_handle h, int enable);
 int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches /*[4]*/);

@@ -904,7 +904,12 @@ struct ptycho_ctx {
     double stage_ms[ST_COUNT] = {};
     long long stage_launches[ST_COUNT] = {};
     std::vector<cudaEvent_t> ev;
-    size_t ev_last = SIZE_MAX;           // index of the last event recorded (shared stage bounds)
+    // stage events of the current ptycho_iterate call: stage s of iteration i ran between events
+    // mark[2 (i ST_COUNT + s)] and mark[... + 1] (-1: not run); ev_used events are recorded,
+    // the last of them with no launch after it while ev_fresh (the next stage starts there)
+    std::vector<int> mark;
+    size_t ev_used = 0;
+    bool ev_fresh = false;
 };
 
 namespace {
@@ -1254,21 +1259,29 @@ int launch_exit_any(ptycho_ctx *h, int *launches) {
 const char *const kStageNames[ST_COUNT] = {"ptycho: exit waves", "ptycho: object update", "ptycho: probe update",
                                            "ptycho: error"};
 
-// Iteration i owns events [i (ST_COUNT + 1), (i + 1) (ST_COUNT + 1)): event s marks where stage
-// s begins and event s + 1 where it ends, so that consecutive stages share one event (each
-// recorded event costs the stream a short serialisation).
+// Stage s of the iteration whose marks start at `base` (= i ST_COUNT): a stage that follows
+// another with no launch in between starts at that stage's end event, so the timed stages of a
+// call cost one recorded event each plus one (each recorded event costs the stream a short
+// serialisation).
 int stage_begin(ptycho_ctx *h, int s, size_t base) {
     nvtxRangePushA(kStageNames[s]);
     if (!h->timing) return PTYCHO_OK;
-    if (h->ev_last != base + s) PM_CUDA(cudaEventRecord(h->ev[base + s], h->st));
+    if (!h->ev_fresh) {
+        if (h->ev_used >= h->ev.size()) return pm::fail(PTYCHO_ECUDA, "stage timing: out of events");
+        PM_CUDA(cudaEventRecord(h->ev[h->ev_used++], h->st));
+    }
+    h->mark[2 * (base + s)] = (int)h->ev_used - 1;
+    h->ev_fresh = false;
     return PTYCHO_OK;
 }
 
 int stage_end(ptycho_ctx *h, int s, size_t base, int launches) {
     nvtxRangePop();
     if (!h->timing) return PTYCHO_OK;
-    PM_CUDA(cudaEventRecord(h->ev[base + s + 1], h->st));
-    h->ev_last = base + s + 1;
+    if (h->ev_used >= h->ev.size()) return pm::fail(PTYCHO_ECUDA, "stage timing: out of events");
+    PM_CUDA(cudaEventRecord(h->ev[h->ev_used], h->st));
+    h->mark[2 * (base + s) + 1] = (int)h->ev_used++;
+    h->ev_fresh = true;
     h->stage_launches[s] += launches;
     return PTYCHO_OK;
 }
@@ -1361,10 +1374,7 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
         PM_LAUNCHED("k_apply(probe)");
     }
     if ((rc = stage_end(h, ST_PROBE, ev_base, update_probe ? 3 : 0))) return rc;
-    // error: formed by block 0 of the object step's k_apply (an empty stage, so that every
-    // iteration has the same stage boundaries)
-    if ((rc = stage_begin(h, ST_ERROR, ev_base))) return rc;
-    if ((rc = stage_end(h, ST_ERROR, ev_base, 0))) return rc;
+    // the error is formed by block 0 of the object step's k_apply: no stage of its own
     return PTYCHO_OK;
 }
 
@@ -1580,29 +1590,30 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
         h->err_cap = n_iter;
     }
     if (h->timing) {
-        const size_t need = (size_t)n_iter * (ST_COUNT + 1);
-        h->ev_last = SIZE_MAX;
+        const size_t need = (size_t)n_iter * ST_COUNT + 1;      // at most one per stage, plus one
         while (h->ev.size() < need) {
             cudaEvent_t ev;
             PM_CUDA(cudaEventCreate(&ev));
             h->ev.push_back(ev);
         }
+        h->mark.assign((size_t)n_iter * ST_COUNT * 2, -1);
+        h->ev_used = 0;
+        h->ev_fresh = false;
     }
     for (int i = 0; i < n_iter; ++i) {
         const bool upd = h->iter >= h->probe_update_start;
-        int rc = iterate_one(h, h->d_err + i, (size_t)i * (ST_COUNT + 1), upd);
+        int rc = iterate_one(h, h->d_err + i, (size_t)i * ST_COUNT, upd);
         if (rc) return rc;
         ++h->iter;
     }
-    if (h->timing) {
-        PM_CUDA(cudaEventSynchronize(h->ev[(size_t)n_iter * (ST_COUNT + 1) - 1]));
-        for (int i = 0; i < n_iter; ++i)
-            for (int s = 0; s < ST_COUNT; ++s) {
-                float ms = 0.f;
-                const size_t b = (size_t)i * (ST_COUNT + 1) + s;
-                PM_CUDA(cudaEventElapsedTime(&ms, h->ev[b], h->ev[b + 1]));
-                h->stage_ms[s] += ms;
-            }
+    if (h->timing && h->ev_used > 0) {
+        PM_CUDA(cudaEventSynchronize(h->ev[h->ev_used - 1]));
+        for (size_t m = 0; m < (size_t)n_iter * ST_COUNT; ++m) {
+            if (h->mark[2 * m] < 0) continue;
+            float ms = 0.f;
+            PM_CUDA(cudaEventElapsedTime(&ms, h->ev[h->mark[2 * m]], h->ev[h->mark[2 * m + 1]]));
+            h->stage_ms[m % ST_COUNT] += ms;
+        }
     }
     if (h_err) {
         int status = 0;
