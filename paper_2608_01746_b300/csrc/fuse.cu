@@ -29,9 +29,10 @@ constexpr int kMaxK = 8;
 constexpr int kMaxLevels = 11;
 
 struct FuseDev {
-    float mu, inv2s2, clip;
+    float mu, inv2s2, clip, inv_clip;
     float tscale[kMaxK];        // E_k = I_k * tscale[k]
     float delta[kMaxLevels];    // quantiser step per level (0 = off)
+    float inv_delta[kMaxLevels];
     int N, L, base_mode;
 };
 
@@ -50,17 +51,20 @@ __device__ __forceinline__ float wg(int a) {
 template <int K>
 __device__ __forceinline__ void level0_counts(const uint16_t (&c)[K], const FuseDev &f, float (&E)[K],
                                               float (&W)[K]) {
+    // FP32 with reciprocal multiplications in place of the divisions by the clip level and by
+    // the weight sum (each adds at most one rounding to a value the FP64 oracle forms exactly)
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const float v = (float)c[k];
         E[k] = v * f.tscale[k];
-        const float d = fminf(v, f.clip) / f.clip - f.mu;
+        const float d = fminf(v, f.clip) * f.inv_clip - f.mu;
         W[k] = expf(-d * d * f.inv2s2);
         s += W[k];
     }
+    const float inv_s = (s > 0.f) ? 1.0f / s : 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) W[k] = (s > 0.f) ? W[k] / s : 1.0f / K;
+    for (int k = 0; k < K; ++k) W[k] = (s > 0.f) ? W[k] * inv_s : 1.0f / K;
 }
 
 template <int K>
@@ -72,8 +76,9 @@ __device__ __forceinline__ void level0_pixel(const uint16_t *raw_j, size_t NN, s
     level0_counts<K>(c, f, E, W);
 }
 
-__device__ __forceinline__ float quantise(float x, float delta) {
-    return delta > 0.f ? delta * rintf(x / delta) : x;
+// Delta rint(x / Delta), the ratio formed with the reciprocal of Delta (0 = no quantiser).
+__device__ __forceinline__ float quantise(float x, float delta, float inv_delta) {
+    return delta > 0.f ? delta * rintf(x * inv_delta) : x;
 }
 
 constexpr int kTile = 16;             // outputs per block side of a reduce
@@ -274,9 +279,15 @@ __global__ void k_base(const float *__restrict__ ge, const float *__restrict__ g
 // R_l = U2(R_{l+1}) + sum_k Q_l(G_l[W_k] (G_l[E_k] - U2(G_{l+1}[E_k]))); level 0 reads raw.
 // One block per 32 x 32 output tile of one position: the 18 x 18 coarse neighbourhoods of
 // R_{l+1} and G_{l+1}[E_k] are staged in shared memory with U2's border extension (coarse
-// index -1 -> 1, n -> n - 1) applied while loading.
+// index -1 -> 1, n -> n - 1) applied while loading.  One thread per 2 x 2 output quad: output
+// 2i takes coarse i - 1, i, i + 1 with weights (1/8, 3/4, 1/8) and 2i + 1 takes i, i + 1 with
+// (1/2, 1/2) (written as three taps with a zero lead), so the quad's four pixels share one
+// 3 x 3 coarse neighbourhood per plane: each coarse row is filtered along x once per column
+// parity, then along y once per pixel, in the same order and with the same FMAs as a
+// pixel-by-pixel evaluation.
 constexpr int kCT = 32;                 // output tile side of the collapse
 constexpr int kCC = kCT / 2 + 2;        // coarse rows / columns the tile needs
+constexpr int kCP = 48;                 // row pitch: the two quad rows of a warp hit distinct banks
 
 __device__ __forceinline__ int coarse_ext(int i, int n) { return i < 0 ? 1 : min(i, n - 1); }
 
@@ -284,8 +295,8 @@ template <int K>
 __global__ void __launch_bounds__(256) k_collapse(const float *__restrict__ ge, const float *__restrict__ gw,
                                                   const uint16_t *__restrict__ raw, const float *__restrict__ ge_next,
                                                   const float *__restrict__ r_next, float *__restrict__ out, int n,
-                                                  float delta, FuseDev f) {
-    __shared__ float s_c[K + 1][kCC][kCC + 1];          // [0..K-1] G_{l+1}[E_k], [K] R_{l+1}
+                                                  float delta, float inv_delta, FuseDev f) {
+    __shared__ float s_c[K + 1][kCC][kCP];              // [0..K-1] G_{l+1}[E_k], [K] R_{l+1}
     const int m = n >> 1;
     const size_t nn = (size_t)n * n, mm = (size_t)m * m;
     const int j = blockIdx.z;
@@ -297,43 +308,62 @@ __global__ void __launch_bounds__(256) k_collapse(const float *__restrict__ ge, 
         s_c[pl][a][b] = (pl < K) ? __ldg(ge_next + ((size_t)j * K + pl) * mm + src) : __ldg(r_next + (size_t)j * mm + src);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kCT * kCT; e += blockDim.x) {
-        const int py = oy0 + e / kCT, px = ox0 + e % kCT;
-        if (py >= n || px >= n) continue;
-        // U2 taps: even m = 2i -> (1/8, 6/8, 1/8) at i-1, i, i+1; odd m = 2i+1 -> (1/2, 1/2) at i, i+1
-        // Three taps at i - 1, i, i + 1 on both parities: the odd case's leading tap has weight
-        // 0, which leaves every partial sum as the two-tap sum would have it.
-        const int y0 = (py >> 1) - cy0 - 1, x0 = (px >> 1) - cx0 - 1;
-        const float wy0 = (py & 1) ? 0.f : 0.125f, wy1 = (py & 1) ? 0.5f : 0.75f, wy2 = (py & 1) ? 0.5f : 0.125f;
-        const float wx0 = (px & 1) ? 0.f : 0.125f, wx1 = (px & 1) ? 0.5f : 0.75f, wx2 = (px & 1) ? 0.5f : 0.125f;
-        auto up = [&](int pl) {
-            const float wy[3] = {wy0, wy1, wy2}, wx[3] = {wx0, wx1, wx2};
-            float acc = 0.f;
+    const int qy = threadIdx.x / (kCT / 2), qx = threadIdx.x % (kCT / 2);
+    const int py0 = oy0 + 2 * qy, px0 = ox0 + 2 * qx;
+    if (py0 >= n || px0 >= n) return;
+    // coarse neighbourhood of the quad: rows / columns qy .. qy + 2, qx .. qx + 2 of the stage
+    // (output 2i has i - 1 at stage index i - cy0 - 1 = qy)
+    constexpr float we[3] = {0.125f, 0.75f, 0.125f}, wo[3] = {0.f, 0.5f, 0.5f};
+    float up[K + 1][2][2];                              // [plane][dy][dx]
+#pragma unroll
+    for (int pl = 0; pl <= K; ++pl) {
+        float rx[3][2];                                 // coarse row a filtered along x, column parity
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float *row = &s_c[pl][qy + a][qx];
+            float re = 0.f, ro = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                re += we[b] * row[b];
+                ro += wo[b] * row[b];
+            }
+            rx[a][0] = re;
+            rx[a][1] = ro;
+        }
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            float ae = 0.f, ao = 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float r = 0.f;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) r += wx[b] * s_c[pl][y0 + a][x0 + b];
-                acc += wy[a] * r;
+                ae += we[a] * rx[a][dx];
+                ao += wo[a] * rx[a][dx];
             }
-            return acc;
-        };
-        const size_t p = (size_t)py * n + px;
-        float E[K], W[K];
-        if (raw) {
-            level0_pixel<K>(raw + (size_t)j * K * nn, nn, p, f, E, W);
-        } else {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                E[k] = __ldg(ge + ((size_t)j * K + k) * nn + p);
-                W[k] = __ldg(gw + ((size_t)j * K + k) * nn + p);
-            }
+            up[pl][0][dx] = ae;
+            up[pl][1][dx] = ao;
         }
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc += quantise(W[k] * (E[k] - up(k)), delta);
-        out[(size_t)j * nn + p] = up(K) + acc;
     }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const int py = py0 + dy, px = px0 + dx;
+            if (py >= n || px >= n) continue;
+            const size_t p = (size_t)py * n + px;
+            float E[K], W[K];
+            if (raw) {
+                level0_pixel<K>(raw + (size_t)j * K * nn, nn, p, f, E, W);
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    E[k] = __ldg(ge + ((size_t)j * K + k) * nn + p);
+                    W[k] = __ldg(gw + ((size_t)j * K + k) * nn + p);
+                }
+            }
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc += quantise(W[k] * (E[k] - up[k][dy][dx]), delta, inv_delta);
+            out[(size_t)j * nn + p] = up[K][dy][dx] + acc;
+        }
 }
 
 unsigned grid_for(size_t total, int threads) {
@@ -384,9 +414,11 @@ int run_fuse(const uint16_t *d_raw, int J, int N, const FuseDev &f, float *d_fus
         const int n = N >> l;
         dim3 grid((n + kCT - 1) / kCT, (n + kCT - 1) / kCT, J);
         if (l == 0) {
-            k_collapse<K><<<grid, 256, 0, st>>>(nullptr, nullptr, d_raw, ge[1], rr[1], d_fused, n, f.delta[0], f);
+            k_collapse<K><<<grid, 256, 0, st>>>(nullptr, nullptr, d_raw, ge[1], rr[1], d_fused, n, f.delta[0],
+                                                f.inv_delta[0], f);
         } else {
-            k_collapse<K><<<grid, 256, 0, st>>>(ge[l], gw[l], nullptr, ge[l + 1], rr[l + 1], rr[l], n, f.delta[l], f);
+            k_collapse<K><<<grid, 256, 0, st>>>(ge[l], gw[l], nullptr, ge[l + 1], rr[l + 1], rr[l], n, f.delta[l],
+                                                f.inv_delta[l], f);
         }
         PM_LAUNCHED("k_collapse");
     }
@@ -435,10 +467,12 @@ int validate_fuse(const uint16_t *d_raw, int J, int K, int N, const float *h_t,
     f.mu = p->mu;
     f.inv2s2 = (float)(1.0 / (2.0 * (double)p->sigma * (double)p->sigma));
     f.clip = p->clip;
+    f.inv_clip = (float)(1.0 / (double)p->clip);
     for (int k = 0; k < K; ++k)
         f.tscale[k] = (p->domain == PTYCHO_DOMAIN_RAW) ? 1.0f : (float)((double)tmax / (double)h_t[k]);
     for (int l = 0; l < kMaxLevels; ++l)
         f.delta[l] = (float)((double)p->delta0 * std::pow((double)p->delta_ratio, (double)l));
+    for (int l = 0; l < kMaxLevels; ++l) f.inv_delta[l] = f.delta[l] > 0.f ? (float)(1.0 / (double)f.delta[l]) : 0.f;
     f.N = N;
     f.L = p->levels;
     f.base_mode = p->base_mode;
