@@ -316,14 +316,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dft64_gemm(Args a) {
                 const float *amp = c.amp + (size_t)(j0 + p) * kN * kN + (size_t)half * kN;
                 for_pairs(lane_addr, p, part, [&](int c, float2 z0, float2 z1) {
                     const float2 A2 = __ldg(reinterpret_cast<const float2 *>(amp + c));
-                    float2 z[2] = {cscale(z0, invN), cscale(z1, invN)};
+                    // z = N Psi (the forward pass unscaled); A Psi / |Psi| = A z / |z|
+                    float2 z[2] = {z0, z1};
                     const float A[2] = {A2.x, A2.y};
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
-                        const float mag = sqrtf(cabs2(z[q]));
-                        const float dm = mag - A[q];
-                        ep += dm * dm;
-                        z[q] = mag > 0.f ? cscale(z[q], A[q] / mag) : make_float2(A[q], 0.f);
+                        const float mag2 = cabs2(z[q]);
+                        if (mag2 > 0.f) {
+                            const float inv = rsqrtf(mag2);
+                            const float dm = mag2 * inv * invN - A[q];
+                            ep += dm * dm;
+                            z[q] = cscale(z[q], A[q] * inv);
+                        } else {
+                            ep += A[q] * A[q];
+                            z[q] = make_float2(A[q], 0.f);
+                        }
                         z[q].y = -z[q].y;
                     }
                     put_pair(sBh, sBl, p * kN + half, c, z[0], z[1]);
@@ -513,12 +520,17 @@ __global__ void __launch_bounds__(kThreads2, 1) k_dft128_gemm(Args a) {
         } else {
             float ep = 0.f;
             const float *amp = a.amp + (size_t)j * kN2 * kN2;    // amp[kx][ky]
-            auto proj = [&](float2 z, float A) {
-                z = cscale(z, invN);
-                const float mag = sqrtf(cabs2(z));
-                const float dm = mag - A;
-                ep += dm * dm;
-                z = mag > 0.f ? cscale(z, A / mag) : make_float2(A, 0.f);
+            auto proj = [&](float2 z, float A) {        // z = N Psi (unscaled): A z / |z|
+                const float mag2 = cabs2(z);
+                if (mag2 > 0.f) {
+                    const float inv = rsqrtf(mag2);
+                    const float dm = mag2 * inv * invN - A;
+                    ep += dm * dm;
+                    z = cscale(z, A * inv);
+                } else {
+                    ep += A * A;
+                    z = make_float2(A, 0.f);
+                }
                 z.y = -z.y;
                 return z;
             };

@@ -135,18 +135,28 @@ __device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const 
                 pm::fft_group<R, +1>(d, xb, tw, t);
             } else {
                 pm::fft_group<R, -1>(d, xb, tw, t);
+                if constexpr (!kFull) {                 // spectra for the modes' common modulus
 #pragma unroll
-                for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
+                    for (int m = 0; m < R; ++m) d[m] = cscale(d[m], invN);
+                }
             }
             if constexpr (kFull) {
+                // d = N Psi (the forward transform unscaled): |Psi| = |d| / N, and the
+                // projection A Psi / |Psi| = A d / |d| does not depend on the scale
 #pragma unroll
                 for (int m = 0; m < R; ++m) {
                     const float2 X = d[m];
                     const float A = __ldg(amp_j + (size_t)col * N + t + R * m);
-                    const float mag = sqrtf(cabs2(X));
-                    const float dm = mag - A;
-                    err += dm * dm;
-                    d[m] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+                    const float mag2 = cabs2(X);
+                    if (mag2 > 0.f) {
+                        const float inv = rsqrtf(mag2);
+                        const float dm = mag2 * inv * invN - A;
+                        err += dm * dm;
+                        d[m] = cscale(X, A * inv);
+                    } else {
+                        err += A * A;
+                        d[m] = make_float2(A, 0.f);
+                    }
                 }
                 pm::fft_group<R, +1>(d, xb, tw, t);
             }
@@ -290,14 +300,21 @@ __device__ __forceinline__ void exit128_unit(const ExitArgs &c, int j, const flo
 #pragma unroll
         for (int m = 0; m < E; ++m) d[m] = rows[(t + R1 * m) * TP + col];
         pm::fft128_nat_to_rev<-1>(d, xb, tw, t);
+        // d = N Psi (the forward transform unscaled); the projection A d / |d| is scale-free
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const float2 X = cscale(d[e], invN);
+            const float2 X = d[e];
             const float A = __ldg(amp_j + (size_t)col * N + pm::rev128(t, e));
-            const float mag = sqrtf(cabs2(X));
-            const float dm = mag - A;
-            err += dm * dm;
-            d[e] = mag > 0.f ? cscale(X, A / mag) : make_float2(A, 0.f);
+            const float mag2 = cabs2(X);
+            if (mag2 > 0.f) {
+                const float inv = rsqrtf(mag2);
+                const float dm = mag2 * inv * invN - A;
+                err += dm * dm;
+                d[e] = cscale(X, A * inv);
+            } else {
+                err += A * A;
+                d[e] = make_float2(A, 0.f);
+            }
         }
         pm::fft128_rev_to_nat<+1>(d, xb, tw, t);
 #pragma unroll
