@@ -160,8 +160,13 @@ __device__ __forceinline__ void fft_group_xs(float2 (&d)[R], float2 *xb, const f
 
 namespace pm {
 
-// N = 128 = 8 x 16 by a group of 8 threads holding 16 elements each.  tw[k1 * 8 + t] = W_128^(t k1)
-// (forward sign), k1 < 16, t < 8.  The exchange buffer is [8][18] float2 per group (rows 18 apart;
+constexpr int kTw128Pitch = 9;                       // twiddle table of the N = 128 transforms
+constexpr int kTw128Size = 16 * kTw128Pitch;
+
+// N = 128 = 8 x 16 by a group of 8 threads holding 16 elements each.  tw[k1 * 9 + n] = W_128^(n k1)
+// (forward sign), k1 < 16, n < 8: rows of 9, so that the 8 threads of a group reading
+// W_128^(k1 n) for their own k1 = 2t + i (fft128_rev_to_nat) hit distinct banks, as do those
+// reading one row (fft128_nat_to_rev).  The exchange buffer is [8][18] float2 per group (rows 18 apart;
 // with groups 145 float2 apart, both exchange patterns of two groups sharing a half-warp hit
 // distinct banks).
 //
@@ -175,7 +180,7 @@ __device__ __forceinline__ void fft128_nat_to_rev(float2 (&d)[16], float2 *xb, c
     dft_reg<16, SIGN>(d);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
-        float2 w = tw[k1 * 8 + t];
+        float2 w = tw[k1 * kTw128Pitch + t];
         if (SIGN > 0) w.y = -w.y;
         d[k1] = cmul(d[k1], w);
     }
@@ -210,7 +215,7 @@ __device__ __forceinline__ void fft128_rev_to_nat(float2 (&d)[16], float2 *xb, c
         const int k1 = 2 * t + i;
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) {
-            float2 w = tw[k1 * 8 + n1];
+            float2 w = tw[k1 * kTw128Pitch + n1];
             if (SIGN > 0) w.y = -w.y;
             d[8 * i + n1] = cmul(e[n1], w);
         }

@@ -258,11 +258,11 @@ constexpr int kXB128 = 145;              // exchange buffer per group: [8][18] f
 
 constexpr size_t exit128_smem_bytes() {
     constexpr int N = 128, G = kThreads128 / 8;
-    return sizeof(float2) * ((size_t)N + (size_t)G * kXB128 + (size_t)N * (N + 1));
+    return sizeof(float2) * ((size_t)pm::kTw128Size + (size_t)G * kXB128 + (size_t)N * (N + 1));
 }
 
 // Per-unit body of the N = 128 exit wave (position j of dataset c), kThreads128 threads.
-// tw: [N] W_128^((i / 8) (i % 8)); xb_all: [G][kXB128]; rows: [N][N + 1]; s_red: [16].
+// tw: [16][kTw128Pitch] W_128^(k1 n); xb_all: [G][kXB128]; rows: [N][N + 1]; s_red: [16].
 __device__ __forceinline__ void exit128_unit(const ExitArgs &c, int j, const float2 *tw, float2 *xb_all,
                                              float2 *rows, double *s_red) {
     constexpr int N = 128, R1 = 8, E = 16;
@@ -345,10 +345,11 @@ __device__ __forceinline__ void exit128_unit(const ExitArgs &c, int j, const flo
     __syncthreads();
 }
 
+// tw[k1 * kTw128Pitch + n] = W_128^(k1 n) (forward sign)
 __device__ __forceinline__ void fill_twiddles128(float2 *tw, int tid, int nt) {
-    for (int i = tid; i < 128; i += nt) {
+    for (int i = tid; i < pm::kTw128Size; i += nt) {
         double sn, cs;
-        sincospi(-2.0 * (double)((i / 8) * (i % 8)) / 128.0, &sn, &cs);
+        sincospi(-2.0 * (double)((i / pm::kTw128Pitch) * (i % pm::kTw128Pitch)) / 128.0, &sn, &cs);
         tw[i] = make_float2((float)cs, (float)sn);
     }
 }
@@ -358,8 +359,8 @@ __global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
     constexpr int N = 128;
     constexpr int G = kThreads128 / 8;
     extern __shared__ float2 smem[];
-    float2 *tw = smem;                       // [N] W_128^((i / 8) (i % 8)), forward sign
-    float2 *xb_all = tw + N;                 // [G][kXB128]
+    float2 *tw = smem;                       // [16][kTw128Pitch] W_128^(k1 n), forward sign
+    float2 *xb_all = tw + pm::kTw128Size;    // [G][kXB128]
     float2 *rows = xb_all + G * kXB128;      // [N][N+1]
     __shared__ double s_red[kThreads128 / 32];
     fill_twiddles128(tw, threadIdx.x, kThreads128);
@@ -436,7 +437,7 @@ __host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a
 constexpr size_t kAllScratch =
     cmax(3 * tma_buf_bytes<32>(),
          cmax(sizeof(float2) * ((size_t)(kThreads128 / 8) * kXB128 + 128 * 129), 4 * quarter_bytes<8>()));
-constexpr size_t kAllTw = sizeof(float2) * (256 + 128 + 64 + 16);
+constexpr size_t kAllTw = sizeof(float2) * (256 + pm::kTw128Size + 64 + 16);
 constexpr size_t all_smem_bytes() { return 1024 + kAllScratch + kAllTw; }
 
 // Out-of-line unit bodies of the one launch (N <= 128), so that the inlined N = 256 body keeps
@@ -459,7 +460,7 @@ k_exit_wave_all(const int4 *__restrict__ units, int nunits, const ExitArgs *__re
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     float2 *tw256 = (float2 *)(base + kAllScratch);
-    float2 *tw128 = tw256 + 256, *tw64 = tw128 + 128, *tw16 = tw64 + 64;
+    float2 *tw128 = tw256 + 256, *tw64 = tw128 + pm::kTw128Size, *tw16 = tw64 + 64;
     __shared__ uint64_t s_bar[4];
     __shared__ double s_red[96];                  // the N = 256 unit: warp sums [2][32], batch sums [8]
     __shared__ uint32_t s_pending;
