@@ -264,8 +264,10 @@ int ptycho_stage_times(ptycho_handle h, double *ms /*[4]*/, long long *launches 
  *                        iteration as a CUDA graph and replays it (re-captured when the set of
  *                        datasets updating their probe changes); PTYCHO_BATCH_AUTOTUNE times
  *                        candidate launch shapes (persistent grid sizes; rows per TMA stage at
- *                        N = 256) on the datasets themselves, keeps the fastest and restores
- *                        every object and probe (results are unaffected).  PTYCHO_BATCH_ONE_LAUNCH
+ *                        N = 256; then the tuned per-size launches against the one persistent
+ *                        launch below, when two or more datasets can share it) on the datasets
+ *                        themselves, keeps the fastest and restores every object and probe
+ *                        (results are unaffected).  PTYCHO_BATCH_ONE_LAUNCH
  *                        computes the exit waves of every single-mode radix-FFT dataset, of any
  *                        N, in ONE persistent launch per iteration (units ordered by cost and
  *                        dealt to one 512-thread CTA per SM; N <= 64 positions four at a time per

@@ -1912,8 +1912,24 @@ std::string class_key(const ptycho_batch_ctx *b, const ptycho_batch_ctx::Class &
     return k;
 }
 
+int setup_one_launch(ptycho_batch_ctx *b);
+
+// Datasets the one persistent exit-wave launch can take (single mode, radix FFT), and the key
+// of the tuner's choice between it and the per-size launches for this set of shapes.
+int one_launch_eligible(const ptycho_batch_ctx *b, std::string *key) {
+    int n = 0;
+    *key = "one:";
+    for (const ptycho_ctx *h : b->hs)
+        if (h->Q == 1 && !h->fft_gemm) {
+            ++n;
+            *key += std::to_string(h->N) + "/" + std::to_string(h->J) + "/" + std::to_string(h->M) + ",";
+        }
+    return n;
+}
+
 // Coordinate search over the launch shapes, on the batch's own data; object, probe and
-// iteration counters are restored afterwards.
+// iteration counters are restored afterwards.  Last, the tuned per-size launches are timed
+// against the one persistent launch for all eligible datasets, and the faster is kept.
 int autotune(ptycho_batch_ctx *b) {
     const int reps = 3;
     std::vector<float2 *> so(b->hs.size()), sp(b->hs.size());
@@ -1931,6 +1947,8 @@ int autotune(ptycho_batch_ctx *b) {
                 any = true;
             }
         need = need || (any && !g_tune_cache.count(bkey));
+        std::string okey;
+        need = need || (!b->one_launch && one_launch_eligible(b, &okey) >= 2 && !g_tune_cache.count(okey));
     }
     for (size_t i = 0; i < b->hs.size() && !rc && need; ++i) {
         ptycho_ctx *h = b->hs[i];
@@ -2031,6 +2049,34 @@ int autotune(ptycho_batch_ctx *b) {
         std::snprintf(buf, sizeof buf, "%s\"tma_rows_n256\": %d, \"tma_rows_tried_ms\": \"%s\"",
                       rep.size() > 1 ? ", " : "", best, tried.c_str());
         rep += buf;
+    }
+    // one persistent launch for every eligible dataset, or the per-size launches tuned above
+    std::string okey;
+    if (!rc && !b->one_launch && one_launch_eligible(b, &okey) >= 2) {
+        int choice = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(okey);
+            if (it != g_tune_cache.end()) choice = it->second;
+        }
+        if (choice >= 0) {
+            ++cached;
+            if (choice == 1) rc = setup_one_launch(b);
+            std::snprintf(buf, sizeof buf, "%s\"one_launch\": %d", rep.size() > 1 ? ", " : "", choice);
+        } else {
+            const double t_sizes = time_iterations(b, reps, &rc);
+            if (!rc) rc = setup_one_launch(b);
+            const double t_one = rc ? 0.0 : time_iterations(b, reps, &rc);
+            choice = (!rc && b->one_launch && t_one < t_sizes) ? 1 : 0;
+            if (!rc) {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune_cache[okey] = choice;
+            }
+            std::snprintf(buf, sizeof buf, "%s\"one_launch\": %d, \"one_launch_tried_ms\": \"sizes:%.3f,one:%.3f\"",
+                          rep.size() > 1 ? ", " : "", choice, t_sizes / reps, t_one / reps);
+        }
+        rep += buf;
+        if (!rc && choice == 0) b->one_launch = false;      // its tables stay allocated, unused
     }
     for (size_t i = 0; i < b->hs.size(); ++i) {
         ptycho_ctx *h = b->hs[i];

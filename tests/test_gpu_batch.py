@@ -87,6 +87,7 @@ def test_batch_matches_individual_handles(api, inputs, reference, graph, autotun
         desc = api.ptycho_batch_describe(b)
         print("autotune:", desc)
         assert "class_radix64_grid" in desc and "tma_rows_n256" in desc
+        assert '"one_launch"' in desc              # the per-size launches against the one launch
     api.ptycho_batch_iterate(b, 2)
     err = api.ptycho_batch_iterate(b, 4)
     for i, h in enumerate(hs):
