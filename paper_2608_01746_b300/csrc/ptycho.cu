@@ -97,6 +97,10 @@ __device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const 
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     const int t = tid % R, g = tid / R;
     float2 *xb = xb_all + g * R * (R + 1);
+    // Row / column of group g within each pass of G: at N = 64 the two groups of a half-warp
+    // take rows (columns) 8 apart, whose 8-byte accesses with the row pitch of 65 then fall on
+    // distinct banks (consecutive rows would overlap on 14 of their 16 banks).
+    const int gp = (R == 8) ? (((g >> 1) & 7) | ((g & 1) << 3) | (g & ~15)) : g;
     const float invN = 1.0f / (float)N;
     const int M = c.M;
     const int j = kFull ? u : u / Q;
@@ -106,7 +110,7 @@ __device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const 
         // (1) psi = P_m * O_j, forward row FFTs in place
         const int2 pj = c.pos[j];
         for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
+            const int r = r0 + gp;
             if (r < N) {                                 // warp-uniform (see fft.cuh)
                 float2 d[R];
                 const float2 *orow = c.obj + (size_t)(pj.x + r) * M + pj.y;
@@ -126,7 +130,7 @@ __device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const 
     float err = 0.f;
     const float *amp_j = c.amp + (size_t)j * N * N;
     for (int c0 = 0; c0 < N; c0 += G) {
-        const int col = c0 + g;
+        const int col = c0 + gp;
         if (col < N) {
             float2 d[R];
 #pragma unroll
@@ -170,7 +174,7 @@ __device__ __forceinline__ void exit_small_unit(const ExitArgs &c, int u, const 
     } else {
         // (3) inverse row FFTs, psi' written row-major
         for (int r0 = 0; r0 < N; r0 += G) {
-            const int r = r0 + g;
+            const int r = r0 + gp;
             if (r < N) {
                 float2 d[R];
 #pragma unroll
