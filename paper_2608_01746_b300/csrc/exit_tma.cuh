@@ -206,7 +206,13 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
     constexpr bool kFull = (XM == XM_FULL || XM == XM_LIST);
     namespace T = pm::tma;
     const int tid = threadIdx.x;
-    const int t = tid & 15, g = tid >> 4;                        // g in [0, B)
+    // group g = one 256-point vector, thread t of 16 (g in [0, B)).  A warp holds groups 2w and
+    // 2w + 1, interleaved by eights: lanes 0-7 and 24-31 are group 2w (t = 0-7, 8-15), lanes
+    // 8-23 group 2w + 1 (t = 8-15, 0-7).  Each half-warp then holds t = 0-7 of one group and
+    // t = 8-15 of the other, so its 8-byte accesses to the two vectors' rows (2 KB apart, the
+    // same banks), to the exchange and to the 128-byte-swizzled staging (rows t and t + 8 share
+    // a swizzle phase) fall on 16 distinct bank pairs.
+    const int t = tid & 15, g = (tid >> 4) ^ ((tid >> 3) & 1);
     const int h = g >> 4, gl = g & 15;                           // 16-wide box of the batch, row in it
     auto bin = [&](int s) { return (float2 *)(p.base + s * kTmaBuf); };
     float2 *bout = (float2 *)(p.base + 2 * kTmaBuf);
