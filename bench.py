@@ -208,7 +208,7 @@ def iteration_flops_per_update(N: int) -> float:
 # positions, one launch: dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256, first 16 hex digits).  A changed kernel
 # reports traffic null until it is captured again.
-EXIT_TRAFFIC = {"sources_sha16": "02e6c983dd1524e1", "bytes_per_position": 2146237,
+EXIT_TRAFFIC = {"sources_sha16": "ad6fdf6af1adf546", "bytes_per_position": 2150116,
                 "capture": "ncu, k_exit_wave_tma<16, FULL>, one launch over 888 lab positions = three whole rounds of 296 CTAs"}
 
 
