@@ -385,27 +385,40 @@ __global__ void __launch_bounds__(kThreads128) k_exit_wave128(ExitArgs a) {
 // Mixed-state modulus constraint, one block per position: S = sum_m |Psi_m|^2,
 // error (sqrt(S) - A)^2, Psi_m <- Psi_m A / sqrt(S) (where S = 0: Psi_0 = A, other modes 0).
 // psi: [J][Q][N][N] spectra (row-major, DC at 0); amp_nat: [J][N][N] row-major amplitudes.
-__global__ void __launch_bounds__(kThreads) k_modulus_modes(float2 *__restrict__ psi,
-                                                            const float *__restrict__ amp_nat,
-                                                            double *__restrict__ err, int N, int Q) {
-    __shared__ double s_red[kThreads / 32];
+// Q is a template parameter so that a pixel's Q loads are issued together and its values stay
+// in registers between the sum and the scaling (one read and one write of each spectrum);
+// 512-thread blocks, two per SM (64 registers), keep the last wave of positions short.
+constexpr int kModThreads = 512;
+
+template <int Q>
+__global__ void __launch_bounds__(kModThreads, 2) k_modulus_modes(float2 *__restrict__ psi,
+                                                               const float *__restrict__ amp_nat,
+                                                               double *__restrict__ err, int N) {
+    __shared__ double s_red[kModThreads / 32];
     const int j = blockIdx.x;
     const size_t NN = (size_t)N * N;
     float2 *pj = psi + (size_t)j * Q * NN;
     double acc = 0.0;
-    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
-        float S = 0.f;
-        for (int m = 0; m < Q; ++m) S += cabs2(pj[m * NN + q]);
+#pragma unroll 1
+    for (size_t q = threadIdx.x; q < NN; q += kModThreads) {
+        float2 v[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) v[m] = pj[m * NN + q];
         const float A = __ldg(amp_nat + (size_t)j * NN + q);
+        float S = 0.f;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) S += cabs2(v[m]);
         if (S > 0.f) {
             const float inv = rsqrtf(S);
             const float dm = S * inv - A;
             acc += (double)(dm * dm);
             const float sc = A * inv;
-            for (int m = 0; m < Q; ++m) pj[m * NN + q] = cscale(pj[m * NN + q], sc);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) pj[m * NN + q] = cscale(v[m], sc);
         } else {
             acc += (double)A * (double)A;
             pj[q] = make_float2(A, 0.f);
+#pragma unroll
             for (int m = 1; m < Q; ++m) pj[m * NN + q] = make_float2(0.f, 0.f);
         }
     }
@@ -415,9 +428,24 @@ __global__ void __launch_bounds__(kThreads) k_modulus_modes(float2 *__restrict__
     __syncthreads();
     if (threadIdx.x == 0) {
         double r = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) r += s_red[w];
+        for (int w = 0; w < kModThreads / 32; ++w) r += s_red[w];
         err[j] = r;
     }
+}
+
+int launch_modulus_modes(float2 *psi, const float *amp_nat, double *err, int J, int N, int Q, cudaStream_t st) {
+    switch (Q) {
+        case 2: k_modulus_modes<2><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 3: k_modulus_modes<3><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 4: k_modulus_modes<4><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 5: k_modulus_modes<5><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 6: k_modulus_modes<6><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 7: k_modulus_modes<7><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        case 8: k_modulus_modes<8><<<J, kModThreads, 0, st>>>(psi, amp_nat, err, N); break;
+        default: return pm::fail(PTYCHO_EINVAL, "k_modulus_modes: Q = %d not in [2, 8]", Q);
+    }
+    PM_LAUNCHED("k_modulus_modes");
+    return PTYCHO_OK;
 }
 
 #include "exit_tma.cuh"
@@ -1272,8 +1300,7 @@ int launch_exit_any(ptycho_ctx *h, int *launches) {
     }
     *launches = 3;
     if ((rc = launch_exit_pass(h, XM_FWD))) return rc;
-    k_modulus_modes<<<h->J, kThreads, 0, h->st>>>(h->d_psi, h->d_amp_nat, h->d_err_pos, h->N, h->Q);
-    PM_LAUNCHED("k_modulus_modes");
+    if ((rc = launch_modulus_modes(h->d_psi, h->d_amp_nat, h->d_err_pos, h->J, h->N, h->Q, h->st))) return rc;
     return launch_exit_pass(h, XM_INV);
 }
 
