@@ -116,3 +116,19 @@ def test_mixed_state_stage_launches(api):
     assert launches == [6, 4, 6, 0]          # forward, modulus, inverse per iteration; the error
                                              # is formed inside the object step's k_apply
     api.ptycho_destroy(h)
+
+
+@pytest.mark.parametrize("q", [2, 3, 5, 6, 7])
+def test_mode_counts_match_oracle(api, q):
+    """Every compile-time mode count of the modulus kernel: the first q probe modes of the
+    small mixed-state scan, 5 iterations with probe updates, against the FP64 oracle."""
+    sc = synth.make_scan("mixed_small")
+    cfg = sc["cfg"]
+    p = oracle.FuseParams(levels=cfg.levels, clip=float(cfg.clip))
+    fused = oracle.mnf_stack(sc["raw"], sc["times"], p).astype(np.float32)
+    sc = dict(sc, probe=sc["probe"][:q])
+    (o, pr, e), (ro, rp, re) = run(api, sc, fused, 5, 0)
+    assert pr.shape == (q, 64, 64)
+    assert rel_l2(o, ro) <= 1e-5
+    assert rel_l2(pr, rp) <= 1e-5
+    np.testing.assert_allclose(e, re, rtol=1e-5)
