@@ -994,7 +994,7 @@ int hfree(ptycho_ctx *h, T **p) {
 
 void free_ctx(ptycho_ctx *h) {
     if (!h) return;
-    if (h->st) cudaStreamSynchronize(h->st);
+    cudaStreamSynchronize(h->st);                       // the default stream too (documented wait)
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
                     h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
                     h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder, h->d_trange,
