@@ -680,11 +680,11 @@ __global__ void __launch_bounds__(kThreads) k_epie_object(float2 *__restrict__ o
     __shared__ float s_mp[kThreads / 32], s_mo[kThreads / 32];
     const int u = blockIdx.x, j = list[u];
     const int2 pj = pos[j];
-    const size_t NN = (size_t)N * N;
+    const int NN = N * N, lgN = __ffs(N) - 1;          // N is a power of two (16, 64, 128, 256)
     float mp = 0.f, mo = 0.f;
-    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
+    for (int q = threadIdx.x; q < NN; q += blockDim.x) {
         mp = fmaxf(mp, cabs2(probe[q]));
-        mo = fmaxf(mo, cabs2(obj[(size_t)(pj.x + q / N) * M + pj.y + q % N]));
+        mo = fmaxf(mo, cabs2(obj[(size_t)(pj.x + (q >> lgN)) * M + pj.y + (q & (N - 1))]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -699,8 +699,8 @@ __global__ void __launch_bounds__(kThreads) k_epie_object(float2 *__restrict__ o
     const float so = mp > 0.f ? alpha / mp : 0.f;
     const float sp = mo > 0.f ? 1.0f / mo : 0.f;
     const float2 *psi_j = psi + (size_t)j * NN;
-    for (size_t q = threadIdx.x; q < NN; q += blockDim.x) {
-        float2 *op = obj + (size_t)(pj.x + q / N) * M + pj.y + q % N;
+    for (int q = threadIdx.x; q < NN; q += blockDim.x) {
+        float2 *op = obj + (size_t)(pj.x + (q >> lgN)) * M + pj.y + (q & (N - 1));
         const float2 p = probe[q];
         const float2 o = *op;
         const float2 d = csub(psi_j[q], cmul(p, o));
