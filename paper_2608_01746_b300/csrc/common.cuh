@@ -43,6 +43,14 @@ struct NvtxRange {
         if (pm_e_ != cudaSuccess) return pm::cuda_fail(pm_e_, what);        \
     } while (0)
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization may
+// be scheduled while the previous kernel on its stream is still running: pdl_wait() (first, before
+// the kernel touches memory) returns once that kernel has completed and its writes are visible.
+// pdl_allow_dependents() lets the next such kernel be scheduled as this one's blocks retire.
+// Both are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

@@ -591,6 +591,8 @@ __global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_object_gather(
     __shared__ WarpTiles wt;
     __shared__ float s_max[kThreads / 32];
     __shared__ int3 s_list[kListChunk];
+    pdl_allow_dependents();
+    pdl_wait();                                       // the exit waves are complete
     const int tile = torder[blockIdx.x];              // longest position lists first
     const int ty0 = (tile / ntx) * kTR, tx0 = (tile % ntx) * kTW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -757,6 +759,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(float2 *__restrict__ x, cons
                                                     int nmax, size_t n, float alpha, const double *__restrict__ err,
                                                     int J, const double *__restrict__ inv_norm,
                                                     double *__restrict__ err_out) {
+    pdl_allow_dependents();
+    pdl_wait();                                       // the numerators and denominators are complete
     const float reg = alpha * block_max(partial_max, nmax);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float d = den[i];
@@ -775,6 +779,8 @@ __global__ void __launch_bounds__(kThreads, QC == 1 ? 3 : 2) k_probe_partial(
     const float2 *__restrict__ psi, const float2 *__restrict__ obj, const int2 *__restrict__ pos,
     float2 *__restrict__ pnum, float *__restrict__ pden, int M, int N, int J, int per_chunk, int Q) {
     __shared__ WarpTiles wt;
+    pdl_allow_dependents();
+    pdl_wait();                                       // the new object is complete
     const int nqx = (N + kTW - 1) / kTW;
     const int qt = blockIdx.x, chunk = blockIdx.y;
     const int qy0 = (qt / nqx) * kTR, qx0 = (qt % nqx) * kTW;
@@ -830,6 +836,8 @@ __global__ void __launch_bounds__(kThreads) k_probe_reduce(const float2 *__restr
                                                            float *__restrict__ den, float *__restrict__ bmax, int NN,
                                                            int nchunk) {
     __shared__ float s[kThreads / 32];
+    pdl_allow_dependents();
+    pdl_wait();                                       // the partial sums are complete
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float d = 0.f;
     if (i < NN) {
@@ -960,6 +968,9 @@ struct ptycho_ctx {
     std::vector<int> mark;
     size_t ev_used = 0;
     bool ev_fresh = false;
+    // the object and probe update kernels of ptycho_iterate are launched with programmatic
+    // stream serialization (not while the stream is being captured, nor from a batch)
+    bool pdl = false;
 };
 
 namespace {
@@ -1335,6 +1346,25 @@ int stage_end(ptycho_ctx *h, int s, size_t base, int launches) {
     return PTYCHO_OK;
 }
 
+// Launch of an update kernel on the handle's stream; with h->pdl, as a programmatic dependent of
+// the kernel before it (the kernel calls pdl_wait before it touches memory).
+template <typename... KArgs, typename... Args>
+int launch_update(ptycho_ctx *h, void (*kernel)(KArgs...), dim3 grid, const char *what, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = h->pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess) return pm::cuda_fail(e, what);
+    return PTYCHO_OK;
+}
+
 // ePIE by colour: colours in ascending order; per colour the fused exit-wave kernel on the
 // colour's positions, the object step (disjoint patches, no atomics) and the averaged probe
 // step.  The whole colour loop is timed as stage 0.
@@ -1388,39 +1418,36 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     }
     // object
     if ((rc = stage_begin(h, ST_OBJECT, ev_base))) return rc;
-    if (h->Q == 1)
-        k_object_gather<1><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tlist, h->d_torder,
-                                                              h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N,
-                                                              h->ntx, 1);
-    else
-        k_object_gather<0><<<h->ntiles, kThreads, 0, h->st>>>(h->d_psi, h->d_probe, h->d_pos, h->d_tlist, h->d_torder,
-                                                              h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N,
-                                                              h->ntx, h->Q);
-    PM_LAUNCHED("k_object_gather");
+    if ((rc = launch_update(h, h->Q == 1 ? k_object_gather<1> : k_object_gather<0>, dim3(h->ntiles),
+                            "k_object_gather", (const float2 *)h->d_psi, (const float2 *)h->d_probe,
+                            (const int2 *)h->d_pos, (const int4 *)h->d_tlist, (const int *)h->d_torder,
+                            (const int2 *)h->d_trange, h->d_num_o, h->d_den_o, h->d_tile_max, h->M, h->N, h->ntx,
+                            h->Q)))
+        return rc;
     const size_t MM = (size_t)h->M * h->M;
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
-    k_apply<<<gapply, kThreads, 0, h->st>>>(h->d_obj, h->d_num_o, h->d_den_o, h->d_tile_max, h->ntiles, MM,
-                                            h->alpha_O, h->d_err_pos, h->J, h->d_inv_norm, err_dst);
-    PM_LAUNCHED("k_apply(object)");
+    if ((rc = launch_update(h, k_apply, dim3(gapply), "k_apply(object)", h->d_obj, (const float2 *)h->d_num_o,
+                            (const float *)h->d_den_o, (const float *)h->d_tile_max, h->ntiles, MM, h->alpha_O,
+                            (const double *)h->d_err_pos, h->J, (const double *)h->d_inv_norm, err_dst)))
+        return rc;
     if ((rc = stage_end(h, ST_OBJECT, ev_base, 2))) return rc;
     // probe
     if ((rc = stage_begin(h, ST_PROBE, ev_base))) return rc;
     if (update_probe) {
         const int NN = h->N * h->N * h->Q;                // all probe modes
-        if (h->Q == 1)
-            k_probe_partial<1><<<dim3(h->nqt, h->nchunk, 1), kThreads, 0, h->st>>>(
-                h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, 1);
-        else
-            k_probe_partial<0><<<dim3(h->nqt, h->nchunk, h->Q), kThreads, 0, h->st>>>(
-                h->d_psi, h->d_obj, h->d_pos, h->d_pnum, h->d_pden, h->M, h->N, h->J, h->per_chunk, h->Q);
-        PM_LAUNCHED("k_probe_partial");
-        k_probe_reduce<<<h->nred, kThreads, 0, h->st>>>(h->d_pnum, h->d_pden, h->d_num_p, h->d_den_p, h->d_pmax, NN,
-                                                        h->nchunk);
-        PM_LAUNCHED("k_probe_reduce");
+        if ((rc = launch_update(h, h->Q == 1 ? k_probe_partial<1> : k_probe_partial<0>,
+                                dim3(h->nqt, h->nchunk, h->Q == 1 ? 1 : h->Q), "k_probe_partial",
+                                (const float2 *)h->d_psi, (const float2 *)h->d_obj, (const int2 *)h->d_pos, h->d_pnum,
+                                h->d_pden, h->M, h->N, h->J, h->per_chunk, h->Q)))
+            return rc;
+        if ((rc = launch_update(h, k_probe_reduce, dim3(h->nred), "k_probe_reduce", (const float2 *)h->d_pnum,
+                                (const float *)h->d_pden, h->d_num_p, h->d_den_p, h->d_pmax, NN, h->nchunk)))
+            return rc;
         const unsigned gp = (unsigned)std::min<int>((NN + kThreads - 1) / kThreads, 148 * 4);
-        k_apply<<<gp, kThreads, 0, h->st>>>(h->d_probe, h->d_num_p, h->d_den_p, h->d_pmax, h->nred, (size_t)NN,
-                                            h->alpha_P, nullptr, 0, nullptr, nullptr);
-        PM_LAUNCHED("k_apply(probe)");
+        if ((rc = launch_update(h, k_apply, dim3(gp), "k_apply(probe)", h->d_probe, (const float2 *)h->d_num_p,
+                                (const float *)h->d_den_p, (const float *)h->d_pmax, h->nred, (size_t)NN, h->alpha_P,
+                                (const double *)nullptr, 0, (const double *)nullptr, (double *)nullptr)))
+            return rc;
     }
     if ((rc = stage_end(h, ST_PROBE, ev_base, update_probe ? 3 : 0))) return rc;
     // the error is formed by block 0 of the object step's k_apply: no stage of its own
@@ -1649,11 +1676,20 @@ extern "C" int ptycho_iterate(ptycho_handle h, int n_iter, double *h_err) {
         h->ev_used = 0;
         h->ev_fresh = false;
     }
-    for (int i = 0; i < n_iter; ++i) {
-        const bool upd = h->iter >= h->probe_update_start;
-        int rc = iterate_one(h, h->d_err + i, (size_t)i * ST_COUNT, upd);
-        if (rc) return rc;
-        ++h->iter;
+    {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        PM_CUDA(cudaStreamIsCapturing(h->st, &cap));
+        struct PdlScope {
+            ptycho_ctx *h;
+            ~PdlScope() { h->pdl = false; }
+        } scope{h};
+        h->pdl = cap == cudaStreamCaptureStatusNone;
+        for (int i = 0; i < n_iter; ++i) {
+            const bool upd = h->iter >= h->probe_update_start;
+            int rc = iterate_one(h, h->d_err + i, (size_t)i * ST_COUNT, upd);
+            if (rc) return rc;
+            ++h->iter;
+        }
     }
     if (h->timing && h->ev_used > 0) {
         PM_CUDA(cudaEventSynchronize(h->ev[h->ev_used - 1]));
