@@ -226,7 +226,9 @@ int ptycho_get_colouring(ptycho_handle h, int32_t *h_colour, int *n_colours);
 
 /* Release every device resource of the handle (waits for its stream; work of other streams
  * on the handle's buffers, e.g. a batch, must be finished or destroyed first).  The buffers go
- * back to the library's memory pool (see ptycho_release_memory).  NULL is a no-op. */
+ * back to the library's memory pool (see ptycho_release_memory), ordered on the handle's stream;
+ * destroy the handle before that stream (if the stream is gone, they are freed after a device
+ * synchronisation instead).  NULL is a no-op. */
 void ptycho_destroy(ptycho_handle h);
 
 /*

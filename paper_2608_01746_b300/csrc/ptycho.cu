@@ -1012,7 +1012,10 @@ void free_ctx(ptycho_ctx *h) {
                     h->d_tail_sync, h->d_tail_err,
                     h->d_colour_list, h->d_epie_part};
     for (void *p : ptrs)
-        if (p) cudaFreeAsync(p, h->st);
+        if (p && cudaFreeAsync(p, h->st) != cudaSuccess) {
+            (void)cudaGetLastError();                    // e.g. the stream was destroyed first:
+            cudaFree(p);                                 // free after a device synchronisation
+        }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
 }
