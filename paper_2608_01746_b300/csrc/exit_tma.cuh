@@ -39,6 +39,10 @@ struct TmaArgs {
     int split, tail_base;
     int *tail_sync;
     double *tail_err;
+    // XM_INV (mixed state): if not NULL, the mode-summed modulus constraint's per-pixel scale
+    // A / sqrt(sum_m |Psi_m|^2), [J][N][N] in the amplitude order (column kx, then thread t's rows
+    // t + 16 k2 contiguous); each loaded spectrum is multiplied by it before the inverse FFTs
+    const float *fscale;
 };
 
 struct TmaMaps {
@@ -424,6 +428,14 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
         if (tid == 0) T::wait_all<0>();
         load_psi_cols(0, 0);
         load_psi_cols(1, kTmaBatch);
+        // the modulus scales of the next column (one column batch ahead, like the amplitudes)
+        const float *fs_j = a.fscale ? a.fscale + (size_t)j * N * N : nullptr;
+        float4 Fn[R / 4];
+        if (fs_j) {
+            const float4 *f = reinterpret_cast<const float4 *>(fs_j + (size_t)g * N + t * R);
+#pragma unroll
+            for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_stream);
+        }
         for (int b = 0; b < NB; ++b) {
             const int s = b & 1;
             wait_stage(s);
@@ -431,6 +443,18 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
             const float2 *colsw = bin(s) + h * 4096;
 #pragma unroll
             for (int m = 0; m < R; ++m) d[m] = colsw[T::swz128_index(t + R * m, gl)];
+            if (fs_j) {
+                const float F[R] = {Fn[0].x, Fn[0].y, Fn[0].z, Fn[0].w, Fn[1].x, Fn[1].y, Fn[1].z, Fn[1].w,
+                                    Fn[2].x, Fn[2].y, Fn[2].z, Fn[2].w, Fn[3].x, Fn[3].y, Fn[3].z, Fn[3].w};
+                if (b + 1 < NB) {
+                    const float4 *f =
+                        reinterpret_cast<const float4 *>(fs_j + (size_t)(kTmaBatch * (b + 1) + g) * N + t * R);
+#pragma unroll
+                    for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_stream);
+                }
+#pragma unroll
+                for (int m = 0; m < R; ++m) d[m] = cscale(d[m], F[m]);
+            }
             if (__syncthreads_or(timed_out)) failed = true;   // batch read: regions free
             if (failed) return tma_state(parity, failed, timed_out, mphase);
             pm::fft_group_xs<R, +1>(d, bin(s) + g * 256, tw, t);

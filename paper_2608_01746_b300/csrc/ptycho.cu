@@ -448,6 +448,81 @@ int launch_modulus_modes(float2 *psi, const float *amp_nat, double *err, int J, 
     return PTYCHO_OK;
 }
 
+// The mode-summed modulus constraint of the N = 256 mixed-state path without rewriting the
+// spectra: per pixel the scale F = A / sqrt(S), S = sum_m |Psi_m|^2, which the inverse TMA
+// kernel applies to each spectrum as it loads it (the same product the rewrite would store);
+// where S = 0 the spectra are written here (Psi_0 = A, the other modes 0) and F = 1.  One
+// block per (32-column strip, position): warp w takes rows w, w + 8, ..., lane = column; the
+// strip's scales are transposed in shared memory into the amplitude order (column kx, then
+// rows t + 16 k2 at t * 16 + k2) and written as 32 contiguous 1 KB columns.  The Fourier
+// error of each strip goes to err[j * 8 + strip] (FP64, fixed order).
+constexpr int kScaleCols = 32;
+
+template <int Q>
+__global__ void __launch_bounds__(kThreads) k_mode_scale(float2 *__restrict__ psi, const float *__restrict__ amp_nat,
+                                                         float *__restrict__ fscale, double *__restrict__ err) {
+    constexpr int N = 256;
+    __shared__ float sF[kScaleCols][N + 1];
+    __shared__ double s_red[kThreads / 32];
+    const int strip = blockIdx.x, j = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t NN = (size_t)N * N;
+    float2 *pj = psi + (size_t)j * Q * NN;
+    const int kx = strip * kScaleCols + lane;
+    double acc = 0.0;
+#pragma unroll 1
+    for (int ky = warp; ky < N; ky += kThreads / 32) {
+        const size_t q = (size_t)ky * N + kx;
+        float2 v[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) v[m] = pj[m * NN + q];
+        const float A = __ldg(amp_nat + (size_t)j * NN + q);
+        float S = 0.f;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) S += cabs2(v[m]);
+        float F = 1.0f;
+        if (S > 0.f) {
+            const float inv = rsqrtf(S);
+            const float dm = S * inv - A;
+            acc += (double)(dm * dm);
+            F = A * inv;
+        } else {
+            acc += (double)A * (double)A;
+            pj[q] = make_float2(A, 0.f);
+#pragma unroll
+            for (int m = 1; m < Q; ++m) pj[m * NN + q] = make_float2(0.f, 0.f);
+        }
+        sF[lane][(ky & 15) * 16 + (ky >> 4)] = F;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    float *fj = fscale + (size_t)j * NN + (size_t)strip * kScaleCols * N;
+    for (int i = threadIdx.x; i < kScaleCols * N; i += kThreads) fj[i] = sF[i / N][i % N];
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) r += s_red[w];
+        err[(size_t)j * (N / kScaleCols) + strip] = r;
+    }
+}
+
+int launch_mode_scale(float2 *psi, const float *amp_nat, float *fscale, double *err, int J, int Q, cudaStream_t st) {
+    const dim3 grid(256 / kScaleCols, J);
+    switch (Q) {
+        case 2: k_mode_scale<2><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 3: k_mode_scale<3><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 4: k_mode_scale<4><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 5: k_mode_scale<5><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 6: k_mode_scale<6><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 7: k_mode_scale<7><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        case 8: k_mode_scale<8><<<grid, kThreads, 0, st>>>(psi, amp_nat, fscale, err); break;
+        default: return pm::fail(PTYCHO_EINVAL, "k_mode_scale: Q = %d not in [2, 8]", Q);
+    }
+    PM_LAUNCHED("k_mode_scale");
+    return PTYCHO_OK;
+}
+
 #include "exit_tma.cuh"
 
 // ---------------------------------------------------------------------------------------
@@ -932,6 +1007,8 @@ struct ptycho_ctx {
     float2 *d_obj = nullptr, *d_probe = nullptr, *d_psi = nullptr, *d_slot = nullptr;
     float2 *d_num_o = nullptr, *d_num_p = nullptr, *d_pnum = nullptr;
     float *d_amp_nat = nullptr;                           // row-major amplitudes (Q > 1)
+    float *d_fscale = nullptr;     // mode-summed modulus scales (Q > 1, N = 256), amplitude order
+    int n_err = 0;                 // per-position error slots summed into the Fourier error
     float *d_amp = nullptr, *d_den_o = nullptr, *d_den_p = nullptr, *d_pden = nullptr;
     float *d_tile_max = nullptr, *d_pmax = nullptr;
     double *d_err_pos = nullptr, *d_a2 = nullptr, *d_inv_norm = nullptr, *d_err = nullptr;
@@ -1007,7 +1084,7 @@ void free_ctx(ptycho_ctx *h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);                       // the default stream too (documented wait)
     void *ptrs[] = {h->d_pos, h->d_obj, h->d_probe, h->d_psi, h->d_slot, h->d_num_o, h->d_num_p, h->d_pnum,
-                    h->d_amp, h->d_amp_nat, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
+                    h->d_amp, h->d_amp_nat, h->d_fscale, h->d_den_o, h->d_den_p, h->d_pden, h->d_tile_max, h->d_pmax, h->d_err_pos,
                     h->d_a2, h->d_inv_norm, h->d_err, h->d_err_batch, h->d_tstart, h->d_tlist, h->d_status, h->d_torder, h->d_trange,
                     h->d_tail_sync, h->d_tail_err,
                     h->d_colour_list, h->d_epie_part};
@@ -1127,6 +1204,7 @@ TmaArgs tma_args(ptycho_ctx *h) {
     a.tail_base = h->J;
     a.tail_sync = h->d_tail_sync;
     a.tail_err = h->d_tail_err;
+    a.fscale = h->d_fscale;
     return a;
 }
 
@@ -1314,7 +1392,9 @@ int launch_exit_any(ptycho_ctx *h, int *launches) {
     }
     *launches = 3;
     if ((rc = launch_exit_pass(h, XM_FWD))) return rc;
-    if ((rc = launch_modulus_modes(h->d_psi, h->d_amp_nat, h->d_err_pos, h->J, h->N, h->Q, h->st))) return rc;
+    if (h->d_fscale) rc = launch_mode_scale(h->d_psi, h->d_amp_nat, h->d_fscale, h->d_err_pos, h->J, h->Q, h->st);
+    else rc = launch_modulus_modes(h->d_psi, h->d_amp_nat, h->d_err_pos, h->J, h->N, h->Q, h->st);
+    if (rc) return rc;
     return launch_exit_pass(h, XM_INV);
 }
 
@@ -1431,7 +1511,7 @@ int iterate_one(ptycho_ctx *h, double *err_dst, size_t ev_base, bool update_prob
     const unsigned gapply = (unsigned)std::min<size_t>((MM + kThreads - 1) / kThreads, 148 * 8);
     if ((rc = launch_update(h, k_apply, dim3(gapply), "k_apply(object)", h->d_obj, (const float2 *)h->d_num_o,
                             (const float *)h->d_den_o, (const float *)h->d_tile_max, h->ntiles, MM, h->alpha_O,
-                            (const double *)h->d_err_pos, h->J, (const double *)h->d_inv_norm, err_dst)))
+                            (const double *)h->d_err_pos, h->n_err, (const double *)h->d_inv_norm, err_dst)))
         return rc;
     if ((rc = stage_end(h, ST_OBJECT, ev_base, 2))) return rc;
     // probe
@@ -1609,7 +1689,9 @@ extern "C" int ptycho_init(ptycho_handle *out, const ptycho_desc *d) {
     if (!rc) rc = halloc(h, &h->d_pmax, h->nred);
     if (!rc) rc = halloc(h, &h->d_amp, (size_t)J * NN);
     if (!rc && Q > 1) rc = halloc(h, &h->d_amp_nat, (size_t)J * NN);
-    if (!rc) rc = halloc(h, &h->d_err_pos, (size_t)J);
+    if (!rc && Q > 1 && h->exit_tma) rc = halloc(h, &h->d_fscale, (size_t)J * NN);
+    h->n_err = (Q > 1 && h->exit_tma) ? J * (256 / kScaleCols) : J;   // mixed N = 256: per strip
+    if (!rc) rc = halloc(h, &h->d_err_pos, (size_t)h->n_err);
     if (!rc) rc = halloc(h, &h->d_a2, J);
     if (!rc) rc = halloc(h, &h->d_inv_norm, 1);
     if (!rc) rc = halloc(h, &h->d_err_batch, 1);

@@ -86,10 +86,12 @@ def test_mixed_state_workload_each_iteration_matches_oracle(api):
     print(f"first step {worst[0]:.2e}, worst later step {worst[1]:.2e} over {n_iter} iterations")
 
 
-def test_mixed_state_256_matches_oracle(api):
-    """The N = 256 forward / modulus / inverse kernels: lab geometry, 120 positions, 4 modes,
-    two iterations."""
-    cfg = dataclasses.replace(synth.CONFIGS["mixed"], J=120, modes=4, name="mixed120")
+@pytest.mark.parametrize("modes", [2, 4, 8])
+def test_mixed_state_256_matches_oracle(api, modes):
+    """The N = 256 forward / mode-scale / inverse kernels: lab geometry, 120 positions, two
+    iterations, for several mode counts (the scale kernel and the inverse pass's scaling are
+    compiled per mode count)."""
+    cfg = dataclasses.replace(synth.CONFIGS["mixed"], J=120, modes=modes, name="mixed120")
     sc = synth.make_scan_torch(cfg, seed=77, device="cuda")
     params = api.fuse_params(levels=cfg.levels, clip=float(cfg.clip))
     fused = api.fuse_stack(sc["raw"], cfg.times, params)
@@ -97,7 +99,7 @@ def test_mixed_state_256_matches_oracle(api):
     fused = fused.cpu().numpy()
     del sc["raw"]
     (o, pr, e), (ro, rp, re) = run(api, sc, fused, 2, 0)
-    assert pr.shape == (4, 256, 256)
+    assert pr.shape == (modes, 256, 256)
     assert rel_l2(o, ro) <= 1e-5
     assert rel_l2(pr, rp) <= 1e-5
     np.testing.assert_allclose(e, re, rtol=1e-5)
