@@ -953,12 +953,12 @@ __global__ void __launch_bounds__(kThreads) k_amplitudes(const float *__restrict
     __shared__ double s[kThreads / 32];
     const int j = blockIdx.x;
     const size_t NN = (size_t)N * N;
-    const int h = N / 2;
+    const int h = N / 2, lgN = __ffs(N) - 1;          // N is a power of two; R is 0 or 16
     double acc = 0.0;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int kx = i / N, w = i % N;             // destination column kx, slot w
-        const int ky = R ? (w / R) + R * (w % R) : w;
-        const int sy = (ky + h) % N, sx = (kx + h) % N;
+        const int kx = i >> lgN, w = i & (N - 1);    // destination column kx, slot w
+        const int ky = R ? (w >> 4) + 16 * (w & 15) : w;
+        const int sy = (ky + h) & (N - 1), sx = (kx + h) & (N - 1);
         const float v = sqrtf(fmaxf(fused[(size_t)j * NN + (size_t)sy * N + sx], 0.f));
         amp[(size_t)j * NN + i] = v;
         if (amp_nat) amp_nat[(size_t)j * NN + (size_t)ky * N + kx] = v;   // row-major [ky][kx]
