@@ -434,7 +434,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
         if (fs_j) {
             const float4 *f = reinterpret_cast<const float4 *>(fs_j + (size_t)g * N + t * R);
 #pragma unroll
-            for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_stream);
+            for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_keep);
         }
         for (int b = 0; b < NB; ++b) {
             const int s = b & 1;
@@ -450,7 +450,7 @@ __device__ __forceinline__ uint32_t tma_unit(const TmaPipe &p, const TmaArgs &a,
                     const float4 *f =
                         reinterpret_cast<const float4 *>(fs_j + (size_t)(kTmaBatch * (b + 1) + g) * N + t * R);
 #pragma unroll
-                    for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_stream);
+                    for (int v = 0; v < R / 4; ++v) Fn[v] = T::ldg_hint(f + v, p.pol_keep);
                 }
 #pragma unroll
                 for (int m = 0; m < R; ++m) d[m] = cscale(d[m], F[m]);
