@@ -208,7 +208,7 @@ def iteration_flops_per_update(N: int) -> float:
 # positions, one launch: dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (their SHA-256, first 16 hex digits).  A changed kernel
 # reports traffic null until it is captured again.
-EXIT_TRAFFIC = {"sources_sha16": "c71d3d741abcc120", "bytes_per_position": 2150299,
+EXIT_TRAFFIC = {"sources_sha16": "7e0377b69d8cbf7c", "bytes_per_position": 2148216,
                 "capture": "ncu, k_exit_wave_tma<16, FULL>, one launch over 888 lab positions = three whole rounds of 296 CTAs"}
 
 
