@@ -152,3 +152,10 @@ def test_batch_create_rejects_null_handle(L):
     assert "handle 0 is NULL" in api.last_error()
     assert L.ptycho_batch_iterate(None, 1, None) == api.PTYCHO_EINVAL
     L.ptycho_batch_destroy(None)
+
+
+def test_release_memory_without_pools(L):
+    """Nothing has allocated (no device here): ptycho_release_memory has no pool to trim and
+    succeeds; the destroy of a NULL handle is a no-op."""
+    assert L.ptycho_release_memory() == api.PTYCHO_OK
+    L.ptycho_destroy(None)
